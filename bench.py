@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: simulate the 30-qubit 5x6 grid circuit (14 cycles, patterns
+ABCDCDAB, random fSim angles; the scale workload of the paper's random-circuit
+benchmarks) on one GB300 per rank, and print one JSON line.
+
+A step = initialise |0...0>, run the fused/tiled plan (every pass of the hot
+path), and reduce the norm (Section 4.1's accuracy check).  The state (8 GB
+complex64) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl own|reference]
+
+For N > 1 (torchrun) every rank simulates its own replica of the circuit
+(the path has no exchange step at one state per GPU): weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "circuit wall time & HBM GB/s at 30–32q; adjoint-gradient time vs forward"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["own", "reference"], default="own")
+    ap.add_argument("--n", type=int, default=30)
+    ap.add_argument("--cycles", type=int, default=14)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--dtype", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--k-max", type=int, default=0, help="0 = pick by a short timing sweep")
+    ap.add_argument("--tile", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def workload_name(a):
+    return f"grid{a.n}_5x6_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}" if a.n == 30 else \
+        f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}"
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- CPU (oracle) sample
+
+def cpu_sample(n: int, cycles: int, seed: int, budget_s: float) -> dict:
+    """Run the FP64 oracle gate by gate on the circuit until `budget_s`
+    seconds have passed (at least one gate); return the seconds per gate."""
+    import oracle
+    from workloads import circuits as C
+    circ = C.scale_grid_circuit(n, cycles, seed)
+    psi = oracle.zero_state(n)
+    t0 = time.perf_counter()
+    done = 0
+    for g in circ.gates:
+        psi = oracle.apply_gate(psi, n, g.qubits, g.matrix)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"n": n, "gates_done": done, "seconds": dt, "sec_per_gate": dt / done,
+            "circuit_gates": len(circ.gates)}
+
+
+def cpu_baseline(a, budget_s=20.0) -> dict:
+    """The oracle as it stands, single-threaded (BLAS pinned to one thread),
+    in a fresh process.  At 30 qubits the oracle needs ~4x the state (16 GB
+    complex128) in host memory; with less memory the sample runs at 28
+    qubits and the per-gate time is scaled by the amplitude ratio."""
+    try:
+        mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        mem = 0
+    need = 4 * (16 << a.n)
+    n_used = a.n if mem > 1.5 * need else min(a.n, 28)
+    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = ("import json,bench;print(json.dumps(bench.cpu_sample(%d,%d,%d,%f)))" % (n_used, a.cycles, a.seed, budget_s))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=600)
+    if r.returncode != 0:
+        raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    scale = float(1 << (a.n - n_used))
+    sec_circuit = d["sec_per_gate"] * scale * d["circuit_gates"]
+    return {"value": 1.0 / sec_circuit, "unit": "circuits/s", "cores": 1, "kind": "oracle",
+            "sample": (f"FP64 numpy oracle, first {d['gates_done']} gates of the {d['n']}-qubit circuit "
+                       f"({d['seconds']:.1f} s), per-gate time x {d['circuit_gates']} gates"
+                       + (f" x {int(scale)} (amplitude ratio {a.n} vs {n_used} qubits)" if scale > 1 else ""))}
+
+
+# ----------------------------------------------------------------- own implementation
+
+def run_own(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+
+    pkg.load()
+    esz = 8 if a.dtype == "c64" else 16
+    state_bytes = (1 << a.n) * esz
+    circ = C.scale_grid_circuit(a.n, a.cycles, a.seed)
+    c = B.circuit_from(circ)
+    state = B.State(a.n, a.dtype)
+    stream = torch.cuda.current_stream()
+
+    def make_plan(k):
+        return B.Plan(c, a.dtype, k_max=k, tile_qubits=a.tile, use_tile=True)
+
+    # pick k_max by timing one execution of each candidate (excluded from the timed region)
+    if a.k_max:
+        k_best = a.k_max
+    else:
+        best = None
+        for k in (2, 3, 4):
+            p = make_plan(k)
+            p.execute(state)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.execute(state)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if best is None or dt < best[0]:
+                best = (dt, k)
+            p.close()
+        k_best = best[1]
+    plan = make_plan(k_best)
+    passes = plan.passes()
+    npass = len(passes)
+
+    def step(events=None):
+        state.init_basis(0)
+        for i in range(npass):
+            plan.execute_range(state, i, 1)
+            if events is not None:
+                events[i].record(stream)
+        return state.norm()
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    pass_events = [[torch.cuda.Event(enable_timing=True) for _ in range(npass)] for _ in range(a.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    norms = []
+    for s in range(a.steps):
+        starts[s].record(stream)
+        norms.append(step(pass_events[s]))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+
+    # per-pass durations from the events recorded inside the timed region
+    by_kind = {}
+    for s in range(a.steps):
+        prev = starts[s]
+        for i in range(npass):
+            dur = prev.elapsed_time(pass_events[s][i])
+            prev = pass_events[s][i]
+            if i == 0:
+                continue  # includes the |0> initialisation
+            kind = passes[i][0]
+            tot, cnt = by_kind.get(kind, (0.0, 0))
+            by_kind[kind] = (tot + dur, cnt + 1)
+    dom = max(by_kind, key=lambda k: by_kind[k][0])
+    avg_ms = by_kind[dom][0] / by_kind[dom][1]
+    peak, peak_src = measured_peaks()
+    achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9
+    ms_step = elapsed_ms / a.steps
+    value = world * a.steps / (elapsed_ms * 1e-3)
+    step_bytes = (npass * 2 + 2) * state_bytes   # passes r+w, init write, norm read
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        e2e_steps = max(1, min(3, a.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h2d = d2h = 0
+        for _ in range(e2e_steps):
+            cc = B.circuit_from(circ)                    # host gate list -> library
+            pp = B.Plan(cc, a.dtype, k_max=k_best, tile_qubits=a.tile, use_tile=True)  # fuse + upload
+            state.init_basis(0)
+            pp.execute(state)
+            nrm = state.norm()                           # D2H 8 bytes
+            amps = state.amplitudes(0, 4096)             # D2H 4096 amplitudes
+            h2d = sum(g.matrix.size * esz for g in circ.gates)
+            d2h = 8 + 4096 * esz
+            pp.close(); cc.close()
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e = {"value": world / e2e_s, "unit": "circuits/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "circuits/s",
+            "n_gpus": world,
+            "steps": a.steps,
+            "warmup": a.warmup,
+            "ms_per_step": ms_step,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": a.dtype,
+            "data": "synthetic (seeded grid circuit generator)",
+            "config": {"workload": workload_name(a), "n": a.n, "cycles": a.cycles, "gates": len(circ.gates),
+                       "k_max": k_best, "tile_qubits": a.tile or "auto", "passes": npass,
+                       "pass_kinds": plan.info()["per_kind"], "l2": "inputs larger than L2 (state 8 GB)",
+                       "parallelism": f"replicas{world}"},
+            "circuit_wall_ms": ms_step,
+            "hbm_gbs_effective": step_bytes / (ms_step * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "avg_launch_ms": avg_ms,
+                         "algorithmic_bytes_per_launch": 2 * state_bytes},
+            "pass_time_ms": {k: {"launches_per_step": v[1] / a.steps, "total_ms_per_step": v[0] / a.steps}
+                             for k, v in by_kind.items()},
+            "norm_last": norms[-1],
+            "gpu_launches": a.steps * (1 + npass + 2),
+            "e2e": e2e,
+            "clocks": clk,
+        }
+        if not a.no_cpu_baseline:
+            try:
+                out["cpu_baseline"] = cpu_baseline(a)
+            except Exception as ex:  # reported, never silently dropped
+                out["cpu_baseline"] = {"error": str(ex)[:300]}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------- reference arm (the oracle)
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each step: a bounded sample of the circuit on the FP64 oracle
+    per_step = []
+    info = None
+    for i in range(a.warmup + a.steps):
+        d = cpu_baseline(a, budget_s=8.0)
+        if i >= a.warmup:
+            per_step.append(1.0 / d["value"])
+            info = d
+    sec = statistics.mean(per_step)
+    value = 1.0 / sec
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded grid circuit generator)",
+           "config": {"workload": workload_name(a), "n": a.n, "cycles": a.cycles},
+           "cpu_baseline": {"value": value, "unit": "circuits/s", "kind": "oracle", "cores": 1,
+                            "sample": info["sample"]},
+           "e2e": {"value": value, "unit": "circuits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse_args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_own(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,242 @@
+/*
+ * qsgb.h -- C ABI of the GB300 (sm_103a) Schroedinger-style state-vector
+ * simulator: fused k-qubit gates applied to a dense 2^n complex state.
+ *
+ * Source of the operations: Fatima & Markov, "Faster Schroedinger-style
+ * simulation of quantum circuits" (arXiv:2008.00216).
+ *   - state: 2^n complex amplitudes alpha_j, computation starts from
+ *     |0...0> (Section 2); all amplitudes are kept (strong simulation).
+ *   - gate: a 2^q x 2^q unitary on qubits i_0..i_{q-1}, applied in place to
+ *     the 2^(n-q) disjoint sets of 2^q amplitudes (Section 3).
+ *   - clustering / reordering of commuting gates before simulation into a
+ *     simulation plan (Sections 4.2 and 4.5, Eq. 2).
+ *   - norm check with robust accumulation (Section 4.1).
+ *
+ * Conventions (every entry point):
+ *   - qubit q is bit q of the amplitude index (qubit 0 = least significant).
+ *   - a k-qubit matrix is 2^k x 2^k, row-major, complex entries interleaved
+ *     (re, im) as doubles, in Kronecker order with qubits[0] the MOST
+ *     significant local bit (Section 2's CNOT lists the control first).
+ *     So kron(A, B) on {a, b} equals A on a followed by B on b.
+ *   - matrices are always FP64 host memory and are copied before return.
+ *   - device state: interleaved complex64 (QS_C64: float re, im) or
+ *     complex128 (QS_C128), the layout of torch.complex64/complex128.
+ *   - every call returns a status and never aborts, traps or asserts;
+ *     arguments are checked on the host before any launch.  On failure,
+ *     qs_last_error() returns a message for the calling thread.
+ *   - work is enqueued on the state's CUDA stream and is asynchronous,
+ *     except calls that return host values (qs_amplitudes, qs_norm,
+ *     qs_expectation, qs_adjoint_gradient, qs_batch_run's results), which
+ *     synchronise that stream.
+ *   - objects are not thread-safe; use one object per thread or lock.
+ */
+#ifndef QSGB_H
+#define QSGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum qs_status {
+    QS_OK = 0,
+    QS_ERR_ARG = 1,          /* invalid argument (null, range, shape, alignment) */
+    QS_ERR_OOM = 2,          /* device or host allocation failed / would not fit */
+    QS_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has details) */
+    QS_ERR_UNSUPPORTED = 4,  /* valid request this build does not implement */
+    QS_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    QS_ERR_STATE = 6         /* object in the wrong state for this call */
+} qs_status;
+
+typedef enum qs_dtype { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Arithmetic of dense fused gates with k >= 5 on a complex64 state.  FP32 is
+ * plain FP32 on the CUDA cores; the others run the 2^k x 2^k complex
+ * product on the tensor cores (tcgen05) with FP32 accumulation: TF32
+ * operands, split 3xTF32 (hi*hi + hi*lo + lo*hi) or split 3xBF16.
+ * Ignored for complex128 states (always FP64-accurate arithmetic). */
+typedef enum qs_precision {
+    QS_PREC_FP32 = 0,
+    QS_PREC_TF32 = 1,
+    QS_PREC_3XTF32 = 2,
+    QS_PREC_3XBF16 = 3
+} qs_precision;
+
+/* Kind of a (fused) gate, from its exact FP64 entries. */
+typedef enum qs_gate_kind {
+    QS_GATE_DENSE = 0,
+    QS_GATE_DIAGONAL = 1,   /* only the diagonal is nonzero */
+    QS_GATE_MONOMIAL = 2    /* one nonzero per row and column (permutation with phases) */
+} qs_gate_kind;
+
+typedef struct qs_state qs_state;
+typedef struct qs_circuit qs_circuit;
+typedef struct qs_plan qs_plan;
+typedef struct qs_pauli_sum qs_pauli_sum;
+
+/* Planner and kernel options (qs_options_default fills the defaults).
+ *   k_max       : largest fused gate, 1..6 (qs_fuse's bound).
+ *   tile_qubits : qubits held per shared-memory tile, 0 = automatic;
+ *                 otherwise 6..13 (c64) / 6..12 (c128).
+ *   use_tile    : 1 = group consecutive gates on tile qubits into one pass.
+ *   precision   : qs_precision for dense k >= 5 gates on complex64.
+ *   fuse        : 1 = run qs_fuse(k_max) inside qs_plan_create.          */
+typedef struct qs_options {
+    int k_max;
+    int tile_qubits;
+    int use_tile;
+    int precision;
+    int fuse;
+    int reserved[8];
+} qs_options;
+
+const char* qs_version(void);
+const char* qs_status_string(qs_status s);
+/* Message of the last failed call on this thread ("" if none). */
+const char* qs_last_error(void);
+qs_status qs_options_default(qs_options* opt);
+
+/* ------------------------------------------------------------------ state */
+
+/* Allocate a library-owned device state of 2^n amplitudes (1 <= n <= 36)
+ * on the current device, initialised to |0...0> (Section 2).  `stream` is a
+ * cudaStream_t (NULL = legacy default stream).  QS_ERR_OOM if the free
+ * device memory cannot hold it. */
+qs_status qs_state_create(int n, qs_dtype dt, void* stream, qs_state** out);
+
+/* Wrap caller-owned device memory (e.g. a torch tensor) of 2^n amplitudes.
+ * `device_ptr` must be 16-byte aligned; the caller keeps it alive until
+ * qs_state_destroy.  The contents are left as they are. */
+qs_status qs_state_wrap(void* device_ptr, int n, qs_dtype dt, void* stream, qs_state** out);
+
+/* Free the handle (and the amplitudes if library-owned).  NULL is a no-op. */
+qs_status qs_state_destroy(qs_state* s);
+
+qs_status qs_state_set_stream(qs_state* s, void* stream);
+qs_status qs_state_info(const qs_state* s, int* n, qs_dtype* dt, void** device_ptr);
+
+/* |index> (all amplitudes 0 except alpha_index = 1). */
+qs_status qs_state_init_basis(qs_state* s, uint64_t index);
+
+/* H on every qubit of |0...0>: every amplitude 2^(-n/2).  Section 4.5 notes
+ * that the initial Hadamard layer can be replaced by this initialisation. */
+qs_status qs_state_init_uniform(qs_state* s);
+
+/* Device-to-device copy of all amplitudes; n and dtype must match. */
+qs_status qs_state_copy(qs_state* dst, const qs_state* src);
+
+/* ------------------------------------------------------------------ gates */
+
+/* Apply one k-qubit gate (1 <= k <= 6, distinct qubits < n) in place
+ * (Section 3).  m: 2^k x 2^k FP64 complex, interleaved, Kronecker order. */
+qs_status qs_apply_gate(qs_state* s, const int* qubits, int k, const double* m);
+
+/* --------------------------------------------------------------- circuits */
+
+qs_status qs_circuit_create(int n, qs_circuit** out);
+qs_status qs_circuit_destroy(qs_circuit* c);
+
+/* Append a fixed gate (copied). */
+qs_status qs_circuit_add(qs_circuit* c, const int* qubits, int k, const double* m);
+
+/* Append a parametrised gate exp(-i theta P / 2) with P the Pauli string
+ * `paulis` ("X", "ZZ", "XY", ... ; paulis[i] acts on qubits[i]), parameter
+ * index `param` >= 0 and current value `theta`. */
+qs_status qs_circuit_add_rotation(qs_circuit* c, const int* qubits, int k,
+                                  const char* paulis, int param, double theta);
+
+/* Set every parameter (theta[p] for p < num) and rebuild rotation matrices. */
+qs_status qs_circuit_set_params(qs_circuit* c, const double* theta, int num);
+
+qs_status qs_circuit_size(const qs_circuit* c, int* n, int* num_gates, int* num_params);
+
+/* Read back gate `index`: k, qubits (up to 6 ints), matrix (up to
+ * 2*4^k doubles) and its qs_gate_kind.  Any output pointer may be NULL. */
+qs_status qs_circuit_gate(const qs_circuit* c, int index, int* k, int* qubits,
+                          double* m, int* kind);
+
+/* Gate fusion with commuting reorder (Sections 4.2 and 4.5, Eq. 2): scan the
+ * gates in order; start a block at the first unplaced gate and pull each
+ * later gate into it when every gate skipped so far commutes with it
+ * (disjoint qubits, or both diagonal) and the block's qubit set stays
+ * within k_max (1..6).  Block matrices are the FP64 products, each block is
+ * classified dense / diagonal / monomial.  Rotation parameters are dropped:
+ * the result is a fixed circuit.  *out is a new circuit owned by the caller. */
+qs_status qs_fuse(const qs_circuit* in, int k_max, qs_circuit** out);
+
+/* ------------------------------------------------------------------ plans */
+
+/* Build an execution plan for circuits on states of c's n and dtype dt:
+ * optional fusion, grouping into passes (shared-memory tile passes, strided
+ * dense passes, diagonal / monomial passes, tensor-core passes), matrices
+ * converted to the state's precision and uploaded to the device.  Uses the
+ * current device; `opt` may be NULL for defaults. */
+qs_status qs_plan_create(const qs_circuit* c, qs_dtype dt, const qs_options* opt, qs_plan** out);
+qs_status qs_plan_destroy(qs_plan* p);
+
+/* Number of passes (full HBM round trips) and kernel launches of the plan,
+ * and the passes of each kind (array of 8: tile, dense, diagonal, monomial,
+ * tensor-core, dense-smem, reserved, reserved; may be NULL). */
+qs_status qs_plan_info(const qs_plan* p, int* num_passes, int* num_launches, int* per_kind);
+
+/* Enqueue the plan on the state's stream.  n and dtype must match. */
+qs_status qs_plan_execute(qs_state* s, const qs_plan* p);
+
+/* Enqueue passes [first, first+count) only (count < 0: to the end); used to
+ * time passes one by one.  Running every range in order equals execute. */
+qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int count);
+
+/* Describe pass i: its kind (index as in qs_plan_info), qubits touched per
+ * amplitude pass (k, or the tile's L), and gates applied in it. */
+qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_gates);
+
+/* Convenience: plan with defaults (k_max 6 fusion) and the given precision,
+ * execute, free the plan.  Asynchronous like qs_plan_execute. */
+qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec);
+
+/* ------------------------------------------------------------ read back */
+
+/* Copy amplitudes [first, first+count) to host `out` as interleaved FP64
+ * (2*count doubles).  Synchronises the state's stream. */
+qs_status qs_amplitudes(const qs_state* s, uint64_t first, uint64_t count, double* out);
+
+/* sum_j |alpha_j|^2 with per-thread compensated (two-float) accumulation
+ * and FP64 cross-block sums (Section 4.1).  Synchronises the stream. */
+qs_status qs_norm(const qs_state* s, double* out);
+
+/* ------------------------------------------------------------ observables */
+
+qs_status qs_pauli_sum_create(int n, qs_pauli_sum** out);
+qs_status qs_pauli_sum_destroy(qs_pauli_sum* h);
+/* Add coeff * P with P = paulis[i] on qubits[i] ('I','X','Y','Z'), len <= n. */
+qs_status qs_pauli_sum_add(qs_pauli_sum* h, double coeff, const int* qubits,
+                           const char* paulis, int len);
+
+/* <psi|H|psi> (real part), FP64 accumulation.  Synchronises the stream. */
+qs_status qs_expectation(const qs_state* s, const qs_pauli_sum* h, double* out);
+
+/* out = H psi (states of equal n and dtype, distinct memory). Asynchronous. */
+qs_status qs_apply_pauli_sum(const qs_state* psi, const qs_pauli_sum* h, qs_state* out);
+
+/* ------------------------------------------------------------ gradients */
+
+/* Adjoint (reverse state-vector) gradient of E(theta) = <0|U^dag H U|0> for a
+ * circuit whose parametrised gates are exp(-i theta_p P / 2) (each
+ * parameter used by one gate).  Sets the circuit's parameters to theta,
+ * runs U on `psi` from |0...0>, forms lambda = H psi in `lam`, E = <psi|lam>,
+ * then walks the gates backwards: at each parametrised gate
+ * dE/dtheta = Im <lambda|P|psi>, then psi <- U_l^dag psi and
+ * lambda <- U_l^dag lambda (no intermediate states stored).  `psi` and
+ * `lam` are work states with the circuit's n and a common dtype;
+ * grad has num_params entries (host).  Synchronises. */
+qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params,
+                              const qs_pauli_sum* h, qs_state* psi, qs_state* lam,
+                              double* energy, double* grad);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSGB_H */

@@ -1,0 +1,740 @@
+// C ABI entry points: argument checks, object management and the host side
+// of every operation.  Device work goes through the launchers in the .cu
+// files; nothing here computes on amplitudes.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <memory>
+#include <new>
+
+#include "qs_internal.h"
+
+namespace qsgb {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+qs_status fail(qs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+qs_status cuda_fail(cudaError_t e, const char* what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    if (e == cudaErrorMemoryAllocation) return QS_ERR_OOM;
+    return QS_ERR_CUDA;
+}
+
+int num_sms() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)
+            v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+static qs_status check_gate_args(int n, const int* qubits, int k, const double* m) {
+    if (!qubits || !m) return fail(QS_ERR_ARG, "null qubits or matrix");
+    if (k < 1 || k > kMaxK) return fail(QS_ERR_ARG, "gate size k=%d outside 1..6", k);
+    if (k > n) return fail(QS_ERR_ARG, "gate on %d qubits in a %d-qubit state", k, n);
+    uint64_t seen = 0;
+    for (int i = 0; i < k; ++i) {
+        if (qubits[i] < 0 || qubits[i] >= n)
+            return fail(QS_ERR_ARG, "qubit %d out of range 0..%d", qubits[i], n - 1);
+        if ((seen >> qubits[i]) & 1) return fail(QS_ERR_ARG, "duplicate qubit %d", qubits[i]);
+        seen |= 1ull << qubits[i];
+    }
+    const int d = 1 << k;
+    for (int i = 0; i < 2 * d * d; ++i)
+        if (!(m[i] == m[i]) || m[i] > 1e300 || m[i] < -1e300)
+            return fail(QS_ERR_ARG, "matrix entry %d is not finite", i);
+    return QS_OK;
+}
+
+static qs_status check_state(const qs_state* s) {
+    if (!s) return fail(QS_ERR_ARG, "null state");
+    int dev = -1;
+    QS_CUDA(cudaGetDevice(&dev));
+    if (dev != s->device)
+        return fail(QS_ERR_ARG, "state lives on device %d but device %d is current", s->device, dev);
+    return QS_OK;
+}
+
+static qs_status state_setup(qs_state* s) {
+    // reduction partials (two per block, plus a result area) and a small
+    // pinned buffer for results
+    s->scratch_doubles = (size_t)reduce_blocks() * 2 + 64;
+    QS_CUDA(cudaMalloc(&s->scratch, s->scratch_doubles * sizeof(double)));
+    QS_CUDA(cudaMallocHost(&s->host_pinned, 64 * sizeof(double)));
+    return QS_OK;
+}
+
+static double* result_area(const qs_state* s) {
+    return s->scratch + s->scratch_doubles - 64;
+}
+
+}  // namespace qsgb
+
+using namespace qsgb;
+
+extern "C" {
+
+const char* qs_version(void) { return "qsgb 0.1 (sm_103a)"; }
+
+const char* qs_status_string(qs_status s) {
+    switch (s) {
+        case QS_OK: return "ok";
+        case QS_ERR_ARG: return "invalid argument";
+        case QS_ERR_OOM: return "out of memory";
+        case QS_ERR_CUDA: return "CUDA error";
+        case QS_ERR_UNSUPPORTED: return "unsupported";
+        case QS_ERR_TIMEOUT: return "device wait timed out";
+        case QS_ERR_STATE: return "object in wrong state";
+    }
+    return "unknown status";
+}
+
+const char* qs_last_error(void) { return g_last_error.c_str(); }
+
+qs_status qs_options_default(qs_options* opt) {
+    if (!opt) return fail(QS_ERR_ARG, "null options");
+    memset(opt, 0, sizeof(*opt));
+    opt->k_max = 4;
+    opt->tile_qubits = 0;
+    opt->use_tile = 1;
+    opt->precision = QS_PREC_FP32;
+    opt->fuse = 1;
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ state
+
+qs_status qs_state_create(int n, qs_dtype dt, void* stream, qs_state** out) {
+    if (!out) return fail(QS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_ARG, "n=%d outside 1..%d", n, kMaxQubits);
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_ERR_ARG, "bad dtype");
+    const size_t bytes = (size_t(1) << n) * (dt == QS_C64 ? 8 : 16);
+    size_t free_b = 0, total_b = 0;
+    QS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    if (bytes + (64u << 20) > free_b)
+        return fail(QS_ERR_OOM, "state needs %zu bytes, %zu free", bytes, free_b);
+    std::unique_ptr<qs_state> s(new (std::nothrow) qs_state);
+    if (!s) return fail(QS_ERR_OOM, "host allocation failed");
+    s->n = n;
+    s->dt = dt;
+    s->stream = (cudaStream_t)stream;
+    QS_CUDA(cudaGetDevice(&s->device));
+    cudaError_t e = cudaMallocAsync(&s->data, bytes, s->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(state)");
+    s->owned = true;
+    qs_status st = state_setup(s.get());
+    if (st != QS_OK) {
+        cudaFreeAsync(s->data, s->stream);
+        return st;
+    }
+    e = launch_init_basis(s->data, n, dt, 0, s->stream);
+    if (e != cudaSuccess) {
+        qs_state_destroy(s.release());
+        return cuda_fail(e, "init |0>");
+    }
+    *out = s.release();
+    return QS_OK;
+}
+
+qs_status qs_state_wrap(void* device_ptr, int n, qs_dtype dt, void* stream, qs_state** out) {
+    if (!out) return fail(QS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (!device_ptr) return fail(QS_ERR_ARG, "null device pointer");
+    if (((uintptr_t)device_ptr) & 15) return fail(QS_ERR_ARG, "device pointer not 16-byte aligned");
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_ARG, "n=%d outside 1..%d", n, kMaxQubits);
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_ERR_ARG, "bad dtype");
+    cudaPointerAttributes attr;
+    QS_CUDA(cudaPointerGetAttributes(&attr, device_ptr));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(QS_ERR_ARG, "pointer is not device memory");
+    std::unique_ptr<qs_state> s(new (std::nothrow) qs_state);
+    if (!s) return fail(QS_ERR_OOM, "host allocation failed");
+    s->n = n;
+    s->dt = dt;
+    s->data = device_ptr;
+    s->owned = false;
+    s->stream = (cudaStream_t)stream;
+    QS_CUDA(cudaGetDevice(&s->device));
+    if (attr.device != s->device)
+        return fail(QS_ERR_ARG, "pointer on device %d, current device %d", attr.device, s->device);
+    qs_status st = state_setup(s.get());
+    if (st != QS_OK) return st;
+    *out = s.release();
+    return QS_OK;
+}
+
+qs_status qs_state_destroy(qs_state* s) {
+    if (!s) return QS_OK;
+    if (s->owned && s->data) cudaFreeAsync(s->data, s->stream);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    else cudaDeviceSynchronize();
+    if (s->scratch) cudaFree(s->scratch);
+    if (s->host_pinned) cudaFreeHost(s->host_pinned);
+    delete s;
+    return QS_OK;
+}
+
+qs_status qs_state_set_stream(qs_state* s, void* stream) {
+    if (!s) return fail(QS_ERR_ARG, "null state");
+    s->stream = (cudaStream_t)stream;
+    return QS_OK;
+}
+
+qs_status qs_state_info(const qs_state* s, int* n, qs_dtype* dt, void** device_ptr) {
+    if (!s) return fail(QS_ERR_ARG, "null state");
+    if (n) *n = s->n;
+    if (dt) *dt = s->dt;
+    if (device_ptr) *device_ptr = s->data;
+    return QS_OK;
+}
+
+qs_status qs_state_init_basis(qs_state* s, uint64_t index) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (index >= s->size()) return fail(QS_ERR_ARG, "basis index out of range");
+    QS_CUDA(launch_init_basis(s->data, s->n, s->dt, index, s->stream));
+    return QS_OK;
+}
+
+qs_status qs_state_init_uniform(qs_state* s) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    QS_CUDA(launch_init_uniform(s->data, s->n, s->dt, s->stream));
+    return QS_OK;
+}
+
+qs_status qs_state_copy(qs_state* dst, const qs_state* src) {
+    qs_status st = check_state(dst);
+    if (st != QS_OK) return st;
+    st = check_state(src);
+    if (st != QS_OK) return st;
+    if (dst->n != src->n || dst->dt != src->dt) return fail(QS_ERR_ARG, "state shapes differ");
+    if (dst->data == src->data) return QS_OK;
+    QS_CUDA(cudaMemcpyAsync(dst->data, src->data, src->size() * src->amp_bytes(),
+                            cudaMemcpyDeviceToDevice, dst->stream));
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ gates
+
+static qs_status apply_one(qs_state* s, const GateRec& g) {
+    cudaError_t e;
+    if (g.kind == QS_GATE_DIAGONAL) {
+        e = launch_diag(s->data, s->n, s->dt, g.k, g.qubits, g.m.data(), s->stream);
+    } else if (g.kind == QS_GATE_MONOMIAL) {
+        e = launch_mono(s->data, s->n, s->dt, g.k, g.qubits, g.m.data(), s->stream);
+    } else if (g.k <= 4) {
+        e = launch_dense(s->data, s->n, s->dt, g.k, g.qubits, g.m.data(), s->stream);
+    } else {
+        // large dense gate: stage the converted matrix in device scratch
+        const int d = 1 << g.k;
+        const size_t elems = (size_t)d * d;
+        void* dm = nullptr;
+        const size_t bytes = elems * (s->dt == QS_C64 ? 8 : 16);
+        QS_CUDA(cudaMallocAsync(&dm, bytes, s->stream));
+        std::vector<float> f;
+        const void* src = g.m.data();
+        if (s->dt == QS_C64) {
+            f.resize(2 * elems);
+            for (size_t i = 0; i < 2 * elems; ++i) f[i] = (float)g.m[i];
+            src = f.data();
+        }
+        e = cudaMemcpyAsync(dm, src, bytes, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);  // host copy stays valid
+        if (e == cudaSuccess) e = launch_dense_smem(s->data, s->n, s->dt, g.k, g.qubits, dm, s->stream);
+        cudaFreeAsync(dm, s->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "gate launch");
+    return QS_OK;
+}
+
+qs_status qs_apply_gate(qs_state* s, const int* qubits, int k, const double* m) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    st = check_gate_args(s->n, qubits, k, m);
+    if (st != QS_OK) return st;
+    GateRec g;
+    g.k = k;
+    for (int i = 0; i < k; ++i) g.qubits[i] = qubits[i];
+    g.m.assign(m, m + 2 * (1 << k) * (1 << k));
+    g.kind = classify_matrix(k, m);
+    return apply_one(s, g);
+}
+
+// --------------------------------------------------------------- circuits
+
+qs_status qs_circuit_create(int n, qs_circuit** out) {
+    if (!out) return fail(QS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_ARG, "n=%d outside 1..%d", n, kMaxQubits);
+    qs_circuit* c = new (std::nothrow) qs_circuit;
+    if (!c) return fail(QS_ERR_OOM, "host allocation failed");
+    c->n = n;
+    *out = c;
+    return QS_OK;
+}
+
+qs_status qs_circuit_destroy(qs_circuit* c) {
+    delete c;
+    return QS_OK;
+}
+
+qs_status qs_circuit_add(qs_circuit* c, const int* qubits, int k, const double* m) {
+    if (!c) return fail(QS_ERR_ARG, "null circuit");
+    qs_status st = check_gate_args(c->n, qubits, k, m);
+    if (st != QS_OK) return st;
+    GateRec g;
+    g.k = k;
+    for (int i = 0; i < k; ++i) g.qubits[i] = qubits[i];
+    g.m.assign(m, m + 2 * (1 << k) * (1 << k));
+    g.kind = classify_matrix(k, m);
+    c->gates.push_back(std::move(g));
+    return QS_OK;
+}
+
+qs_status qs_circuit_add_rotation(qs_circuit* c, const int* qubits, int k, const char* paulis,
+                                  int param, double theta) {
+    if (!c || !qubits || !paulis) return fail(QS_ERR_ARG, "null argument");
+    if (k < 1 || k > kMaxK || k > c->n) return fail(QS_ERR_ARG, "bad rotation size %d", k);
+    if (param < 0) return fail(QS_ERR_ARG, "parameter index must be >= 0");
+    if ((int)strnlen(paulis, kMaxK + 1) != k) return fail(QS_ERR_ARG, "Pauli string length != k");
+    for (int i = 0; i < k; ++i)
+        if (!strchr("IXYZ", paulis[i])) return fail(QS_ERR_ARG, "bad Pauli letter '%c'", paulis[i]);
+    GateRec g;
+    g.k = k;
+    for (int i = 0; i < k; ++i) g.qubits[i] = qubits[i];
+    g.m.resize(2 * (1 << k) * (1 << k));
+    rotation_matrix(k, paulis, theta, g.m.data());
+    qs_status st = check_gate_args(c->n, qubits, k, g.m.data());
+    if (st != QS_OK) return st;
+    g.kind = classify_matrix(k, g.m.data());
+    g.param = param;
+    memcpy(g.paulis, paulis, k);
+    g.paulis[k] = 0;
+    c->gates.push_back(std::move(g));
+    c->num_params = std::max(c->num_params, param + 1);
+    return QS_OK;
+}
+
+qs_status qs_circuit_set_params(qs_circuit* c, const double* theta, int num) {
+    if (!c || (!theta && num > 0)) return fail(QS_ERR_ARG, "null argument");
+    if (num < c->num_params) return fail(QS_ERR_ARG, "need %d parameters, got %d", c->num_params, num);
+    for (GateRec& g : c->gates) {
+        if (g.param < 0) continue;
+        rotation_matrix(g.k, g.paulis, theta[g.param], g.m.data());
+        g.kind = classify_matrix(g.k, g.m.data());
+    }
+    return QS_OK;
+}
+
+qs_status qs_circuit_size(const qs_circuit* c, int* n, int* num_gates, int* num_params) {
+    if (!c) return fail(QS_ERR_ARG, "null circuit");
+    if (n) *n = c->n;
+    if (num_gates) *num_gates = (int)c->gates.size();
+    if (num_params) *num_params = c->num_params;
+    return QS_OK;
+}
+
+qs_status qs_circuit_gate(const qs_circuit* c, int index, int* k, int* qubits, double* m, int* kind) {
+    if (!c) return fail(QS_ERR_ARG, "null circuit");
+    if (index < 0 || index >= (int)c->gates.size()) return fail(QS_ERR_ARG, "gate index out of range");
+    const GateRec& g = c->gates[index];
+    if (k) *k = g.k;
+    if (qubits) memcpy(qubits, g.qubits, sizeof(int) * g.k);
+    if (m) memcpy(m, g.m.data(), sizeof(double) * g.m.size());
+    if (kind) *kind = g.kind;
+    return QS_OK;
+}
+
+qs_status qs_fuse(const qs_circuit* in, int k_max, qs_circuit** out) {
+    if (!in || !out) return fail(QS_ERR_ARG, "null argument");
+    *out = nullptr;
+    std::unique_ptr<qs_circuit> c(new (std::nothrow) qs_circuit);
+    if (!c) return fail(QS_ERR_OOM, "host allocation failed");
+    c->n = in->n;
+    qs_status st = fuse_gates(in->n, in->gates, k_max, c->gates);
+    if (st != QS_OK) return st;
+    *out = c.release();
+    return QS_OK;
+}
+
+// ------------------------------------------------------------------ plans
+
+qs_status qs_plan_create(const qs_circuit* c, qs_dtype dt, const qs_options* opt_in, qs_plan** out) {
+    if (!c || !out) return fail(QS_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (dt != QS_C64 && dt != QS_C128) return fail(QS_ERR_ARG, "bad dtype");
+    qs_options opt;
+    if (opt_in) opt = *opt_in;
+    else qs_options_default(&opt);
+    if (opt.k_max < 1 || opt.k_max > kMaxK) return fail(QS_ERR_ARG, "k_max outside 1..6");
+    const int maxL = dt == QS_C64 ? 13 : 12;
+    if (opt.tile_qubits != 0 && (opt.tile_qubits < 6 || opt.tile_qubits > maxL))
+        return fail(QS_ERR_ARG, "tile_qubits outside 6..%d", maxL);
+    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XBF16)
+        return fail(QS_ERR_ARG, "bad precision");
+    std::unique_ptr<qs_plan> p(new (std::nothrow) qs_plan);
+    if (!p) return fail(QS_ERR_OOM, "host allocation failed");
+    p->n = c->n;
+    p->dt = dt;
+    p->opt = opt;
+    QS_CUDA(cudaGetDevice(&p->device));
+    std::vector<GateRec> blocks;
+    qs_status st;
+    if (opt.fuse) {
+        st = fuse_gates(c->n, c->gates, opt.k_max, blocks);
+        if (st != QS_OK) return st;
+    } else {
+        blocks = c->gates;
+    }
+    st = build_passes(c->n, dt, blocks, opt, p->passes);
+    if (st != QS_OK) return st;
+    // upload every pass's matrices, converted to the state's precision
+    size_t total = 0;
+    for (Pass& ps : p->passes) {
+        ps.dev_offset = total;
+        total += ps.mats.size() / 2;
+    }
+    p->dev_elems = total;
+    if (total) {
+        const size_t esz = dt == QS_C64 ? 8 : 16;
+        std::vector<char> host(total * esz);
+        size_t at = 0;
+        for (const Pass& ps : p->passes) {
+            for (size_t i = 0; i < ps.mats.size(); ++i) {
+                if (dt == QS_C64) ((float*)host.data())[2 * at + i] = (float)ps.mats[i];
+                else ((double*)host.data())[2 * at + i] = ps.mats[i];
+            }
+            at += ps.mats.size() / 2;
+        }
+        QS_CUDA(cudaMalloc(&p->dev_mats, total * esz));
+        cudaError_t e = cudaMemcpy(p->dev_mats, host.data(), total * esz, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p->dev_mats);
+            return cuda_fail(e, "plan matrix upload");
+        }
+    }
+    *out = p.release();
+    return QS_OK;
+}
+
+qs_status qs_plan_destroy(qs_plan* p) {
+    if (!p) return QS_OK;
+    if (p->dev_mats) cudaFree(p->dev_mats);
+    delete p;
+    return QS_OK;
+}
+
+qs_status qs_plan_info(const qs_plan* p, int* num_passes, int* num_launches, int* per_kind) {
+    if (!p) return fail(QS_ERR_ARG, "null plan");
+    if (num_passes) *num_passes = (int)p->passes.size();
+    if (num_launches) *num_launches = (int)p->passes.size();
+    if (per_kind) {
+        for (int i = 0; i < 8; ++i) per_kind[i] = 0;
+        for (const Pass& ps : p->passes) per_kind[ps.kind]++;
+    }
+    return QS_OK;
+}
+
+qs_status qs_plan_execute(qs_state* s, const qs_plan* p) { return qs_plan_execute_range(s, p, 0, -1); }
+
+qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_gates) {
+    if (!p) return fail(QS_ERR_ARG, "null plan");
+    if (i < 0 || i >= (int)p->passes.size()) return fail(QS_ERR_ARG, "pass index out of range");
+    const Pass& ps = p->passes[i];
+    if (kind) *kind = ps.kind;
+    if (width) *width = ps.kind == PASS_TILE ? ps.L : ps.k;
+    if (num_gates) *num_gates = ps.kind == PASS_TILE ? (int)ps.tgates.size() : 1;
+    return QS_OK;
+}
+
+qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int count) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!p) return fail(QS_ERR_ARG, "null plan");
+    const int np = (int)p->passes.size();
+    if (first < 0 || first > np) return fail(QS_ERR_ARG, "first pass out of range");
+    const int last = count < 0 ? np : std::min(np, first + count);
+    if (p->n != s->n || p->dt != s->dt) return fail(QS_ERR_ARG, "plan built for another n/dtype");
+    if (p->device != s->device) return fail(QS_ERR_ARG, "plan built on another device");
+    const size_t esz = s->dt == QS_C64 ? 8 : 16;
+    for (int pi = first; pi < last; ++pi) {
+        const Pass& ps = p->passes[pi];
+        const char* dm = (const char*)p->dev_mats + ps.dev_offset * esz;
+        cudaError_t e = cudaSuccess;
+        switch (ps.kind) {
+            case PASS_TILE: e = launch_tile(s->data, s->n, s->dt, ps, dm, s->stream); break;
+            case PASS_DENSE:
+                e = launch_dense(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+                break;
+            case PASS_DIAG:
+                e = launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+                break;
+            case PASS_MONO:
+                e = launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+                break;
+            case PASS_GEMM:
+                e = launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, p->opt.precision, s->stream);
+                if (e == cudaErrorNotSupported)
+                    return fail(QS_ERR_UNSUPPORTED, "tensor-core pass unavailable in this build");
+                break;
+            case PASS_DENSE_SMEM:
+                e = launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
+                break;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "pass launch");
+    }
+    return QS_OK;
+}
+
+qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec) {
+    if (!s || !c) return fail(QS_ERR_ARG, "null argument");
+    if (c->n != s->n) return fail(QS_ERR_ARG, "circuit and state qubit counts differ");
+    qs_options opt;
+    qs_options_default(&opt);
+    opt.precision = prec;
+    qs_plan* p = nullptr;
+    qs_status st = qs_plan_create(c, s->dt, &opt, &p);
+    if (st != QS_OK) return st;
+    st = qs_plan_execute(s, p);
+    if (st == QS_OK) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);  // the plan's buffers are freed next
+        if (e != cudaSuccess) st = cuda_fail(e, "synchronise after circuit");
+    }
+    qs_plan_destroy(p);
+    return st;
+}
+
+// ------------------------------------------------------------- read back
+
+qs_status qs_amplitudes(const qs_state* s, uint64_t first, uint64_t count, double* out) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!out && count) return fail(QS_ERR_ARG, "null output");
+    if (first > s->size() || count > s->size() - first) return fail(QS_ERR_ARG, "range out of bounds");
+    if (!count) return QS_OK;
+    const size_t esz = s->amp_bytes();
+    const char* src = (const char*)s->data + first * esz;
+    if (s->dt == QS_C128) {
+        QS_CUDA(cudaMemcpyAsync(out, src, count * esz, cudaMemcpyDeviceToHost, s->stream));
+        QS_CUDA(cudaStreamSynchronize(s->stream));
+        return QS_OK;
+    }
+    // complex64: copy in chunks through a host buffer, widen to FP64
+    const uint64_t chunk = 1ull << 22;
+    std::vector<float> buf((size_t)std::min(count, chunk) * 2);
+    for (uint64_t at = 0; at < count; at += chunk) {
+        const uint64_t c = std::min(chunk, count - at);
+        QS_CUDA(cudaMemcpyAsync(buf.data(), src + at * esz, c * esz, cudaMemcpyDeviceToHost, s->stream));
+        QS_CUDA(cudaStreamSynchronize(s->stream));
+        for (uint64_t i = 0; i < 2 * c; ++i) out[2 * at + i] = (double)buf[i];
+    }
+    return QS_OK;
+}
+
+qs_status qs_norm(const qs_state* s, double* out) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!out) return fail(QS_ERR_ARG, "null output");
+    double* res = result_area(s);
+    QS_CUDA(launch_norm(s->data, s->n, s->dt, s->scratch, res, s->stream));
+    QS_CUDA(cudaMemcpyAsync(s->host_pinned, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    *out = s->host_pinned[0];
+    return QS_OK;
+}
+
+// ------------------------------------------------------------ observables
+
+qs_status qs_pauli_sum_create(int n, qs_pauli_sum** out) {
+    if (!out) return fail(QS_ERR_ARG, "null output pointer");
+    *out = nullptr;
+    if (n < 1 || n > kMaxQubits) return fail(QS_ERR_ARG, "n=%d outside 1..%d", n, kMaxQubits);
+    qs_pauli_sum* h = new (std::nothrow) qs_pauli_sum;
+    if (!h) return fail(QS_ERR_OOM, "host allocation failed");
+    h->n = n;
+    *out = h;
+    return QS_OK;
+}
+
+qs_status qs_pauli_sum_destroy(qs_pauli_sum* h) {
+    delete h;
+    return QS_OK;
+}
+
+qs_status qs_pauli_sum_add(qs_pauli_sum* h, double coeff, const int* qubits, const char* paulis, int len) {
+    if (!h || (len > 0 && (!qubits || !paulis))) return fail(QS_ERR_ARG, "null argument");
+    if (len < 0 || len > h->n) return fail(QS_ERR_ARG, "bad term length %d", len);
+    if (!(coeff == coeff)) return fail(QS_ERR_ARG, "coefficient is NaN");
+    qs_pauli_sum::Term t{coeff, 0, 0, 0};
+    uint64_t seen = 0;
+    for (int i = 0; i < len; ++i) {
+        const int q = qubits[i];
+        if (q < 0 || q >= h->n) return fail(QS_ERR_ARG, "qubit %d out of range", q);
+        if ((seen >> q) & 1) return fail(QS_ERR_ARG, "duplicate qubit %d in term", q);
+        seen |= 1ull << q;
+        switch (paulis[i]) {
+            case 'I': break;
+            case 'X': t.xmask |= 1ull << q; break;
+            case 'Y': t.xmask |= 1ull << q; t.zmask |= 1ull << q; t.ny++; break;
+            case 'Z': t.zmask |= 1ull << q; break;
+            default: return fail(QS_ERR_ARG, "bad Pauli letter '%c'", paulis[i]);
+        }
+    }
+    h->terms.push_back(t);
+    return QS_OK;
+}
+
+qs_status qs_expectation(const qs_state* s, const qs_pauli_sum* h, double* out) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    if (!h || !out) return fail(QS_ERR_ARG, "null argument");
+    if (h->n != s->n) return fail(QS_ERR_ARG, "Hamiltonian and state qubit counts differ");
+    // group terms by flip mask: one pass over the state per group
+    std::map<uint64_t, std::vector<qs_pauli_sum::Term>> groups;
+    for (const auto& t : h->terms) groups[t.xmask].push_back(t);
+    double* res = result_area(s);
+    QS_CUDA(cudaMemsetAsync(res, 0, sizeof(double), s->stream));
+    for (auto& kv : groups) {
+        const auto& v = kv.second;
+        for (size_t at = 0; at < v.size(); at += 32) {
+            const int cnt = (int)std::min<size_t>(32, v.size() - at);
+            QS_CUDA(launch_pauli_group(s->data, s->n, s->dt, kv.first, v.data() + at, cnt, s->scratch,
+                                       res, s->stream));
+        }
+    }
+    QS_CUDA(cudaMemcpyAsync(s->host_pinned, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    *out = s->host_pinned[0];
+    return QS_OK;
+}
+
+qs_status qs_apply_pauli_sum(const qs_state* psi, const qs_pauli_sum* h, qs_state* out) {
+    qs_status st = check_state(psi);
+    if (st != QS_OK) return st;
+    st = check_state(out);
+    if (st != QS_OK) return st;
+    if (!h) return fail(QS_ERR_ARG, "null Hamiltonian");
+    if (h->n != psi->n || out->n != psi->n || out->dt != psi->dt)
+        return fail(QS_ERR_ARG, "shapes differ");
+    if (out->data == psi->data) return fail(QS_ERR_ARG, "output must not alias the input");
+    QS_CUDA(launch_apply_pauli_sum(psi->data, out->data, psi->n, psi->dt, *h, out->stream));
+    return QS_OK;
+}
+
+// -------------------------------------------------------------- gradients
+
+qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params, const qs_pauli_sum* h,
+                              qs_state* psi, qs_state* lam, double* energy, double* grad) {
+    if (!c || !h || !psi || !lam || !energy || (num_params > 0 && !grad))
+        return fail(QS_ERR_ARG, "null argument");
+    qs_status st = check_state(psi);
+    if (st != QS_OK) return st;
+    st = check_state(lam);
+    if (st != QS_OK) return st;
+    if (psi->n != c->n || lam->n != c->n || h->n != c->n || psi->dt != lam->dt)
+        return fail(QS_ERR_ARG, "circuit, states and Hamiltonian disagree on n or dtype");
+    if (psi->data == lam->data) return fail(QS_ERR_ARG, "psi and lambda must be distinct");
+    if (num_params != c->num_params)
+        return fail(QS_ERR_ARG, "circuit has %d parameters, %d given", c->num_params, num_params);
+    for (const GateRec& g : c->gates)
+        if (g.param >= 0)
+            for (const GateRec& g2 : c->gates)
+                if (&g2 != &g && g2.param == g.param)
+                    return fail(QS_ERR_UNSUPPORTED, "parameter %d is shared by several gates", g.param);
+    if (num_params) {
+        st = qs_circuit_set_params(c, theta, num_params);
+        if (st != QS_OK) return st;
+    }
+    cudaStream_t sm = psi->stream;
+    if (lam->stream != sm) return fail(QS_ERR_ARG, "psi and lambda must share a stream");
+    // forward: psi = U |0>
+    QS_CUDA(launch_init_basis(psi->data, psi->n, psi->dt, 0, sm));
+    {
+        qs_options opt;
+        qs_options_default(&opt);
+        qs_plan* p = nullptr;
+        st = qs_plan_create(c, psi->dt, &opt, &p);
+        if (st != QS_OK) return st;
+        st = qs_plan_execute(psi, p);
+        cudaError_t e = cudaStreamSynchronize(sm);
+        qs_plan_destroy(p);
+        if (st != QS_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "forward pass");
+    }
+    // lambda = H psi; E = <psi|lambda>
+    QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
+    double* res = result_area(psi);
+    QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
+    // reverse sweep with per-parameter partial sums
+    const int nb = reduce_blocks();
+    double* partials = nullptr;
+    double* sums = nullptr;
+    const int rows = std::max(num_params, 1);
+    QS_CUDA(cudaMallocAsync(&partials, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    QS_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2 * rows, sm));
+    QS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    std::vector<double> udag, pm;
+    for (int l = (int)c->gates.size() - 1; l >= 0; --l) {
+        const GateRec& g = c->gates[l];
+        const int d = 1 << g.k;
+        udag.assign(2 * d * d, 0.0);
+        for (int r = 0; r < d; ++r)
+            for (int col = 0; col < d; ++col) {
+                udag[2 * (r * d + col)] = g.m[2 * (col * d + r)];
+                udag[2 * (r * d + col) + 1] = -g.m[2 * (col * d + r) + 1];
+            }
+        const double* pauli = nullptr;
+        if (g.param >= 0) {
+            pm.assign(2 * d * d, 0.0);
+            pauli_matrix(g.k, g.paulis, pm.data());
+            pauli = pm.data();
+        }
+        cudaError_t e = launch_adjoint_gate(psi->data, lam->data, psi->n, psi->dt, g.k, g.qubits, udag.data(),
+                                            pauli, partials, g.param, sm);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(partials, sm);
+            cudaFreeAsync(sums, sm);
+            return cuda_fail(e, "adjoint gate");
+        }
+    }
+    QS_CUDA(launch_sum_partials(partials, rows, nb, sums, sm));
+    std::vector<double> host(2 * rows + 2);
+    QS_CUDA(cudaMemcpyAsync(host.data(), sums, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, sm));
+    QS_CUDA(cudaMemcpyAsync(host.data() + 2 * rows, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, sm));
+    QS_CUDA(cudaStreamSynchronize(sm));
+    cudaFreeAsync(partials, sm);
+    cudaFreeAsync(sums, sm);
+    *energy = host[2 * rows];
+    for (int p = 0; p < num_params; ++p) grad[p] = host[2 * p + 1];  // Im <lambda|P|psi>
+    return QS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,179 @@
+// Internal declarations of the GB300 state-vector library (not part of the
+// C ABI).  Host objects, plan passes and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qsgb.h"
+
+namespace qsgb {
+
+constexpr int kMaxQubits = 36;
+constexpr int kMaxK = 6;            // largest gate / fused block
+constexpr int kMaxTileGates = 96;   // gates per shared-memory tile pass
+
+// ----------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+qs_status fail(qs_status st, const char* fmt, ...);
+qs_status cuda_fail(cudaError_t e, const char* what);
+#define QS_CUDA(call)                                                          \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) return ::qsgb::cuda_fail(_e, #call);            \
+    } while (0)
+
+// ----------------------------------------------------------------- gates
+struct GateRec {
+    int k = 0;
+    int qubits[kMaxK] = {0};
+    std::vector<double> m;          // 2 * 4^k doubles, interleaved, Kronecker order
+    int kind = QS_GATE_DENSE;
+    int param = -1;                 // >= 0: exp(-i theta P / 2)
+    char paulis[kMaxK + 1] = {0};   // generator P (one letter per qubit)
+};
+
+// Exact structural class of a 2^k x 2^k FP64 matrix.
+int classify_matrix(int k, const double* m);
+// m = exp(-i theta P / 2) for the Pauli string (Kronecker order).
+void rotation_matrix(int k, const char* paulis, double theta, double* m);
+// The Pauli string's 2^k x 2^k matrix.
+void pauli_matrix(int k, const char* paulis, double* m);
+
+}  // namespace qsgb
+
+struct qs_circuit {
+    int n = 0;
+    int num_params = 0;
+    std::vector<qsgb::GateRec> gates;
+};
+
+struct qs_pauli_sum {
+    int n = 0;
+    struct Term {
+        double coeff;
+        uint64_t xmask;   // X or Y positions (bit flips)
+        uint64_t zmask;   // Z or Y positions (sign from the input bit)
+        int ny;           // number of Y factors (phase i^ny)
+    };
+    std::vector<Term> terms;
+};
+
+struct qs_state {
+    int n = 0;
+    qs_dtype dt = QS_C64;
+    void* data = nullptr;
+    bool owned = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    // device scratch for reductions (partials), allocated at create/wrap
+    double* scratch = nullptr;
+    size_t scratch_doubles = 0;
+    double* host_pinned = nullptr;  // small pinned buffer for results
+    uint64_t size() const { return 1ull << n; }
+    size_t amp_bytes() const { return dt == QS_C64 ? 8 : 16; }
+};
+
+namespace qsgb {
+
+// ----------------------------------------------------------------- passes
+enum PassKind {
+    PASS_TILE = 0,       // several gates on a shared-memory tile
+    PASS_DENSE = 1,      // one dense gate, k <= 4, strided register kernel
+    PASS_DIAG = 2,       // one diagonal gate (phase table), streaming
+    PASS_MONO = 3,       // one permutation-with-phase gate
+    PASS_GEMM = 4,       // one dense k in {5,6} gate on tensor cores
+    PASS_DENSE_SMEM = 5  // one dense gate via a shared-memory block GEMM (SIMT)
+};
+
+struct TileGate {
+    uint8_t k;
+    uint8_t kind;         // QS_GATE_*
+    uint8_t q[kMaxK];     // tile-local bit positions (Kronecker order)
+    uint32_t mat;         // element offset of the matrix in the pass buffer
+};
+
+struct Pass {
+    int kind = PASS_DENSE;
+    // single-gate passes
+    int k = 0;
+    int qubits[kMaxK] = {0};
+    int gate_kind = QS_GATE_DENSE;
+    // tile passes: local bit i -> global bit pos[i]; pos[0..L-1]
+    int L = 0;
+    int pos[16] = {0};
+    std::vector<TileGate> tgates;
+    // matrices (FP64 host copies; converted on upload)
+    std::vector<double> mats;       // concatenated interleaved matrices
+    size_t dev_offset = 0;          // element offset in the plan's device buffer
+};
+
+}  // namespace qsgb
+
+struct qs_plan {
+    int n = 0;
+    qs_dtype dt = QS_C64;
+    qs_options opt{};
+    std::vector<qsgb::Pass> passes;
+    void* dev_mats = nullptr;       // float2 or double2 matrices of all passes
+    size_t dev_elems = 0;
+    int device = 0;
+};
+
+namespace qsgb {
+
+// ----------------------------------------------------------------- planner
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
+qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
+                       const qs_options& opt, std::vector<Pass>& passes);
+int auto_tile_qubits(int n, qs_dtype dt);
+
+// ----------------------------------------------------------------- launchers
+// All launchers enqueue on `st` and return the launch error (cudaSuccess).
+// `dmats` points at the pass's matrices already converted to the state's
+// precision (complex float or double, interleaved).
+cudaError_t launch_dense(void* psi, int n, qs_dtype dt, int k, const int* qubits,
+                         const double* m_host, cudaStream_t st);
+cudaError_t launch_diag(void* psi, int n, qs_dtype dt, int k, const int* qubits,
+                        const double* m_host, cudaStream_t st);
+cudaError_t launch_mono(void* psi, int n, qs_dtype dt, int k, const int* qubits,
+                        const double* m_host, cudaStream_t st);
+cudaError_t launch_dense_smem(void* psi, int n, qs_dtype dt, int k, const int* qubits,
+                              const void* dmat, cudaStream_t st);
+cudaError_t launch_tile(void* psi, int n, qs_dtype dt, const Pass& p, const void* dmats,
+                        cudaStream_t st);
+cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat_f32,
+                        int precision, cudaStream_t st);
+
+cudaError_t launch_init_basis(void* psi, int n, qs_dtype dt, uint64_t index, cudaStream_t st);
+cudaError_t launch_init_uniform(void* psi, int n, qs_dtype dt, cudaStream_t st);
+
+// Reductions write `nparts` FP64 partial sums to scratch, then one block
+// sums them in a fixed order into result[0..count).
+int reduce_blocks();
+cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* scratch, double* result,
+                        cudaStream_t st);
+// Expectation of the terms sharing one flip mask; adds into result[0].
+cudaError_t launch_pauli_group(const void* psi, int n, qs_dtype dt, uint64_t xmask,
+                               const qs_pauli_sum::Term* terms, int nterms, double* scratch,
+                               double* result, cudaStream_t st);
+cudaError_t launch_apply_pauli_sum(const void* psi, void* out, int n, qs_dtype dt,
+                                   const qs_pauli_sum& h, cudaStream_t st);
+// <a|b> partial sums (complex, FP64) into result[0..1].
+cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, double* scratch,
+                         double* result, cudaStream_t st);
+
+// Adjoint step: g += <lam| P |psi> over the gate's sets (complex partials
+// into scratch row `slot`), then psi <- U^dag psi, lam <- U^dag lam.
+cudaError_t launch_adjoint_gate(void* psi, void* lam, int n, qs_dtype dt, int k,
+                                const int* qubits, const double* udag, const double* pauli,
+                                double* partials, int slot, cudaStream_t st);
+cudaError_t launch_sum_partials(const double* partials, int rows, int cols, double* out,
+                                cudaStream_t st);
+
+int num_sms();
+
+}  // namespace qsgb

@@ -1,0 +1,298 @@
+// Host-side planning: gate classification, rotation matrices, gate fusion
+// with commuting reorder, and grouping of fused blocks into passes.
+//
+// Fusion and pass formation are the same scan (Section 4.5, "Gate clustering
+// by reordering"): start at the first unplaced gate and walk forward; a later
+// gate joins the current group when it commutes with every gate skipped so
+// far -- disjoint qubits, or both diagonal (Sections 4.2 and 4.3) -- and the
+// group's qubit set stays within its bound.  A skipped gate marks its qubits
+// obstructed.  The paper's "same kind" test is replaced by "fits in the
+// group's qubit bound": k_max qubits for a fused matrix (whose FP64 product
+// replaces the group, as in Eq. 2's coalescing), or the tile's qubit count
+// for a shared-memory pass that applies the group's blocks one after another.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+
+#include "qs_internal.h"
+
+namespace qsgb {
+
+using cd = std::complex<double>;
+
+int classify_matrix(int k, const double* m) {
+    const int d = 1 << k;
+    bool diag = true, mono = true;
+    for (int r = 0; r < d; ++r) {
+        int nz = 0;
+        for (int c = 0; c < d; ++c) {
+            const double re = m[2 * (r * d + c)], im = m[2 * (r * d + c) + 1];
+            if (re != 0.0 || im != 0.0) {
+                ++nz;
+                if (r != c) diag = false;
+            }
+        }
+        if (nz != 1) mono = false;
+    }
+    if (mono) {  // columns must also hold exactly one nonzero
+        for (int c = 0; c < d && mono; ++c) {
+            int nz = 0;
+            for (int r = 0; r < d; ++r)
+                if (m[2 * (r * d + c)] != 0.0 || m[2 * (r * d + c) + 1] != 0.0) ++nz;
+            if (nz != 1) mono = false;
+        }
+    }
+    if (diag && mono) return QS_GATE_DIAGONAL;
+    if (mono) return QS_GATE_MONOMIAL;
+    return QS_GATE_DENSE;
+}
+
+static void pauli_1q(char c, cd p[2][2]) {
+    p[0][0] = p[0][1] = p[1][0] = p[1][1] = 0.0;
+    switch (c) {
+        case 'X': p[0][1] = 1.0; p[1][0] = 1.0; break;
+        case 'Y': p[0][1] = cd(0, -1); p[1][0] = cd(0, 1); break;
+        case 'Z': p[0][0] = 1.0; p[1][1] = -1.0; break;
+        default: p[0][0] = 1.0; p[1][1] = 1.0; break;
+    }
+}
+
+void pauli_matrix(int k, const char* paulis, double* m) {
+    const int d = 1 << k;
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            cd v = 1.0;
+            for (int i = 0; i < k; ++i) {  // paulis[0] is the most significant local bit
+                cd p[2][2];
+                pauli_1q(paulis[i], p);
+                const int br = (r >> (k - 1 - i)) & 1, bc = (c >> (k - 1 - i)) & 1;
+                v *= p[br][bc];
+            }
+            m[2 * (r * d + c)] = v.real();
+            m[2 * (r * d + c) + 1] = v.imag();
+        }
+}
+
+void rotation_matrix(int k, const char* paulis, double theta, double* m) {
+    // exp(-i theta P / 2) = cos(theta/2) I - i sin(theta/2) P, since P^2 = I
+    const int d = 1 << k;
+    pauli_matrix(k, paulis, m);
+    const double c = cos(0.5 * theta), s = sin(0.5 * theta);
+    for (int r = 0; r < d; ++r)
+        for (int col = 0; col < d; ++col) {
+            const double pr = m[2 * (r * d + col)], pi = m[2 * (r * d + col) + 1];
+            // -i s (pr + i pi) = s pi - i s pr
+            double re = s * pi, im = -s * pr;
+            if (r == col) re += c;
+            m[2 * (r * d + col)] = re;
+            m[2 * (r * d + col) + 1] = im;
+        }
+}
+
+static inline uint64_t qmask(const GateRec& g) {
+    uint64_t m = 0;
+    for (int i = 0; i < g.k; ++i) m |= 1ull << g.qubits[i];
+    return m;
+}
+
+// Multiply gate g (on its qubits) into the block matrix `acc` whose local
+// bit b corresponds to qubit bq[K-1-b] (bq listed most significant first):
+// acc <- E(g) acc, column by column.
+static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector<cd>& acc) {
+    const int D = 1 << K, d = 1 << g.k;
+    int lpos[kMaxK];  // local bit of each gate qubit
+    for (int i = 0; i < g.k; ++i) {
+        lpos[i] = -1;
+        for (int j = 0; j < K; ++j)
+            if (bq[j] == g.qubits[i]) lpos[i] = K - 1 - j;
+    }
+    uint64_t gmask = 0;
+    for (int i = 0; i < g.k; ++i) gmask |= 1ull << lpos[i];
+    std::vector<cd> col(D), out(D);
+    for (int c = 0; c < D; ++c) {
+        for (int r = 0; r < D; ++r) col[r] = acc[r * D + c];
+        for (int r = 0; r < D; ++r) {
+            if (r & gmask) continue;  // r = set base (gate bits zero)
+            cd a[1 << kMaxK];
+            for (int l = 0; l < d; ++l) {
+                int idx = r;
+                for (int i = 0; i < g.k; ++i)
+                    if ((l >> (g.k - 1 - i)) & 1) idx |= 1 << lpos[i];
+                a[l] = col[idx];
+            }
+            for (int lo = 0; lo < d; ++lo) {
+                cd s = 0.0;
+                for (int li = 0; li < d; ++li)
+                    s += cd(g.m[2 * (lo * d + li)], g.m[2 * (lo * d + li) + 1]) * a[li];
+                int idx = r;
+                for (int i = 0; i < g.k; ++i)
+                    if ((lo >> (g.k - 1 - i)) & 1) idx |= 1 << lpos[i];
+                out[idx] = s;
+            }
+        }
+        for (int r = 0; r < D; ++r) acc[r * D + c] = out[r];
+    }
+}
+
+// One greedy scan from the first unplaced gate; returns the indices taken.
+// `bound` limits popcount(init_mask | taken qubits); `max_dense_k` bounds
+// the size of non-diagonal members (diagonal ones may use up to kMaxK).
+static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<char>& placed,
+                                   int start, uint64_t init_mask, int bound, int window,
+                                   int max_dense_k = kMaxK) {
+    std::vector<int> taken;
+    uint64_t support = init_mask | qmask(g[start]);
+    taken.push_back(start);
+    placed[start] = 1;
+    uint64_t blocked_any = 0, blocked_diag = 0;
+    int scanned = 0;
+    for (int j = start + 1; j < (int)g.size() && scanned < window; ++j) {
+        if (placed[j]) continue;
+        ++scanned;
+        const uint64_t gm = qmask(g[j]);
+        const bool gdiag = g[j].kind == QS_GATE_DIAGONAL;
+        const bool commutes = (gm & blocked_any) == 0 && (gdiag || (gm & blocked_diag) == 0);
+        const bool fits = __builtin_popcountll(support | gm) <= bound &&
+                          (gdiag || g[j].k <= max_dense_k);
+        if (commutes && fits) {
+            taken.push_back(j);
+            placed[j] = 1;
+            support |= gm;
+        } else if (gdiag) {
+            blocked_diag |= gm;
+        } else {
+            blocked_any |= gm;
+        }
+        // nothing more can join: the support is full and fully obstructed
+        if (__builtin_popcountll(support) >= bound && (support & ~blocked_any) == 0) break;
+    }
+    return taken;
+}
+
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out) {
+    if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
+    out.clear();
+    std::vector<char> placed(in.size(), 0);
+    for (int start = 0; start < (int)in.size(); ++start) {
+        if (placed[start]) continue;
+        if (in[start].k > k_max) {  // wider than the bound: kept as it is
+            placed[start] = 1;
+            GateRec b = in[start];
+            b.param = -1;
+            b.paulis[0] = 0;
+            out.push_back(b);
+            continue;
+        }
+        std::vector<int> taken = scan_group(in, placed, start, 0, k_max, 1 << 14);
+        uint64_t support = 0;
+        for (int t : taken) support |= qmask(in[t]);
+        GateRec b;
+        b.k = __builtin_popcountll(support);
+        int bq[kMaxK];
+        int j = 0;
+        for (int q = n - 1; q >= 0; --q)
+            if ((support >> q) & 1) bq[j++] = q;  // descending: qubits[0] most significant
+        for (int i = 0; i < b.k; ++i) b.qubits[i] = bq[i];
+        const int D = 1 << b.k;
+        std::vector<cd> acc(D * D, 0.0);
+        for (int i = 0; i < D; ++i) acc[i * D + i] = 1.0;
+        for (int t : taken) apply_into_block(in[t], b.k, bq, acc);
+        b.m.resize(2 * D * D);
+        for (int i = 0; i < D * D; ++i) {
+            b.m[2 * i] = acc[i].real();
+            b.m[2 * i + 1] = acc[i].imag();
+        }
+        b.kind = classify_matrix(b.k, b.m.data());
+        out.push_back(std::move(b));
+    }
+    (void)n;
+    return QS_OK;
+}
+
+int auto_tile_qubits(int n, qs_dtype dt) {
+    const int L = dt == QS_C64 ? 12 : 11;
+    return std::min(L, n);
+}
+
+static int low_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
+
+// largest non-diagonal gate the tile kernel applies (register path), and
+// the complex matrix entries one tile pass may stage in shared memory
+constexpr int kTileDenseK = 4;
+constexpr size_t kTileMatElems = 3072;
+
+qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
+                       const qs_options& opt, std::vector<Pass>& passes) {
+    passes.clear();
+    const int L = opt.tile_qubits > 0 ? std::min(opt.tile_qubits, n) : auto_tile_qubits(n, dt);
+    const int b = std::min(low_bits(dt), L);
+    const uint64_t lowmask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
+    std::vector<char> placed(blocks.size(), 0);
+    for (int start = 0; start < (int)blocks.size(); ++start) {
+        if (placed[start]) continue;
+        std::vector<int> taken;
+        const bool start_ok = blocks[start].kind == QS_GATE_DIAGONAL || blocks[start].k <= kTileDenseK;
+        if (opt.use_tile && start_ok && blocks[start].k <= L && (int)blocks.size() > 1) {
+            std::vector<char> trial = placed;
+            taken = scan_group(blocks, trial, start, lowmask, L, 1 << 14, kTileDenseK);
+            // keep a prefix within the gate-count and shared-matrix budgets
+            // (members are in circuit order, so any prefix is a valid group)
+            size_t elems = 0, keep = 0;
+            for (; keep < taken.size() && (int)keep < kMaxTileGates; ++keep) {
+                const size_t d = 1u << blocks[taken[keep]].k;
+                if (elems + d * d > kTileMatElems) break;
+                elems += d * d;
+            }
+            taken.resize(std::max<size_t>(keep, 1));
+            for (int t : taken) placed[t] = 1;
+        } else {
+            taken.push_back(start);
+            placed[start] = 1;
+        }
+        Pass p;
+        if (taken.size() == 1) {
+            const GateRec& g = blocks[taken[0]];
+            p.k = g.k;
+            for (int i = 0; i < g.k; ++i) p.qubits[i] = g.qubits[i];
+            p.gate_kind = g.kind;
+            p.mats = g.m;
+            if (g.kind == QS_GATE_DIAGONAL) p.kind = PASS_DIAG;
+            else if (g.kind == QS_GATE_MONOMIAL) p.kind = PASS_MONO;
+            else if (g.k <= 4) p.kind = PASS_DENSE;
+            else if (dt == QS_C64 && opt.precision != QS_PREC_FP32) p.kind = PASS_GEMM;
+            else p.kind = PASS_DENSE_SMEM;
+        } else {
+            p.kind = PASS_TILE;
+            uint64_t S = lowmask;
+            for (int t : taken)
+                for (int i = 0; i < blocks[t].k; ++i) S |= 1ull << blocks[t].qubits[i];
+            // fill the tile up to L qubits with the lowest unused bits so
+            // the rows stay long (coalesced) -- extra bits cost nothing
+            for (int q = 0; q < n && __builtin_popcountll(S) < L; ++q) S |= 1ull << q;
+            int local_of[kMaxQubits];
+            int j = 0;
+            for (int q = 0; q < n; ++q)
+                if ((S >> q) & 1) {
+                    local_of[q] = j;
+                    p.pos[j++] = q;
+                }
+            p.L = j;
+            for (int t : taken) {
+                const GateRec& g = blocks[t];
+                TileGate tg{};
+                tg.k = (uint8_t)g.k;
+                tg.kind = (uint8_t)g.kind;
+                for (int i = 0; i < g.k; ++i) tg.q[i] = (uint8_t)local_of[g.qubits[i]];
+                tg.mat = (uint32_t)(p.mats.size() / 2);
+                p.mats.insert(p.mats.end(), g.m.begin(), g.m.end());
+                p.tgates.push_back(tg);
+            }
+        }
+        passes.push_back(std::move(p));
+    }
+    return QS_OK;
+}
+
+}  // namespace qsgb

@@ -1,0 +1,123 @@
+"""The C ABI on the CPU: the library loads, exports every entry point the
+header declares, rejects bad arguments with status codes, and its host-side
+fusion (Sections 4.2 and 4.5) produces blocks whose product equals the
+original circuit (checked with the FP64 oracle).  No device is needed."""
+
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_2008_00216_gb300 as qs
+from paper_2008_00216_gb300 import binding as B
+from workloads import circuits as C
+from workloads import gates as G
+from workloads.rng import random_state
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "qsgb.h")
+
+
+def declared_symbols():
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_]+\*?\s+\*?(qs_[a-z0-9_]+)\s*\(", text, re.M)))
+
+
+def test_header_declares_what_the_binding_uses():
+    decl = declared_symbols()
+    assert len(decl) >= 30
+    assert set(B.exported_symbols()) <= set(decl)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = qs.load()
+    missing = [s for s in declared_symbols() if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    lib = qs.load()
+    assert b"sm_103a" in lib.qs_version()
+    for s in range(7):
+        assert lib.qs_status_string(s)
+
+
+@pytest.mark.parametrize("qubits,k", [([0, 0], 2), ([12], 1), ([-1], 1), ([0, 1, 2, 3, 4, 5, 6], 7)])
+def test_circuit_add_rejects_bad_gates(qubits, k):
+    c = B.Circuit(12)
+    m = np.eye(1 << min(k, 6), dtype=complex)
+    with pytest.raises(B.QsError) as e:
+        B._call("qs_circuit_add", c.handle, B._ints(qubits), k, B._mat(m))
+    assert e.value.status == 1
+
+
+def test_fuse_rejects_bad_kmax():
+    c = B.circuit_from(C.small_grid_circuit())
+    for k in (0, 7):
+        with pytest.raises(B.QsError):
+            B.fuse(c, k)
+
+
+def test_rotation_matrix_roundtrip():
+    circ = C.ansatz_circuit(3, 1, C.ansatz_theta(3, 1, seed=2))
+    c = B.circuit_from(circ)
+    for i, g in enumerate(circ.gates):
+        qs_, m, kind = c.gate(i)
+        assert qs_ == g.qubits
+        assert np.max(np.abs(m - g.matrix)) < 1e-15
+
+
+def test_gate_classification():
+    c = B.Circuit(4, [((0, 1), G.CZ), ((2,), G.SQRT_X), ((1, 3), G.fsim(np.pi / 2, 0.3)), ((0,), G.T)])
+    kinds = [c.gate(i)[2] for i in range(4)]
+    assert kinds == ["diagonal", "dense", "monomial", "diagonal"]
+
+
+def _oracle_of(circ_obj):
+    return [(q, m) for q, m, _ in circ_obj.gates()]
+
+
+@pytest.mark.parametrize("k_max", [1, 2, 3, 4, 5, 6])
+def test_fusion_preserves_the_circuit(k_max):
+    circ = C.grid_circuit(10, 6, seed=3)
+    c = B.circuit_from(circ)
+    f = B.fuse(c, k_max)
+    blocks = f.gates()
+    assert all(len(q) <= max(k_max, 2) for q, _, _ in blocks)  # wider gates pass through
+    if k_max > 1:
+        assert len(blocks) < len(circ.gates)
+    psi0 = random_state(10, 1)
+    ref = oracle.simulate(10, circ.gates, psi0)
+    got = oracle.simulate(10, _oracle_of(f), psi0)
+    assert oracle.metrics.rel_l2(got, ref) < 1e-13
+
+
+def test_fusion_reorders_commuting_diagonals():
+    # CZ(0,1), H(2), CZ(1,2) cannot merge directly, but CZ(0,1) and a later
+    # CZ(0,3) commute with the skipped diagonal, so they join one block
+    gates = [((0, 1), G.CZ), ((1, 2), G.CZ), ((2,), G.H), ((0, 3), G.CZ), ((3, 4), G.CZ)]
+    c = B.Circuit(5, gates)
+    f = B.fuse(c, 3)
+    blocks = f.gates()
+    psi0 = random_state(5, 2)
+    assert oracle.metrics.rel_l2(oracle.simulate(5, _oracle_of(f), psi0), oracle.simulate(5, gates, psi0)) < 1e-14
+    assert len(blocks) <= 3
+
+
+def test_fusion_random_circuits_all_kinds():
+    for seed in range(4):
+        circ = C.random_circuit(8, 50, seed, max_k=3)
+        c = B.circuit_from(circ)
+        for k_max in (3, 4, 6):
+            f = B.fuse(c, k_max)
+            psi0 = random_state(8, seed)
+            assert oracle.metrics.rel_l2(oracle.simulate(8, _oracle_of(f), psi0),
+                                         oracle.simulate(8, circ.gates, psi0)) < 1e-13
+
+
+def test_fused_block_kinds_are_exact():
+    # a block of only diagonal gates must come out diagonal
+    gates = [((0, 1), G.CZ), ((1,), G.T), ((0,), G.S), ((1, 2), G.cphase(0.3))]
+    f = B.fuse(B.Circuit(3, gates), 3)
+    assert [k for _, _, k in f.gates()] == ["diagonal"]

@@ -48,12 +48,23 @@ SQRT_W = 0.5 * np.array([[1 + 1j, -1j * np.sqrt(2.0)], [np.sqrt(2.0), 1 + 1j]],
 ONE_QUBIT_SET = {"sqrt_x": SQRT_X, "sqrt_y": SQRT_Y, "sqrt_w": SQRT_W}
 
 
+def _snap(x: float) -> float:
+    """cos/sin values within a few ulp of 0 or +-1 are those exact values
+    (cos(pi/2) evaluates to 6e-17); exact zeros keep fSim(pi/2, phi) a
+    permutation-with-phase matrix."""
+    for v in (0.0, 1.0, -1.0):
+        if abs(x - v) < 4e-16:
+            return v
+    return float(x)
+
+
 def fsim(theta: float, phi: float) -> np.ndarray:
-    c, s = np.cos(theta), np.sin(theta)
+    c, s = _snap(np.cos(theta)), _snap(np.sin(theta))
     return np.array([[1, 0, 0, 0],
                      [0, c, -1j * s, 0],
                      [0, -1j * s, c, 0],
-                     [0, 0, 0, np.exp(-1j * phi)]], dtype=np.complex128)
+                     [0, 0, 0, complex(_snap(np.cos(phi)), -_snap(np.sin(phi)))]],
+                    dtype=np.complex128)
 
 
 def cphase(phi: float) -> np.ndarray:
