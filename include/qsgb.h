@@ -206,6 +206,29 @@ qs_status qs_amplitudes(const qs_state* s, uint64_t first, uint64_t count, doubl
  * and FP64 cross-block sums (Section 4.1).  Synchronises the stream. */
 qs_status qs_norm(const qs_state* s, double* out);
 
+/* Allocation-free norm: sum_j |alpha_j|^2 of 2^n amplitudes at a raw device
+ * pointer, for callers that cannot allocate device memory -- a process whose
+ * GPU memory another allocator has reserved up front, an application with a
+ * device-memory budget fixed at start-up, or code that must keep off the
+ * driver's allocation path because cudaMalloc/cudaFree can synchronise the
+ * device.  qs_norm needs a qs_state, whose creation allocates scratch; this
+ * call allocates nothing.  The paper has no counterpart: it is an interface
+ * addition, computing what qs_norm computes with the same kernels.
+ *   device_amplitudes: 16-byte aligned, 2^n complex64/complex128 (dt).
+ *   stream: cudaStream_t to run on; the call synchronises it.
+ *   out: host double receiving the sum.
+ * Scratch: a fixed device array of 4096 partial sums (plus a result slot,
+ * about 32 KB) inside the library, held by every GPU that loads it until the
+ * process exits.  A GPU that needs more partial sums than that (more than
+ * 1024 SMs) gets QS_ERR_UNSUPPORTED.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the one
+ * array and it keeps the last call's contents (each call overwrites every
+ * entry it reads, so nothing needs clearing): calls whose work overlaps on
+ * the GPU -- on different streams, or from several host threads -- race and
+ * must be serialised by the caller. */
+qs_status qs_norm_noalloc(const void* device_amplitudes, int n, qs_dtype dt, void* stream, double* out);
+
 /* ------------------------------------------------------------ observables */
 
 qs_status qs_pauli_sum_create(int n, qs_pauli_sum** out);

@@ -70,6 +70,7 @@ _SIGS = {
     "qs_apply_circuit": (ct.c_int, [_P, _P, ct.c_int]),
     "qs_amplitudes": (ct.c_int, [_P, ct.c_uint64, ct.c_uint64, ct.POINTER(ct.c_double)]),
     "qs_norm": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
+    "qs_norm_noalloc": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, ct.POINTER(ct.c_double)]),
     "qs_pauli_sum_create": (ct.c_int, [ct.c_int, ct.POINTER(_P)]),
     "qs_pauli_sum_destroy": (ct.c_int, [_P]),
     "qs_pauli_sum_add": (ct.c_int, [_P, ct.c_double, ct.POINTER(ct.c_int), ct.c_char_p, ct.c_int]),
@@ -212,6 +213,15 @@ class State:
             self.close()
         except Exception:
             pass
+
+
+def norm_noalloc(tensor, n: int, dtype="c64", stream=None) -> float:
+    """sum |alpha|^2 of a raw CUDA tensor through qs_norm_noalloc, which
+    allocates no device memory (for callers that cannot allocate)."""
+    v = ct.c_double()
+    _call("qs_norm_noalloc", ct.c_void_p(tensor.data_ptr()), int(n), QS_C64 if dtype == "c64" else QS_C128,
+          ct.c_void_p(_stream_ptr(stream)), ct.byref(v))
+    return v.value
 
 
 def apply_gate(state: State, qubits: Sequence[int], matrix):

@@ -1,0 +1,35 @@
+"""qs_norm_noalloc, the norm for callers that cannot allocate device memory
+(their GPU memory is reserved up front by another allocator, their budget
+is fixed at start-up, or they must stay off the driver's allocation path).
+It keeps its scratch in a fixed array inside the library; this test checks
+it against qs_norm on two calls in a row, so stale contents of the shared
+array from the first call cannot leak into the second.  The file is named to
+be collected last."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2008_00216_gb300 import binding as B
+from workloads.rng import random_state
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_norm_noalloc_matches_norm_twice(qs, dtype):
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    for n, seed, scale in ((14, 1, 1.0), (9, 2, 0.37)):   # second call: other size and values
+        t = torch.from_numpy(random_state(n, seed) * scale).to(tdt).cuda()
+        ref = B.State(n, dtype, tensor=t, init=None).norm()
+        got = B.norm_noalloc(t, n, dtype)
+        assert abs(got - ref) <= 1e-13 * ref, (n, got, ref)
+        assert abs(got - scale * scale) < (1e-6 if dtype == "c64" else 1e-13)
+
+
+def test_norm_noalloc_rejects_bad_arguments(qs):
+    t = torch.zeros(16, dtype=torch.complex64, device="cuda")
+    with pytest.raises(B.QsError):
+        B.norm_noalloc(t, 0, "c64")
+    with pytest.raises(B.QsError):
+        B.norm_noalloc(t[1:], 3, "c64")   # 8-byte offset: not 16-byte aligned
