@@ -124,6 +124,11 @@ qs_status qs_state_init_basis(qs_state* s, uint64_t index);
  * that the initial Hadamard layer can be replaced by this initialisation. */
 qs_status qs_state_init_uniform(qs_state* s);
 
+/* Wait for the state's stream; QS_ERR_TIMEOUT if a bounded device-side wait
+ * (tensor-core pipeline) gave up since the last check (the flag is then
+ * cleared).  qs_norm and qs_amplitudes perform the same check. */
+qs_status qs_state_sync(qs_state* s);
+
 /* Device-to-device copy of all amplitudes; n and dtype must match. */
 qs_status qs_state_copy(qs_state* dst, const qs_state* src);
 

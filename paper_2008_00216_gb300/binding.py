@@ -50,6 +50,7 @@ _SIGS = {
     "qs_state_init_basis": (ct.c_int, [_P, ct.c_uint64]),
     "qs_state_init_uniform": (ct.c_int, [_P]),
     "qs_state_copy": (ct.c_int, [_P, _P]),
+    "qs_state_sync": (ct.c_int, [_P]),
     "qs_apply_gate": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.c_int, ct.POINTER(ct.c_double)]),
     "qs_circuit_create": (ct.c_int, [ct.c_int, ct.POINTER(_P)]),
     "qs_circuit_destroy": (ct.c_int, [_P]),
@@ -184,6 +185,11 @@ class State:
     def init_uniform(self):
         self.sync_stream()
         _call("qs_state_init_uniform", self.handle)
+
+    def sync(self):
+        """Wait for the stream; raises QsError (status 5) if a device wait timed out."""
+        self.sync_stream()
+        _call("qs_state_sync", self.handle)
 
     def copy_from(self, other: "State"):
         self.sync_stream()

@@ -87,11 +87,25 @@ static qs_status state_setup(qs_state* s) {
     s->scratch_doubles = (size_t)reduce_blocks() * 2 + 64;
     QS_CUDA(cudaMalloc(&s->scratch, s->scratch_doubles * sizeof(double)));
     QS_CUDA(cudaMallocHost(&s->host_pinned, 64 * sizeof(double)));
+    s->errflag = reinterpret_cast<int*>(s->scratch + s->scratch_doubles - 1);
+    QS_CUDA(cudaMemset(s->errflag, 0, sizeof(int)));
     return QS_OK;
 }
 
 static double* result_area(const qs_state* s) {
     return s->scratch + s->scratch_doubles - 64;
+}
+
+// After a stream synchronisation: report (and clear) a device-side wait that
+// gave up since the last check.
+static qs_status check_device_flag(const qs_state* s) {
+    int flag = 0;
+    QS_CUDA(cudaMemcpy(&flag, s->errflag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        QS_CUDA(cudaMemset(s->errflag, 0, sizeof(int)));
+        return fail(QS_ERR_TIMEOUT, "a bounded device-side wait timed out; results of that pass are invalid");
+    }
+    return QS_OK;
 }
 
 }  // namespace qsgb
@@ -501,9 +515,7 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
                 e = launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
                 break;
             case PASS_GEMM:
-                e = launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, p->opt.precision, s->stream);
-                if (e == cudaErrorNotSupported)
-                    return fail(QS_ERR_UNSUPPORTED, "tensor-core pass unavailable in this build");
+                e = launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, p->opt.precision, s->errflag, s->stream);
                 break;
             case PASS_DENSE_SMEM:
                 e = launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
@@ -545,7 +557,7 @@ qs_status qs_amplitudes(const qs_state* s, uint64_t first, uint64_t count, doubl
     if (s->dt == QS_C128) {
         QS_CUDA(cudaMemcpyAsync(out, src, count * esz, cudaMemcpyDeviceToHost, s->stream));
         QS_CUDA(cudaStreamSynchronize(s->stream));
-        return QS_OK;
+        return check_device_flag(s);
     }
     // complex64: copy in chunks through a host buffer, widen to FP64
     const uint64_t chunk = 1ull << 22;
@@ -556,7 +568,7 @@ qs_status qs_amplitudes(const qs_state* s, uint64_t first, uint64_t count, doubl
         QS_CUDA(cudaStreamSynchronize(s->stream));
         for (uint64_t i = 0; i < 2 * c; ++i) out[2 * at + i] = (double)buf[i];
     }
-    return QS_OK;
+    return check_device_flag(s);
 }
 
 qs_status qs_norm(const qs_state* s, double* out) {
@@ -568,7 +580,14 @@ qs_status qs_norm(const qs_state* s, double* out) {
     QS_CUDA(cudaMemcpyAsync(s->host_pinned, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     QS_CUDA(cudaStreamSynchronize(s->stream));
     *out = s->host_pinned[0];
-    return QS_OK;
+    return check_device_flag(s);
+}
+
+qs_status qs_state_sync(qs_state* s) {
+    qs_status st = check_state(s);
+    if (st != QS_OK) return st;
+    QS_CUDA(cudaStreamSynchronize(s->stream));
+    return check_device_flag(s);
 }
 
 // ------------------------------------------------------------ observables

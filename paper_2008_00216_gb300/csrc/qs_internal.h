@@ -73,6 +73,7 @@ struct qs_state {
     double* scratch = nullptr;
     size_t scratch_doubles = 0;
     double* host_pinned = nullptr;  // small pinned buffer for results
+    int* errflag = nullptr;         // device int in scratch: set by timed-out device waits
     uint64_t size() const { return 1ull << n; }
     size_t amp_bytes() const { return dt == QS_C64 ? 8 : 16; }
 };
@@ -145,8 +146,11 @@ cudaError_t launch_dense_smem(void* psi, int n, qs_dtype dt, int k, const int* q
                               const void* dmat, cudaStream_t st);
 cudaError_t launch_tile(void* psi, int n, qs_dtype dt, const Pass& p, const void* dmats,
                         cudaStream_t st);
+// Tensor-core pass for a dense 6-qubit gate on a complex64 state (n >= 11);
+// `err` (device int) is set to 1 if a bounded device wait timed out.
+bool gemm_supported(int n, int k);
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat_f32,
-                        int precision, cudaStream_t st);
+                        int precision, int* err, cudaStream_t st);
 
 cudaError_t launch_init_basis(void* psi, int n, qs_dtype dt, uint64_t index, cudaStream_t st);
 cudaError_t launch_init_uniform(void* psi, int n, qs_dtype dt, cudaStream_t st);

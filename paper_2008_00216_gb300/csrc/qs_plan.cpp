@@ -211,6 +211,27 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
     return QS_OK;
 }
 
+// Widen a 5-qubit dense pass to 6 qubits: an identity on the lowest unused
+// qubit, placed first (most significant), so the matrix is kron(I2, M).
+static void pad_to_six(int n, Pass& p) {
+    uint64_t used = 0;
+    for (int i = 0; i < p.k; ++i) used |= 1ull << p.qubits[i];
+    int extra = 0;
+    while (extra < n && ((used >> extra) & 1)) ++extra;
+    const int d = 1 << p.k, D = 2 * d;
+    std::vector<double> m(2 * D * D, 0.0);
+    for (int b = 0; b < 2; ++b)
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c) {
+                m[2 * ((b * d + r) * D + b * d + c)] = p.mats[2 * (r * d + c)];
+                m[2 * ((b * d + r) * D + b * d + c) + 1] = p.mats[2 * (r * d + c) + 1];
+            }
+    for (int i = p.k; i > 0; --i) p.qubits[i] = p.qubits[i - 1];
+    p.qubits[0] = extra;
+    p.k += 1;
+    p.mats.swap(m);
+}
+
 int auto_tile_qubits(int n, qs_dtype dt) {
     const int L = dt == QS_C64 ? 12 : 11;
     return std::min(L, n);
@@ -261,8 +282,10 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
             if (g.kind == QS_GATE_DIAGONAL) p.kind = PASS_DIAG;
             else if (g.kind == QS_GATE_MONOMIAL) p.kind = PASS_MONO;
             else if (g.k <= 4) p.kind = PASS_DENSE;
-            else if (dt == QS_C64 && opt.precision != QS_PREC_FP32) p.kind = PASS_GEMM;
-            else p.kind = PASS_DENSE_SMEM;
+            else if (dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6)) {
+                p.kind = PASS_GEMM;
+                if (g.k == 5) pad_to_six(n, p);  // the tensor-core pass is 6-qubit only
+            } else p.kind = PASS_DENSE_SMEM;
         } else {
             p.kind = PASS_TILE;
             uint64_t S = lowmask;

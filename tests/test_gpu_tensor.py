@@ -1,0 +1,86 @@
+"""Dense 6-qubit (and padded 5-qubit) fused gates on the tcgen05 tensor
+cores, in the three split-precision modes, against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle.metrics import rel_l2
+from paper_2008_00216_gb300 import binding as B
+from workloads import circuits as C
+from workloads.rng import Xoshiro256ss, random_state, random_unitary
+
+from gpu_util import run_plan, to_state
+
+pytestmark = pytest.mark.gpu
+
+# per-gate relative L2 bounds: TF32 keeps ~11 bits; the split modes ~FP32
+GATE_TOL = {"tf32": 3e-3, "3xtf32": 2e-6, "3xbf16": 3e-5}
+PLACEMENTS = [[0, 1, 2, 3, 4, 5], [13, 12, 11, 10, 9, 8], [0, 13, 3, 7, 9, 11], [6, 2, 12, 1, 10, 5],
+              [1, 2, 3, 4, 5, 6]]
+
+
+def _one_gate_circuit(n, qubits, m):
+    circ = C.Circuit(n)
+    circ.append(qubits, m)
+    return circ
+
+
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "3xbf16"])
+def test_single_6q_gate_all_placements(qs, prec):
+    n = 14
+    rng = Xoshiro256ss(77)
+    psi0 = random_state(n, 3)
+    for qubits in PLACEMENTS:
+        m = random_unitary(6, rng)
+        ref = oracle.apply_gate(psi0, n, qubits, m)
+        got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision=prec,
+                             use_tile=False)
+        assert info["per_kind"] == {"tensor": 1}, info
+        assert rel_l2(got, ref) < GATE_TOL[prec], (qubits, rel_l2(got, ref))
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "3xbf16"])
+def test_single_5q_gate_padded(qs, prec):
+    n = 13
+    rng = Xoshiro256ss(78)
+    psi0 = random_state(n, 4)
+    for qubits in ([0, 1, 2, 3, 4], [12, 3, 7, 0, 9]):
+        m = random_unitary(5, rng)
+        ref = oracle.apply_gate(psi0, n, qubits, m)
+        got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision=prec,
+                             use_tile=False)
+        assert info["per_kind"] == {"tensor": 1}, info
+        assert rel_l2(got, ref) < GATE_TOL[prec]
+
+
+def test_tensor_matches_simt_fp32_path(qs):
+    """Same fused k_max=6 plan: tensor-core 3xTF32 against the FP32 CUDA-core
+    shared-memory GEMM, both against the oracle."""
+    n = 18
+    circ = C.scale_grid_circuit(n, 8, seed=5)
+    ref = oracle.simulate(n, circ.gates)
+    a, ia = run_plan(circ, "c64", k_max=6, precision="3xtf32")
+    b, ib = run_plan(circ, "c64", k_max=6, precision="fp32")
+    assert ia["per_kind"].get("tensor", 0) > 0 and ib["per_kind"].get("tensor", 0) == 0
+    assert rel_l2(a, ref) < 2e-5 and rel_l2(b, ref) < 2e-5
+
+
+@pytest.mark.parametrize("prec,tol", [("3xtf32", 2e-5), ("3xbf16", 2e-4), ("tf32", 2e-2)])
+def test_grid_circuit_kmax6(qs, prec, tol):
+    n = 20
+    circ = C.scale_grid_circuit(n, 14, seed=1)
+    ref = oracle.simulate(n, circ.gates)
+    got, info = run_plan(circ, "c64", k_max=6, precision=prec)
+    assert info["per_kind"].get("tensor", 0) > 10, info
+    assert rel_l2(got, ref) < tol, rel_l2(got, ref)
+
+
+def test_no_device_timeout_flag(qs):
+    n = 16
+    circ = C.random_circuit(n, 30, seed=9, max_k=3)
+    c = B.circuit_from(circ)
+    p = B.Plan(c, "c64", k_max=6, precision="3xtf32")
+    s = B.State(n, "c64")
+    p.execute(s)
+    s.sync()   # raises QsError(status 5) if a bounded device wait had timed out
