@@ -15,9 +15,10 @@
 //
 // One persistent CTA per SM, warp-specialised:
 //   warps 0-3  epilogue: tensor memory -> registers -> recombine -> HBM
-//   warps 4-7  producer: gather 32 sets x 64 amplitudes (coalesced), split,
-//              write swizzled shared-memory stages
-//   warp 8     one thread issues the MMAs and commits to mbarriers
+//   warps 4-11 producer: cp.async gathers of 32 sets x 64 amplitudes
+//              (coalesced) several tiles ahead into a raw ring, then the
+//              hi/lo split into the swizzled shared-memory stages
+//   warp 12    one thread issues the MMAs and commits to mbarriers
 // Every mbarrier wait is bounded (about two seconds of clock64); on timeout
 // the CTA sets the error flag, drains its MMAs, frees tensor memory, exits.
 #include <cuda_bf16.h>
@@ -33,8 +34,11 @@ namespace tc {
 
 constexpr int kSets = 32;          // sets (N/2) per tile
 constexpr int kRowsB = 2 * kSets;  // B rows: (set, re/im)
-constexpr int kStages = 3;
-constexpr int kThreads = 288;
+constexpr int kStages = 2;         // split, swizzled B stages
+constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kProdThreads = 32 * kProdWarps;
+constexpr int kMmaWarp = kEpiWarps + kProdWarps;
+constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kTmemCols = 128;     // two accumulators of 64 columns
 constexpr long long kTimeout = 4ll << 30;
 
@@ -74,7 +78,15 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void named_sync(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+// Barrier among the threads of one role (init count = role size), built on an
+// mbarrier so a wait is bounded: a role whose member left on an error path
+// times out instead of hanging.  The result is made warp-uniform.
+__device__ __forceinline__ bool group_sync(uint64_t* bar, uint32_t& phase, int* err, volatile int* abort_flag) {
+    mbar_arrive(bar);
+    const bool ok = mbar_wait(bar, phase, err, abort_flag);
+    phase ^= 1u;
+    return __all_sync(0xffffffffu, ok);
+}
 
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO); the leading offset is unused for this layout
@@ -134,15 +146,26 @@ __device__ __forceinline__ float tf32_rna(float x) {
     return __uint_as_float(r);
 }
 
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // byte offset of 16-byte chunk `c` of row `r` in a [rows][128 B] swizzled block
 __device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
 struct Args {
-    uint64_t off[64];   // offset of local index l (Kronecker order)
+    uint64_t off[64];   // offset of local index l; the gate's qubits are in
+                        // descending order, so local bit b is the b-th lowest target
     int sorted[6];      // target bits ascending
     uint64_t ntiles;    // 2^(n-6) / 32
 };
 
+// Q0T: qubit 0 is a target.  Then amplitude pairs (l, l+1), l even, are
+// adjacent in memory; otherwise set pairs (s, s+1), s even, are.  Either way
+// every gather and write-back moves 16-byte pairs.
 template <int SPLITS, int KIND>
 struct Layout {
     static constexpr int kAtomsK = KIND == 0 ? 2 : 1;           // 64 K elements
@@ -152,14 +175,17 @@ struct Layout {
     static constexpr int kA = 0;
     static constexpr int kB = kA + SPLITS_A * kABytes;
     static constexpr int kStageBytes = SPLITS_A * kBBytes;
-    static constexpr int kX = kB + kStages * kStageBytes;        // Im-row exchange, 64 x 65 floats
-    static constexpr int kY = kX + 64 * 65 * 4;                  // output staging, 64 x 34 float2
-    static constexpr int kOff = kY + 64 * 34 * 8;                // offsets (64 x u64)
+    static constexpr int kRaw = 4;                               // gathered tiles in flight
+    static constexpr int kRawBytes = 32 * 66 * 8;                // [64][32] or [32][66] float2
+    static constexpr int kR = kB + kStages * kStageBytes;
+    static constexpr int kY = kR + kRaw * kRawBytes;             // [64][34] or [32][66] float2
+    static constexpr int kYBytes = 32 * 68 * 8;
+    static constexpr int kOff = kY + kYBytes;                    // offsets (64 x u64)
     static constexpr int kBar = kOff + 64 * 8;                   // barriers
     static constexpr int kTotal = kBar + 128;
 };
 
-template <int SPLITS, int KIND>
+template <int SPLITS, int KIND, bool Q0T>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm6(float2* __restrict__ psi, const float2* __restrict__ U, const __grid_constant__ Args a, int* err) {
     using LY = Layout<SPLITS, KIND>;
@@ -172,16 +198,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* dfull = empty + kStages;
     uint64_t* dempty = dfull + 2;
     uint64_t* drain = dempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* prodbar = drain + 1;
+    uint64_t* epibar = prodbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epibar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     uint64_t* soff = reinterpret_cast<uint64_t*>(sm + LY::kOff);
-    float* xbuf = reinterpret_cast<float*>(sm + LY::kX);
     float2* ystage = reinterpret_cast<float2*>(sm + LY::kY);
 
-    // ---- A = [Re U; Im U] split into hi (and lo) parts, swizzled K-major
+    // ---- A: row m = 32q + 16h + rr holds (h ? Im : Re) U[16q + rr][:], so
+    // each epilogue warp owns the real and imaginary rows of 16 outputs
     for (int idx = threadIdx.x; idx < 128 * 64; idx += blockDim.x) {
         const int m = idx >> 6, l = idx & 63;
-        const float v = m < 64 ? U[m * 64 + l].x : U[(m - 64) * 64 + l].y;
+        const int r = 16 * (m >> 5) + (m & 15), h = (m >> 4) & 1;
+        const float v = h ? U[r * 64 + l].y : U[r * 64 + l].x;
         if constexpr (KIND == 0) {
             const float hi = tf32_rna(v);
             const int atom = l >> 5, kin = l & 31;
@@ -200,14 +229,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = threadIdx.x; i < 64; i += blockDim.x) soff[i] = a.off[i];
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 128);
+            mbar_init(&full[s], kProdThreads);
             mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&dfull[s], 1);
-            mbar_init(&dempty[s], 128);
+            mbar_init(&dempty[s], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
+        mbar_init(prodbar, kProdThreads);
+        mbar_init(epibar, 32 * kEpiWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -223,27 +254,67 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ================= producer
-        const int pw = warp - 4;
-        const int j = (lane & 15) + 16 * (pw & 1), lsel = lane >> 4, lg = pw >> 1;
+        // (1) cp.async gathers tile it+kRaw-1 into a raw ring slot while
+        // (2) tile it, already in shared memory, is split and written into
+        //     the swizzled stage the MMA reads.
+        const int ptid = threadIdx.x - 32 * kEpiWarps, pw = ptid >> 5;
+        unsigned char* raw = sm + LY::kR;
+        auto issue = [&](uint64_t itx) {
+            const uint64_t tt = blockIdx.x + itx * gridDim.x;
+            if (tt < a.ntiles) {
+                float2* slot = reinterpret_cast<float2*>(raw + (itx % LY::kRaw) * LY::kRawBytes);
+                if constexpr (Q0T) {
+                    // pairs (l, l+1) of one set; a warp reads one whole set
+                    const int lp = ptid & 31;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int jj = (ptid >> 5) + 8 * i;
+                        uint64_t base = tt * kSets + jj;
+#pragma unroll
+                        for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
+                        cp_async16(slot + jj * 66 + 2 * lp, psi + base + soff[2 * lp]);
+                    }
+                } else {
+                    // pairs (s, s+1) of one local index; a warp reads 2 rows
+                    const int sp = ptid & 15;
+                    uint64_t base = tt * kSets + 2 * sp;
+#pragma unroll
+                    for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const int l = (ptid >> 4) + 16 * i;
+                        cp_async16(slot + l * 32 + 2 * sp, psi + base + soff[l]);
+                    }
+                }
+            }
+            cp_async_commit();  // one group per tile, possibly empty
+        };
+        for (int p = 0; p < LY::kRaw - 1; ++p) issue((uint64_t)p);
+        // conversion unit: (set j, chunk Q of 4 (TF32) or 8 (BF16) local indices)
+        const int j = (ptid & 15) + 16 * (pw & 1), lsel = (ptid >> 4) & 1, lg = pw >> 1;
+        uint32_t gph = 0;
         for (uint64_t it = 0;; ++it) {
             const uint64_t t = blockIdx.x + it * gridDim.x;
             if (t >= a.ntiles) break;
+            issue(it + LY::kRaw - 1);
+            cp_async_wait<LY::kRaw - 1>();
+            // every producer's copies of tile `it` have landed
+            if (!group_sync(prodbar, gph, err, abort_flag)) break;
             const int stage = (int)(it % kStages);
             const uint32_t ph = (uint32_t)((it / kStages) & 1);
-            if (!mbar_wait(&empty[stage], ph ^ 1, err, abort_flag)) break;
-            uint64_t base = t * kSets + j;
-#pragma unroll
-            for (int i = 0; i < 6; ++i) base = insert_zero(base, a.sorted[i]);
+            if (!__all_sync(0xffffffffu, mbar_wait(&empty[stage], ph ^ 1, err, abort_flag))) break;
+            const float2* rs = reinterpret_cast<const float2*>(raw + (it % LY::kRaw) * LY::kRawBytes);
+            auto rawat = [&](int l) { return Q0T ? rs[j * 66 + l] : rs[l * 32 + j]; };
             unsigned char* bst = sm + LY::kB + stage * LY::kStageBytes;
             if constexpr (KIND == 0) {
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int Q = lsel + 2 * lg + 4 * i;  // chunk of 4 consecutive local indices
+                for (int i = 0; i < 2; ++i) {
+                    const int Q = lsel + 2 * lg + 8 * i;  // 4 consecutive local indices
                     float2 x[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) x[e] = psi[base + soff[4 * Q + e]];
+                    for (int e = 0; e < 4; ++e) x[e] = rawat(4 * Q + e);
                     const int atom = Q >> 3, q = Q & 7;
                     float4 rh, ih, rl, il;
                     rh.x = tf32_rna(x[0].x); rh.y = tf32_rna(x[1].x); rh.z = tf32_rna(x[2].x); rh.w = tf32_rna(x[3].x);
@@ -262,41 +333,41 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
             } else {
+                const int Q = lsel + 2 * lg;  // 8 consecutive local indices
+                float2 x[8];
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int Q = lsel + 2 * lg + 4 * i;  // chunk of 8 consecutive local indices
-                    float2 x[8];
+                for (int e = 0; e < 8; ++e) x[e] = rawat(8 * Q + e);
+                uint32_t rh[4], ih[4], rl[4], il[4];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) x[e] = psi[base + soff[8 * Q + e]];
-                    uint32_t rh[4], ih[4], rl[4], il[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const __nv_bfloat16 r0 = __float2bfloat16_rn(x[2 * e].x), r1 = __float2bfloat16_rn(x[2 * e + 1].x);
-                        const __nv_bfloat16 i0 = __float2bfloat16_rn(x[2 * e].y), i1 = __float2bfloat16_rn(x[2 * e + 1].y);
-                        rh[e] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
-                        ih[e] = (uint32_t)__bfloat16_as_ushort(i0) | ((uint32_t)__bfloat16_as_ushort(i1) << 16);
-                        if constexpr (SPLITS == 3) {
-                            const __nv_bfloat16 a0 = __float2bfloat16_rn(x[2 * e].x - __bfloat162float(r0));
-                            const __nv_bfloat16 a1 = __float2bfloat16_rn(x[2 * e + 1].x - __bfloat162float(r1));
-                            const __nv_bfloat16 b0 = __float2bfloat16_rn(x[2 * e].y - __bfloat162float(i0));
-                            const __nv_bfloat16 b1 = __float2bfloat16_rn(x[2 * e + 1].y - __bfloat162float(i1));
-                            rl[e] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
-                            il[e] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-                        }
-                    }
-                    const uint32_t o_re = swz(2 * j, Q), o_im = swz(2 * j + 1, Q);
-                    *reinterpret_cast<uint4*>(bst + o_re) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                    *reinterpret_cast<uint4*>(bst + o_im) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                for (int e = 0; e < 4; ++e) {
+                    const __nv_bfloat16 r0 = __float2bfloat16_rn(x[2 * e].x), r1 = __float2bfloat16_rn(x[2 * e + 1].x);
+                    const __nv_bfloat16 i0 = __float2bfloat16_rn(x[2 * e].y), i1 = __float2bfloat16_rn(x[2 * e + 1].y);
+                    rh[e] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
+                    ih[e] = (uint32_t)__bfloat16_as_ushort(i0) | ((uint32_t)__bfloat16_as_ushort(i1) << 16);
                     if constexpr (SPLITS == 3) {
-                        *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_re) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                        *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_im) = make_uint4(il[0], il[1], il[2], il[3]);
+                        const __nv_bfloat16 a0 = __float2bfloat16_rn(x[2 * e].x - __bfloat162float(r0));
+                        const __nv_bfloat16 a1 = __float2bfloat16_rn(x[2 * e + 1].x - __bfloat162float(r1));
+                        const __nv_bfloat16 b0 = __float2bfloat16_rn(x[2 * e].y - __bfloat162float(i0));
+                        const __nv_bfloat16 b1 = __float2bfloat16_rn(x[2 * e + 1].y - __bfloat162float(i1));
+                        rl[e] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
+                        il[e] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
                     }
+                }
+                const uint32_t o_re = swz(2 * j, Q), o_im = swz(2 * j + 1, Q);
+                *reinterpret_cast<uint4*>(bst + o_re) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                *reinterpret_cast<uint4*>(bst + o_im) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                if constexpr (SPLITS == 3) {
+                    *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_re) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                    *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_im) = make_uint4(il[0], il[1], il[2], il[3]);
                 }
             }
             fence_async_smem();
             mbar_arrive(&full[stage]);
+            // raw slot of tile `it` is free for tile it+kRaw
+            if (!group_sync(prodbar, gph, err, abort_flag)) break;
         }
-    } else if (warp == 8) {
+        cp_async_wait<0>();  // nothing of ours still in flight at exit
+    } else if (warp == kMmaWarp) {
         // ================= MMA issuer
         if (lane == 0) {
             const uint32_t a_base = su32(sm + LY::kA);
@@ -340,13 +411,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ================= epilogue (warps 0-3 own TMEM lanes 32w .. 32w+31)
+        // ================= epilogue: warp q owns TMEM lanes 32q..32q+31 =
+        // real rows (lanes 0-15) and imaginary rows (16-31) of outputs
+        // r = 16q + (lane & 15)
         const int tid = threadIdx.x;  // 0..127
+        const int h = lane >> 4, r = 16 * warp + (lane & 15);
+        uint32_t gph = 0;
         for (uint64_t it = 0;; ++it) {
             const uint64_t t = blockIdx.x + it * gridDim.x;
             if (t >= a.ntiles) break;
             const int acc = (int)(it & 1);
-            if (!mbar_wait(&dfull[acc], (uint32_t)((it >> 1) & 1), err, abort_flag)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(&dfull[acc], (uint32_t)((it >> 1) & 1), err, abort_flag))) break;
             tc_after();
             float v[64];
             const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kRowsB);
@@ -355,34 +430,56 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld_wait();
             tc_before();
             mbar_arrive(&dempty[acc]);
-            if (warp >= 2) {  // rows of Im U: hand them to the Re U rows
-                const int r = tid - 64;
+            // lane h=0 (real row) finishes sets 0..15, lane h=1 (imaginary row) sets 16..31
+            float w[32];
 #pragma unroll
-                for (int c = 0; c < 64; ++c) xbuf[r * 65 + c] = v[c];
-            }
-            named_sync(1, 128);
-            if (warp < 2) {
-                const int r = tid;
+            for (int c = 0; c < 32; ++c) w[c] = __shfl_xor_sync(0xffffffffu, h ? v[c] : v[32 + c], 16);
+            float2 y[16];
+            if (h == 0) {  // own = Re-row (sets 0..15), w = Im-row columns 0..31
 #pragma unroll
-                for (int s = 0; s < kSets; ++s) {
-                    float2 y;
-                    y.x = v[2 * s] - xbuf[r * 65 + 2 * s + 1];
-                    y.y = v[2 * s + 1] + xbuf[r * 65 + 2 * s];
-                    ystage[r * 34 + s] = y;
+                for (int si = 0; si < 16; ++si) {
+                    y[si].x = v[2 * si] - w[2 * si + 1];
+                    y[si].y = v[2 * si + 1] + w[2 * si];
+                }
+            } else {       // own = Im-row (sets 16..31), w = Re-row columns 32..63
+#pragma unroll
+                for (int si = 0; si < 16; ++si) {
+                    y[si].x = w[2 * si] - v[32 + 2 * si + 1];
+                    y[si].y = w[2 * si + 1] + v[32 + 2 * si];
                 }
             }
-            named_sync(1, 128);
-            // coalesced write-back: thread owns set j, rows l = tid/32 + 4i
-            const int j = tid & 31;
-            uint64_t base = t * kSets + j;
 #pragma unroll
-            for (int i = 0; i < 6; ++i) base = insert_zero(base, a.sorted[i]);
-#pragma unroll 4
-            for (int i = 0; i < 16; ++i) {
-                const int l = (tid >> 5) + 4 * i;
-                psi[base + soff[l]] = ystage[l * 34 + j];
+            for (int si = 0; si < 16; ++si) {
+                const int s = 16 * h + si;
+                if constexpr (Q0T) ystage[s * 66 + r] = y[si];
+                else ystage[r * 34 + s] = y[si];
             }
-            named_sync(1, 128);
+            if (!group_sync(epibar, gph, err, abort_flag)) break;
+            // coalesced 16-byte write-back
+            if constexpr (Q0T) {
+                const int lp = tid & 31;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int s = (tid >> 5) + 4 * i;
+                    uint64_t base = t * kSets + s;
+#pragma unroll
+                    for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
+                    const float4 y2 = *reinterpret_cast<const float4*>(ystage + s * 66 + 2 * lp);
+                    *reinterpret_cast<float4*>(psi + base + soff[2 * lp]) = y2;
+                }
+            } else {
+                const int sp = tid & 15;
+                uint64_t base = t * kSets + 2 * sp;
+#pragma unroll
+                for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int l = (tid >> 4) + 8 * i;
+                    const float4 y2 = *reinterpret_cast<const float4*>(ystage + l * 34 + 2 * sp);
+                    *reinterpret_cast<float4*>(psi + base + soff[l]) = y2;
+                }
+            }
+            if (!group_sync(epibar, gph, err, abort_flag)) break;
         }
     }
 
@@ -393,15 +490,21 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-template <int SPLITS, int KIND>
-static cudaError_t run(float2* psi, const float2* U, const Args& a, int* err, cudaStream_t st) {
+template <int SPLITS, int KIND, bool Q0T>
+static cudaError_t run_q(float2* psi, const float2* U, const Args& a, int* err, cudaStream_t st) {
     using LY = Layout<SPLITS, KIND>;
     const int smem = LY::kTotal + 1024;  // slack to align the base to 1024 bytes
-    cudaError_t e = cudaFuncSetAttribute(k_gemm6<SPLITS, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_gemm6<SPLITS, KIND, Q0T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
-    k_gemm6<SPLITS, KIND><<<grid, kThreads, smem, st>>>(psi, U, a, err);
+    k_gemm6<SPLITS, KIND, Q0T><<<grid, kThreads, smem, st>>>(psi, U, a, err);
     return cudaGetLastError();
+}
+
+template <int SPLITS, int KIND>
+static cudaError_t run(float2* psi, const float2* U, const Args& a, int* err, cudaStream_t st) {
+    return a.sorted[0] == 0 ? run_q<SPLITS, KIND, true>(psi, U, a, err, st)
+                            : run_q<SPLITS, KIND, false>(psi, U, a, err, st);
 }
 
 }  // namespace tc
@@ -411,6 +514,8 @@ bool gemm_supported(int n, int k) { return k == 6 && n >= 11; }
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat, int precision, int* err,
                         cudaStream_t st) {
     if (!gemm_supported(n, k)) return cudaErrorInvalidValue;
+    for (int i = 0; i + 1 < 6; ++i)  // the planner hands over descending qubit lists
+        if (qubits[i] <= qubits[i + 1]) return cudaErrorInvalidValue;
     tc::Args a{};
     for (int l = 0; l < 64; ++l) {
         uint64_t o = 0;

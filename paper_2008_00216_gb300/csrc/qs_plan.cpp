@@ -232,6 +232,32 @@ static void pad_to_six(int n, Pass& p) {
     p.mats.swap(m);
 }
 
+// Reorder a pass's qubit list to descending order (local bit b = b-th lowest
+// qubit), permuting the matrix's rows and columns to match.
+static void sort_qubits_descending(Pass& p) {
+    const int k = p.k, d = 1 << k;
+    int order[kMaxK];  // new position i takes old position order[i]
+    for (int i = 0; i < k; ++i) order[i] = i;
+    std::sort(order, order + k, [&](int x, int y) { return p.qubits[x] > p.qubits[y]; });
+    auto old_index = [&](int ln) {
+        int lo = 0;
+        for (int i = 0; i < k; ++i)
+            if ((ln >> (k - 1 - i)) & 1) lo |= 1 << (k - 1 - order[i]);
+        return lo;
+    };
+    std::vector<double> m(p.mats.size());
+    for (int r = 0; r < d; ++r)
+        for (int c = 0; c < d; ++c) {
+            const int ro = old_index(r), co = old_index(c);
+            m[2 * (r * d + c)] = p.mats[2 * (ro * d + co)];
+            m[2 * (r * d + c) + 1] = p.mats[2 * (ro * d + co) + 1];
+        }
+    int q[kMaxK];
+    for (int i = 0; i < k; ++i) q[i] = p.qubits[order[i]];
+    for (int i = 0; i < k; ++i) p.qubits[i] = q[i];
+    p.mats.swap(m);
+}
+
 int auto_tile_qubits(int n, qs_dtype dt) {
     const int L = dt == QS_C64 ? 12 : 11;
     return std::min(L, n);
@@ -285,6 +311,7 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
             else if (dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6)) {
                 p.kind = PASS_GEMM;
                 if (g.k == 5) pad_to_six(n, p);  // the tensor-core pass is 6-qubit only
+                sort_qubits_descending(p);
             } else p.kind = PASS_DENSE_SMEM;
         } else {
             p.kind = PASS_TILE;
