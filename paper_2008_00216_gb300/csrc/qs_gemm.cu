@@ -4,10 +4,11 @@
 // of the 2^(n-k) disjoint sets of 2^k amplitudes (Section 3), i.e. it is the
 // product U X with X = 2^k x 2^(n-k).  With real arithmetic:
 //   D = [Re U; Im U] (128 x 64)  x  B^T,   B = [re x_s; im x_s] per set s,
-//   y_s = (D_top re - D_bot im) + i (D_top im + D_bot re).
-// Both operands are K-major (K = the gate's 64 local indices) with the
-// 128-byte swizzle; the accumulator D (128 lanes x 64 fp32 columns per tile
-// of 32 sets) lives in tensor memory.  Precision modes on complex64 states:
+//   y_s = (D_re-rows . re-col - D_im-rows . im-col) + i (...).
+// A (the gate, split into hi/lo parts) stays resident in tensor memory for
+// the whole kernel; B (K-major, K = the gate's 64 local indices, 128-byte
+// swizzle) is streamed through shared memory; the accumulator D (128 lanes x
+// 64 FP32 columns per tile of 32 sets) is double-buffered in tensor memory.  Precision modes on complex64 states:
 //   TF32     one product, operands rounded to TF32
 //   3xTF32   A_hi B_hi + A_hi B_lo + A_lo B_hi, hi = TF32(x), lo = x - hi
 //   3xBF16   the same split with bfloat16 parts
@@ -39,7 +40,10 @@ constexpr int kEpiWarps = 4, kProdWarps = 8;
 constexpr int kProdThreads = 32 * kProdWarps;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
-constexpr int kTmemCols = 128;     // two accumulators of 64 columns
+// tensor memory: A_hi | A_lo (64 columns each for TF32, 32 for packed BF16)
+// then two 64-column FP32 accumulators
+constexpr int kTmemCols = 256;
+constexpr int kTmemD = 128;
 constexpr long long kTimeout = 4ll << 30;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -107,19 +111,21 @@ __host__ __device__ constexpr uint32_t idesc() {
            ((uint32_t)(128 >> 4) << 24);
 }
 
+// D[tmem] (+)= A[tmem] * B[smem]^T: A is read from tensor memory (row m in
+// lane m, K along columns), so only B is streamed from shared memory
 template <int KIND>
-__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void umma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc) {
     if constexpr (KIND == 0) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc<0>()), "r"(acc)
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc<0>()), "r"(acc)
             : "memory");
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-            "l"(a), "l"(b), "r"(idesc<1>()), "r"(acc)
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d),
+            "r"(a_tmem), "l"(b), "r"(idesc<1>()), "r"(acc)
             : "memory");
     }
 }
@@ -139,6 +145,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32_rna(float x) {
     uint32_t r;
@@ -169,13 +184,12 @@ struct Args {
 template <int SPLITS, int KIND>
 struct Layout {
     static constexpr int kAtomsK = KIND == 0 ? 2 : 1;           // 64 K elements
-    static constexpr int kABytes = kAtomsK * 128 * 128;          // one A split
     static constexpr int kBBytes = kAtomsK * kRowsB * 128;       // one B split, one stage
     static constexpr int SPLITS_A = SPLITS == 3 ? 2 : 1;        // stored parts (hi, lo)
-    static constexpr int kA = 0;
-    static constexpr int kB = kA + SPLITS_A * kABytes;
+    static constexpr int kACols = KIND == 0 ? 64 : 32;          // TMEM columns of one A part
+    static constexpr int kB = 0;
     static constexpr int kStageBytes = SPLITS_A * kBBytes;
-    static constexpr int kRaw = 4;                               // gathered tiles in flight
+    static constexpr int kRaw = 6;                               // gathered tiles in flight
     static constexpr int kRawBytes = 32 * 66 * 8;                // [64][32] or [32][66] float2
     static constexpr int kR = kB + kStages * kStageBytes;
     static constexpr int kY = kR + kRaw * kRawBytes;             // [64][34] or [32][66] float2
@@ -205,27 +219,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* soff = reinterpret_cast<uint64_t*>(sm + LY::kOff);
     float2* ystage = reinterpret_cast<float2*>(sm + LY::kY);
 
-    // ---- A: row m = 32q + 16h + rr holds (h ? Im : Re) U[16q + rr][:], so
-    // each epilogue warp owns the real and imaginary rows of 16 outputs
-    for (int idx = threadIdx.x; idx < 128 * 64; idx += blockDim.x) {
-        const int m = idx >> 6, l = idx & 63;
-        const int r = 16 * (m >> 5) + (m & 15), h = (m >> 4) & 1;
-        const float v = h ? U[r * 64 + l].y : U[r * 64 + l].x;
-        if constexpr (KIND == 0) {
-            const float hi = tf32_rna(v);
-            const int atom = l >> 5, kin = l & 31;
-            const uint32_t o = atom * (128 * 128) + swz(m, kin >> 2) + (kin & 3) * 4;
-            *reinterpret_cast<float*>(sm + LY::kA + o) = hi;
-            if constexpr (SPLITS == 3) *reinterpret_cast<float*>(sm + LY::kA + LY::kABytes + o) = tf32_rna(v - hi);
-        } else {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            const uint32_t o = swz(m, l >> 3) + (l & 7) * 2;
-            *reinterpret_cast<__nv_bfloat16*>(sm + LY::kA + o) = hi;
-            if constexpr (SPLITS == 3)
-                *reinterpret_cast<__nv_bfloat16*>(sm + LY::kA + LY::kABytes + o) =
-                    __float2bfloat16_rn(v - __bfloat162float(hi));
-        }
-    }
     for (int i = threadIdx.x; i < 64; i += blockDim.x) soff[i] = a.off[i];
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -248,11 +241,50 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    fence_async_smem();
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
+
+    // ---- A into tensor memory: row m = 32q + 16h + rr holds (h ? Im : Re)
+    // U[16q + rr][:], so each epilogue warp owns the real and imaginary rows
+    // of 16 outputs.  Warp q writes lanes 32q..32q+31, 16 columns at a time.
+    if (warp < kEpiWarps) {
+        const int m = threadIdx.x;
+        const int r = 16 * (m >> 5) + (m & 15), h = (m >> 4) & 1;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll
+        for (int part = 0; part < LY::SPLITS_A; ++part) {
+#pragma unroll
+            for (int cb = 0; cb < LY::kACols / 16; ++cb) {
+                uint32_t w16[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    if constexpr (KIND == 0) {
+                        const int l = 16 * cb + c;
+                        const float v = h ? U[r * 64 + l].y : U[r * 64 + l].x;
+                        const float hi = tf32_rna(v);
+                        w16[c] = __float_as_uint(part == 0 ? hi : tf32_rna(v - hi));
+                    } else {  // two bf16 per column, lower K index in the low half
+                        const int l = 2 * (16 * cb + c);
+                        const float v0 = h ? U[r * 64 + l].y : U[r * 64 + l].x;
+                        const float v1 = h ? U[r * 64 + l + 1].y : U[r * 64 + l + 1].x;
+                        __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
+                        if (part == 1) {
+                            b0 = __float2bfloat16_rn(v0 - __bfloat162float(b0));
+                            b1 = __float2bfloat16_rn(v1 - __bfloat162float(b1));
+                        }
+                        w16[c] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+                    }
+                }
+                tmem_st16(lane_base + (uint32_t)(part * LY::kACols + 16 * cb), w16);
+            }
+        }
+        tmem_st_wait();
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ================= producer
@@ -370,7 +402,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kMmaWarp) {
         // ================= MMA issuer
         if (lane == 0) {
-            const uint32_t a_base = su32(sm + LY::kA);
             constexpr int ksteps = KIND == 0 ? 8 : 4;
             bool issued = false;
             for (uint64_t it = 0;; ++it) {
@@ -381,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!mbar_wait(&dempty[acc], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag)) break;
                 tc_after();
                 const uint32_t b_base = su32(sm + LY::kB + stage * LY::kStageBytes);
-                const uint32_t d = tmem + (uint32_t)(acc * kRowsB);
+                const uint32_t d = tmem + (uint32_t)(kTmemD + acc * kRowsB);
                 // products, small terms first: (A_lo, B_hi), (A_hi, B_lo), (A_hi, B_hi)
                 constexpr int nprod = SPLITS == 3 ? 3 : 1;
                 for (int pr = 0; pr < nprod; ++pr) {
@@ -389,10 +420,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int bsel = (SPLITS == 3 && pr == 1) ? 1 : 0;
 #pragma unroll
                     for (int kk = 0; kk < ksteps; ++kk) {
-                        const uint32_t aoff = KIND == 0 ? (kk >> 2) * (128 * 128) + (kk & 3) * 32 : kk * 32;
+                        // 8 TMEM columns per K step (8 TF32, or 16 packed BF16)
+                        const uint32_t a_t = tmem + (uint32_t)(asel * LY::kACols + 8 * kk);
                         const uint32_t boff = KIND == 0 ? (kk >> 2) * (kRowsB * 128) + (kk & 3) * 32 : kk * 32;
-                        umma<KIND>(d, sdesc(a_base + asel * LY::kABytes + aoff), sdesc(b_base + bsel * LY::kBBytes + boff),
-                                   (pr > 0 || kk > 0) ? 1u : 0u);
+                        umma_ts<KIND>(d, a_t, sdesc(b_base + bsel * LY::kBBytes + boff), (pr > 0 || kk > 0) ? 1u : 0u);
                     }
                 }
                 umma_commit(&empty[stage]);
@@ -424,7 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu, mbar_wait(&dfull[acc], (uint32_t)((it >> 1) & 1), err, abort_flag))) break;
             tc_after();
             float v[64];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(acc * kRowsB);
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kTmemD + acc * kRowsB);
 #pragma unroll
             for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
             tmem_ld_wait();
