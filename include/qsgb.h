@@ -263,6 +263,42 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
                               const qs_pauli_sum* h, qs_state* psi, qs_state* lam,
                               double* energy, double* grad);
 
+/* ------------------------------------------------------------ batches */
+
+typedef struct qs_batch qs_batch;
+
+/* Plan many circuits (any mix of 1..30 qubits) for one persistent launch.
+ * Each circuit starts from |0...0>.  Circuits with n <= tile_qubits (13 for
+ * complex64, 12 for complex128 by default) run entirely inside one thread
+ * block's shared memory; wider ones run as shared-memory tile passes whose
+ * work items are claimed from a device queue (pass p of a circuit waits,
+ * bounded, for its passes < p).  `opt` may be NULL (k_max 3); k_max <= 4.
+ * The circuits are copied; they may be destroyed afterwards.  Extends the
+ * paper's Section 3 simulation to many circuits at once (its introduction
+ * cites VQE-style workloads that run numerous circuits in sequence). */
+qs_status qs_batch_create(const qs_circuit* const* circuits, int count, qs_dtype dt,
+                          const qs_options* opt, qs_batch** out);
+
+/* offsets[0..count]: amplitude offset of each circuit's state in the state
+ * buffer; offsets[count] = total amplitudes the buffer must hold. */
+qs_status qs_batch_layout(const qs_batch* b, uint64_t* offsets);
+
+qs_status qs_batch_info(const qs_batch* b, int* items, int* passes, int* gates, int* grid);
+
+/* Run the whole batch on `stream` into `device_states` (16-byte aligned,
+ * offsets from qs_batch_layout): one CUDA-graph launch (counter reset +
+ * persistent kernel), captured on first use for that buffer.  Async. */
+qs_status qs_batch_run(qs_batch* b, void* device_states, void* stream);
+
+/* Wait for the last run; QS_ERR_TIMEOUT if a device-side wait gave up. */
+qs_status qs_batch_sync(qs_batch* b);
+qs_status qs_batch_destroy(qs_batch* b);
+
+/* Time k_max in {2,3,4} x two tile widths on this batch (runs it 2x each)
+ * and return the fastest options in *best. */
+qs_status qs_batch_autotune(const qs_circuit* const* circuits, int count, qs_dtype dt,
+                            void* device_states, void* stream, qs_options* best);
+
 #ifdef __cplusplus
 }
 #endif

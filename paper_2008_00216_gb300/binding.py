@@ -79,6 +79,14 @@ _SIGS = {
     "qs_apply_pauli_sum": (ct.c_int, [_P, _P, _P]),
     "qs_adjoint_gradient": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int, _P, _P, _P,
                                        ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "qs_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.c_int, ct.POINTER(Options), ct.POINTER(_P)]),
+    "qs_batch_layout": (ct.c_int, [_P, ct.POINTER(ct.c_uint64)]),
+    "qs_batch_info": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                 ct.POINTER(ct.c_int)]),
+    "qs_batch_run": (ct.c_int, [_P, _P, _P]),
+    "qs_batch_sync": (ct.c_int, [_P]),
+    "qs_batch_destroy": (ct.c_int, [_P]),
+    "qs_batch_autotune": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.c_int, _P, _P, ct.POINTER(Options)]),
 }
 
 
@@ -412,6 +420,66 @@ def adjoint_gradient(circ: Circuit, theta, h: PauliSum, psi: State, lam: State):
     _call("qs_adjoint_gradient", circ.handle, _dbl(theta), int(theta.size), h.handle, psi.handle, lam.handle,
           ct.byref(e), g.ctypes.data_as(ct.POINTER(ct.c_double)))
     return e.value, g
+
+
+# ---------------------------------------------------------------------- batches
+
+class Batch:
+    """Many circuits in one persistent launch (qs_batch_*).  `states` is one
+    torch tensor holding every circuit's final state at `offsets[i]`."""
+
+    def __init__(self, circuits: Sequence[Circuit], dtype="c64", opts: Optional[Options] = None, **kw):
+        import torch
+        self.circuits = list(circuits)
+        self.dtype = dtype
+        arr = (ct.c_void_p * len(self.circuits))(*[c.handle.value for c in self.circuits])
+        opts = opts if opts is not None else options(**({"k_max": 3} | kw))
+        h = ct.c_void_p()
+        _call("qs_batch_create", arr, len(self.circuits), QS_C64 if dtype == "c64" else QS_C128, ct.byref(opts),
+              ct.byref(h))
+        self.handle = h
+        offs = (ct.c_uint64 * (len(self.circuits) + 1))()
+        _call("qs_batch_layout", self.handle, offs)
+        self.offsets = [int(x) for x in offs]
+        tdt = torch.complex64 if dtype == "c64" else torch.complex128
+        self.states = torch.empty(self.offsets[-1], dtype=tdt, device="cuda")
+
+    def info(self):
+        v = [ct.c_int() for _ in range(4)]
+        _call("qs_batch_info", self.handle, *[ct.byref(x) for x in v])
+        return dict(zip(("items", "passes", "gates", "grid"), (x.value for x in v)))
+
+    def run(self, stream=None):
+        _call("qs_batch_run", self.handle, ct.c_void_p(self.states.data_ptr()), ct.c_void_p(_stream_ptr(stream)))
+
+    def sync(self):
+        _call("qs_batch_sync", self.handle)
+
+    def state(self, i: int):
+        return self.states[self.offsets[i]:self.offsets[i + 1]]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load().qs_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_autotune(circuits: Sequence[Circuit], dtype="c64", stream=None) -> Options:
+    """Fastest (k_max, tile width) for this batch, by timing each candidate."""
+    import torch
+    probe = Batch(circuits, dtype)
+    arr = (ct.c_void_p * len(probe.circuits))(*[c.handle.value for c in probe.circuits])
+    best = Options()
+    _call("qs_batch_autotune", arr, len(probe.circuits), QS_C64 if dtype == "c64" else QS_C128,
+          ct.c_void_p(probe.states.data_ptr()), ct.c_void_p(_stream_ptr(stream)), ct.byref(best))
+    probe.close()
+    return best
 
 
 def version() -> str:
