@@ -47,6 +47,11 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="auto",
                     help="fp32 | 3xtf32 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of fp32 and 3xtf32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "precision"], default="grid",
+                    help="grid: the headline circuit; adjoint: gradient vs forward on the ansatz; "
+                         "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q")
+    ap.add_argument("--layers", type=int, default=20)
+    ap.add_argument("--count", type=int, default=512)
     return ap.parse_args(argv)
 
 
@@ -370,10 +375,149 @@ def run_reference(a):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------- secondary workloads
+
+def _events_ms(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_adjoint(a):
+    """Hardware-efficient ansatz (RY, RZ per qubit per layer + CZ ladder),
+    transverse-field Ising H: adjoint gradient time against one forward
+    evaluation of E(theta) (circuit + expectation)."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    pkg.load()
+    n, layers = a.n, a.layers
+    theta = C.ansatz_theta(n, layers, seed=a.seed)
+    spec = C.ansatz_circuit(n, layers, theta)
+    c = B.circuit_from(spec)
+    h = B.PauliSum(n, C.ising_hamiltonian(n))
+    psi, lam = B.State(n, a.dtype), B.State(n, a.dtype, init=None)
+    best = None
+    for k in (1, 2, 3, 4):
+        p = B.Plan(c, a.dtype, k_max=k)
+        ms = _events_ms(lambda: (psi.init_basis(0), p.execute(psi), B.expectation(psi, h)), 2, 1)
+        if best is None or ms < best[0]:
+            best = (ms, k)
+        p.close()
+    plan = B.Plan(c, a.dtype, k_max=best[1])
+    fwd_ms = _events_ms(lambda: (psi.init_basis(0), plan.execute(psi), B.expectation(psi, h)), a.steps, a.warmup)
+    adj_ms = _events_ms(lambda: B.adjoint_gradient(c, theta, h, psi, lam), a.steps, a.warmup)
+    out = {"metric": "adjoint-gradient time vs forward", "workload": "adjoint", "value": adj_ms / fwd_ms,
+           "unit": "adjoint/forward time ratio", "higher_is_better": False, "n": n, "layers": layers,
+           "params": int(theta.size), "dtype": a.dtype, "forward_ms": fwd_ms, "forward_k_max": best[1],
+           "adjoint_ms": adj_ms, "gradients_per_s": 1e3 / adj_ms, "steps": a.steps, "warmup": a.warmup}
+    print(json.dumps(out), flush=True)
+
+
+def run_batch(a):
+    """512 seeded grid circuits, n ~ U{10..22}, depth ~ U{8..24}: one batched
+    graph launch against looping the single-circuit plans."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    pkg.load()
+    specs = C.batched_workload(a.count, seed0=0)
+    circs = [B.circuit_from(s) for s in specs]
+    t0 = time.perf_counter()
+    best = B.batch_autotune(circs, a.dtype)
+    tune_s = time.perf_counter() - t0
+    bt = B.Batch(circs, a.dtype, opts=best)
+    ms = _events_ms(lambda: bt.run(), a.steps, a.warmup)
+    bt.sync()
+    # loop of the single-circuit path: one plan and state per circuit, built beforehand
+    plans = [B.Plan(c, a.dtype, k_max=best.k_max) for c in circs]
+    states = [B.State(s.n, a.dtype) for s in specs]
+
+    def loop():
+        for p, st in zip(plans, states):
+            st.init_basis(0)
+            p.execute(st)
+    loop_ms = _events_ms(loop, max(1, a.steps // 2), 1)
+    amps_gates = sum((1 << s.n) * len(s.gates) for s in specs)
+    out = {"metric": "batched circuits/s vs looped single-circuit path", "workload": "batch", "value": a.count / (ms * 1e-3),
+           "unit": "circuits/s", "higher_is_better": True, "dtype": a.dtype, "circuits": a.count,
+           "batch_ms": ms, "loop_ms": loop_ms, "loop_circuits_per_s": a.count / (loop_ms * 1e-3),
+           "speedup_vs_loop": loop_ms / ms, "autotune": {"k_max": best.k_max, "tile_qubits": best.tile_qubits,
+                                                         "seconds": tune_s}, "batch_info": bt.info(),
+           "amplitude_gate_updates_per_s": amps_gates / (ms * 1e-3), "steps": a.steps, "warmup": a.warmup}
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(a):
+    """32-qubit 4x8 grid, 20 cycles, fused k_max 5 and 6 on a complex64
+    state: time and error of the tensor-core modes and the FP32 CUDA-core
+    path against the complex128 GPU path of the same circuit."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    pkg.load()
+    n = a.n
+    spec = C.scale_grid_circuit(n, a.cycles, seed=a.seed)
+    c = B.circuit_from(spec)
+    ref = B.State(n, "c128")
+    pref = B.Plan(c, "c128", k_max=2)
+    pref.execute(ref)
+    ref.sync()
+    ref_ms = _events_ms(lambda: (ref.init_basis(0), pref.execute(ref)), 1, 0)
+    rt = ref.tensor
+
+    def errors(xt):
+        """relative L2, max |dp| and TV distance against the complex128 state,
+        in chunks of 2^26 amplitudes (bounded temporaries)"""
+        d2 = r2 = mx = tv = 0.0
+        step = 1 << 26
+        for i in range(0, rt.numel(), step):
+            r = rt[i:i + step]
+            x = xt[i:i + step].to(torch.complex128)
+            d2 += (torch.linalg.vector_norm(x - r) ** 2).item()
+            r2 += (torch.linalg.vector_norm(r) ** 2).item()
+            dp = (x.abs() ** 2 - r.abs() ** 2).abs()
+            mx = max(mx, dp.max().item())
+            tv += 0.5 * dp.sum().item()
+        return math.sqrt(d2 / r2), mx, tv
+
+    rows = []
+    st = B.State(n, "c64")
+    for k in (5, 6):
+        for prec in ("fp32", "tf32", "3xtf32", "3xbf16"):
+            p = B.Plan(c, "c64", k_max=k, precision=prec)
+            ms = _events_ms(lambda: (st.init_basis(0), p.execute(st)), a.steps, 1)
+            st.sync()
+            err, mx, tv = errors(st.tensor)
+            rows.append({"k_max": k, "precision": prec, "ms": ms, "rel_l2_vs_c128": err,
+                         "max_prob_err": mx, "tv": tv, "passes": p.info()["passes"]})
+            p.close()
+    out = {"metric": "split-precision tensor-core form vs FP32 (time and error vs complex128)", "workload": "precision",
+           "n": n, "cycles": a.cycles, "c128_ms": ref_ms, "rows": rows}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "adjoint":
+        run_adjoint(a)
+    elif a.workload == "batch":
+        run_batch(a)
+    elif a.workload == "precision":
+        run_precision(a)
     else:
         run_own(a)
 

@@ -712,36 +712,103 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
     double* res = result_area(psi);
     QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
-    // reverse sweep with per-parameter partial sums
+    // reverse sweep: units (gradient of the gate's parameter, then U^dag)
+    // grouped into tile passes over psi and lambda together.  A unit
+    // commutes with units on disjoint qubits, which leaves every
+    // <lambda|P|psi> unchanged (P acts on the unit's own qubits); diagonal
+    // units whose generator is diagonal also commute with each other.
     const int nb = reduce_blocks();
-    double* partials = nullptr;
-    double* sums = nullptr;
     const int rows = std::max(num_params, 1);
-    QS_CUDA(cudaMallocAsync(&partials, sizeof(double) * 2 * nb * (size_t)rows, sm));
-    QS_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2 * rows, sm));
-    QS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * 2 * nb * (size_t)rows, sm));
-    std::vector<double> udag, pm;
+    std::vector<GateRec> units;
+    std::vector<int> appl_kind;
     for (int l = (int)c->gates.size() - 1; l >= 0; --l) {
         const GateRec& g = c->gates[l];
+        if (g.k > 4 && g.kind != QS_GATE_DIAGONAL)
+            return fail(QS_ERR_UNSUPPORTED, "adjoint sweep supports dense gates on up to 4 qubits");
+        GateRec u = g;
         const int d = 1 << g.k;
-        udag.assign(2 * d * d, 0.0);
         for (int r = 0; r < d; ++r)
             for (int col = 0; col < d; ++col) {
-                udag[2 * (r * d + col)] = g.m[2 * (col * d + r)];
-                udag[2 * (r * d + col) + 1] = -g.m[2 * (col * d + r) + 1];
+                u.m[2 * (r * d + col)] = g.m[2 * (col * d + r)];
+                u.m[2 * (r * d + col) + 1] = -g.m[2 * (col * d + r) + 1];
             }
-        const double* pauli = nullptr;
-        if (g.param >= 0) {
-            pm.assign(2 * d * d, 0.0);
-            pauli_matrix(g.k, g.paulis, pm.data());
-            pauli = pm.data();
+        u.kind = classify_matrix(g.k, u.m.data());
+        appl_kind.push_back(u.kind);
+        if (g.param >= 0)
+            for (int i = 0; i < g.k; ++i)
+                if (g.paulis[i] == 'X' || g.paulis[i] == 'Y') u.kind = QS_GATE_DENSE;  // generator mixes amplitudes
+        units.push_back(std::move(u));
+    }
+    const int L = auto_tile_qubits(psi->n, psi->dt);
+    const int lowb = std::min(psi->dt == QS_C64 ? 5 : 4, L);
+    std::vector<std::vector<int>> groups = group_for_tiles(units, L, lowb, 3072);
+    // phase 1 (host): every pass's tile layout, gradient slots and
+    // matrices; phase 2: one upload, then the passes back to back
+    struct AdjPass {
+        int L = 0;
+        int pos[16] = {0};
+        std::vector<AdjTileGate> tg;
+        std::vector<double> mats;  // U^dagger, interleaved
+        size_t mat0 = 0;
+    };
+    std::vector<AdjPass> aps(groups.size());
+    std::vector<double> allm;
+    for (size_t gi = 0; gi < groups.size(); ++gi) {
+        const auto& gr = groups[gi];
+        AdjPass& ap = aps[gi];
+        uint64_t S = (1ull << lowb) - 1;
+        for (int u : gr)
+            for (int i = 0; i < units[u].k; ++i) S |= 1ull << units[u].qubits[i];
+        for (int q = 0; q < psi->n && __builtin_popcountll(S) < L; ++q) S |= 1ull << q;
+        int local_of[kMaxQubits];
+        for (int q = 0; q < psi->n; ++q)
+            if ((S >> q) & 1) {
+                local_of[q] = ap.L;
+                ap.pos[ap.L++] = q;
+            }
+        for (int u : gr) {
+            const GateRec& g = units[u];
+            AdjTileGate a{};
+            a.g.k = (uint8_t)g.k;
+            a.g.kind = (uint8_t)appl_kind[u];
+            for (int i = 0; i < g.k; ++i) a.g.q[i] = (uint8_t)local_of[g.qubits[i]];
+            a.g.mat = (uint32_t)(ap.mats.size() / 2);
+            ap.mats.insert(ap.mats.end(), g.m.begin(), g.m.end());
+            a.slot = g.param;
+            for (int i = 0; g.param >= 0 && i < g.k; ++i) {
+                const uint32_t bit = 1u << local_of[g.qubits[i]];
+                if (g.paulis[i] == 'X' || g.paulis[i] == 'Y') a.px |= bit;
+                if (g.paulis[i] == 'Z' || g.paulis[i] == 'Y') a.pz |= bit;
+                if (g.paulis[i] == 'Y') a.ny++;
+            }
+            ap.tg.push_back(a);
         }
-        cudaError_t e = launch_adjoint_gate(psi->data, lam->data, psi->n, psi->dt, g.k, g.qubits, udag.data(),
-                                            pauli, partials, g.param, sm);
+        ap.mat0 = allm.size() / 2;
+        allm.insert(allm.end(), ap.mats.begin(), ap.mats.end());
+    }
+    const size_t esz = psi->amp_bytes();
+    std::vector<char> hostm(allm.size() / 2 * esz);  // kept until the final synchronisation
+    for (size_t i = 0; i < allm.size(); ++i) {
+        if (psi->dt == QS_C64) ((float*)hostm.data())[i] = (float)allm[i];
+        else ((double*)hostm.data())[i] = allm[i];
+    }
+    double* partials = nullptr;
+    double* sums = nullptr;
+    void* dmats = nullptr;
+    QS_CUDA(cudaMallocAsync(&partials, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    QS_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2 * rows, sm));
+    QS_CUDA(cudaMallocAsync(&dmats, std::max<size_t>(hostm.size(), 16), sm));
+    QS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    QS_CUDA(cudaMemcpyAsync(dmats, hostm.data(), hostm.size(), cudaMemcpyHostToDevice, sm));
+    for (const AdjPass& ap : aps) {
+        const void* dm = (const char*)dmats + ap.mat0 * esz;
+        cudaError_t e = launch_adjoint_tile(psi->data, lam->data, psi->n, psi->dt, ap.L, ap.pos, ap.tg, dm,
+                                            ap.mats.size() / 2, partials, nb, sm);
         if (e != cudaSuccess) {
             cudaFreeAsync(partials, sm);
             cudaFreeAsync(sums, sm);
-            return cuda_fail(e, "adjoint gate");
+            cudaFreeAsync(dmats, sm);
+            return cuda_fail(e, "adjoint pass");
         }
     }
     QS_CUDA(launch_sum_partials(partials, rows, nb, sums, sm));
@@ -751,6 +818,7 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     QS_CUDA(cudaStreamSynchronize(sm));
     cudaFreeAsync(partials, sm);
     cudaFreeAsync(sums, sm);
+    cudaFreeAsync(dmats, sm);
     *energy = host[2 * rows];
     for (int p = 0; p < num_params; ++p) grad[p] = host[2 * p + 1];  // Im <lambda|P|psi>
     return QS_OK;

@@ -131,6 +131,11 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 int auto_tile_qubits(int n, qs_dtype dt);
+// Greedy commuting-reorder grouping of `units` (in order) into tiles of L
+// qubits that always contain the lowest `low_bits_in_tile` qubits; dense
+// members have k <= 4; each group's matrices fit `mat_budget` entries.
+std::vector<std::vector<int>> group_for_tiles(const std::vector<GateRec>& units, int L, int low_bits_in_tile,
+                                              size_t mat_budget);
 
 // ----------------------------------------------------------------- launchers
 // All launchers enqueue on `st` and return the launch error (cudaSuccess).
@@ -170,13 +175,21 @@ cudaError_t launch_apply_pauli_sum(const void* psi, void* out, int n, qs_dtype d
 cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, double* scratch,
                          double* result, cudaStream_t st);
 
-// Adjoint step: g += <lam| P |psi> over the gate's sets (complex partials
-// into scratch row `slot`), then psi <- U^dag psi, lam <- U^dag lam.
-cudaError_t launch_adjoint_gate(void* psi, void* lam, int n, qs_dtype dt, int k,
-                                const int* qubits, const double* udag, const double* pauli,
-                                double* partials, int slot, cudaStream_t st);
 cudaError_t launch_sum_partials(const double* partials, int rows, int cols, double* out,
                                 cudaStream_t st);
+
+// Reverse-sweep tile pass over psi and lambda together: for each member in
+// order, optionally accumulate <lambda|P|psi> on the tile (parameter slot),
+// then apply the member's matrix (U^dagger) to both tiles.
+struct AdjTileGate {
+    TileGate g;            // U^dagger on local qubits
+    int slot;              // parameter, or -1
+    uint32_t px, pz;       // Pauli generator on local bits: flip mask, sign mask
+    int ny;                // number of Y factors
+};
+cudaError_t launch_adjoint_tile(void* psi, void* lam, int n, qs_dtype dt, int L, const int* pos,
+                                const std::vector<AdjTileGate>& gates, const void* dmats, size_t mat_elems,
+                                double* partials, int nblocks, cudaStream_t st);
 
 int num_sms();
 

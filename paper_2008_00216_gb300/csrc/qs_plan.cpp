@@ -263,6 +263,28 @@ int auto_tile_qubits(int n, qs_dtype dt) {
     return std::min(L, n);
 }
 
+std::vector<std::vector<int>> group_for_tiles(const std::vector<GateRec>& units, int L, int low_bits_in_tile,
+                                              size_t mat_budget) {
+    const uint64_t lowmask = (1ull << low_bits_in_tile) - 1;
+    std::vector<std::vector<int>> groups;
+    std::vector<char> placed(units.size(), 0);
+    for (int start = 0; start < (int)units.size(); ++start) {
+        if (placed[start]) continue;
+        std::vector<char> trial = placed;
+        std::vector<int> taken = scan_group(units, trial, start, lowmask, L, 1 << 14, 4);
+        size_t elems = 0, keep = 0;
+        for (; keep < taken.size() && (int)keep < kMaxTileGates; ++keep) {
+            const size_t d = 1u << units[taken[keep]].k;
+            if (elems + d * d > mat_budget) break;
+            elems += d * d;
+        }
+        taken.resize(std::max<size_t>(keep, 1));
+        for (int t : taken) placed[t] = 1;
+        groups.push_back(taken);
+    }
+    return groups;
+}
+
 static int low_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
 
 // largest non-diagonal gate the tile kernel applies (register path), and

@@ -1,5 +1,5 @@
 // Reductions over the state (norm, Pauli expectations, inner products),
-// H|psi> for a Pauli sum, and the adjoint-gradient gate step.
+// H|psi> for a Pauli sum, and the adjoint-gradient tile pass.
 //
 // Every reduction runs on a fixed grid of reduce_blocks() CTAs; each CTA
 // writes one FP64 partial and a single CTA adds the partials in a fixed
@@ -12,6 +12,7 @@
 
 #include "qs_device.cuh"
 #include "qs_internal.h"
+#include "qs_tile.cuh"
 
 namespace qsgb {
 
@@ -302,122 +303,191 @@ cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, doubl
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ adjoint step
+// ------------------------------------------------------------------ adjoint tile pass
 
-template <typename R, int K>
-struct AdjP {
-    typename C2<R>::T u[1 << K][1 << K];   // U^dagger
-    uint64_t off[1 << K];
-    uint64_t psrc[1 << K];                  // (P psi)_r = i^pcode[r] psi[base + psrc[r]]
-    int pcode[1 << K];
-    int sorted[K];
-    int has_param;
-    int slot;
-    uint64_t units;
+// A single-qubit unit (local bit q) with a parameter: accumulate
+// <lambda|P|psi> and apply U^dagger to psi and lambda in the same sweep --
+// the thread holds both amplitudes of each pair of both states.  P is the
+// unit's Pauli letter: flip fx (X, Y), sign fz (Z, Y), ny factors of i.
+template <typename T, typename R>
+__device__ __forceinline__ void adj_1q_grad_apply(T* tp, T* tl, int L, int q, const T* m, int fx, int fz, int ny,
+                                                  R& zr, R& zi) {
+    const T m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+    for (uint32_t s = threadIdx.x; s < (1u << (L - 1)); s += blockDim.x) {
+        const uint32_t i0 = insert_zero32(s, q), i1 = i0 | (1u << q);
+        T a0 = tp[i0], a1 = tp[i1], b0 = tl[i0], b1 = tl[i1];
+        // (P a)_e = i^ny (-1)^((e ^ fx) & fz) a_(e ^ fx), e = bit q of the index
+        const T p0 = rot_i(fx ? a1 : a0, ny + 2 * (fx & fz));
+        const T p1 = rot_i(fx ? a0 : a1, ny + 2 * ((1 ^ fx) & fz));
+        zr += b0.x * p0.x + b0.y * p0.y + b1.x * p1.x + b1.y * p1.y;
+        zi += b0.x * p0.y - b0.y * p0.x + b1.x * p1.y - b1.y * p1.x;
+        T o0, o1;
+        o0.x = o0.y = o1.x = o1.y = 0;
+        cmac(o0, m00, a0); cmac(o0, m01, a1); cmac(o1, m10, a0); cmac(o1, m11, a1);
+        tp[i0] = o0;
+        tp[i1] = o1;
+        o0.x = o0.y = o1.x = o1.y = 0;
+        cmac(o0, m00, b0); cmac(o0, m01, b1); cmac(o1, m10, b0); cmac(o1, m11, b1);
+        tl[i0] = o0;
+        tl[i1] = o1;
+    }
+}
+
+// diagonal U^dagger on both tiles in one sweep
+template <typename T>
+__device__ __forceinline__ void adj_diag_both(T* tp, T* tl, int L, const TileGate& g, const T* m) {
+    const int k = g.k, D = 1 << k;
+    for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
+        int l = 0;
+        for (int i = 0; i < k; ++i) l = (l << 1) | ((e >> g.q[i]) & 1);
+        const T ph = m[l * D + l];
+        tp[e] = cmul(ph, tp[e]);
+        tl[e] = cmul(ph, tl[e]);
+    }
+}
+
+struct AdjTileArgs {
+    int L, b, ngates;
+    int pos[16];
+    uint32_t mat_elems;
+    uint64_t ntiles;
+    AdjTileGate g[kMaxTileGates];
 };
 
-template <typename R, int K>
-__global__ void __launch_bounds__(256) k_adjoint(typename C2<R>::T* __restrict__ psi,
-                                                 typename C2<R>::T* __restrict__ lam,
-                                                 const __grid_constant__ AdjP<R, K> p,
-                                                 double* __restrict__ partials) {
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_tile(typename C2<R>::T* __restrict__ psi, typename C2<R>::T* __restrict__ lam,
+                                                  const typename C2<R>::T* __restrict__ mats,
+                                                  const __grid_constant__ AdjTileArgs a, double* __restrict__ partials) {
     using T = typename C2<R>::T;
-    constexpr int D = 1 << K;
-    __shared__ double sh[32];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    double zr = 0.0, zi = 0.0;
-    for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < p.units; u += stride) {
-        uint64_t base = u;
-#pragma unroll
-        for (int i = 0; i < K; ++i) base = insert_zero(base, p.sorted[i]);
-        T a[D], l[D];
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-            a[r] = psi[base + p.off[r]];
-            l[r] = lam[base + p.off[r]];
-        }
-        if (p.has_param) {
-            // <lambda| P |psi> over this set
-#pragma unroll
-            for (int r = 0; r < D; ++r) {
-                const T pp = rot_i(psi[base + p.psrc[r]], p.pcode[r]);
-                zr += (double)(l[r].x * pp.x + l[r].y * pp.y);
-                zi += (double)(l[r].x * pp.y - l[r].y * pp.x);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < D; ++r) {
-            T o1, o2;
-            o1.x = o1.y = o2.x = o2.y = 0;
-#pragma unroll
-            for (int c = 0; c < D; ++c) {
-                cmac(o1, p.u[r][c], a[c]);
-                cmac(o2, p.u[r][c], l[c]);
-            }
-            psi[base + p.off[r]] = o1;
-            lam[base + p.off[r]] = o2;
-        }
-    }
-    if (p.has_param) {
-        zr = block_sum(zr, sh);
-        zi = block_sum(zi, sh);
-        if (threadIdx.x == 0) {
-            partials[((size_t)p.slot * gridDim.x + blockIdx.x) * 2] = zr;
-            partials[((size_t)p.slot * gridDim.x + blockIdx.x) * 2 + 1] = zi;
-        }
-    }
-}
-
-template <typename R, int K>
-static cudaError_t adjoint_k(void* psi, void* lam, int n, const int* qubits, const double* udag,
-                             const double* pauli, double* partials, int slot, cudaStream_t st) {
-    using T = typename C2<R>::T;
-    constexpr int D = 1 << K;
-    AdjP<R, K> p{};
-    for (int r = 0; r < D; ++r)
-        for (int c = 0; c < D; ++c) {
-            p.u[r][c].x = (R)udag[2 * (r * D + c)];
-            p.u[r][c].y = (R)udag[2 * (r * D + c) + 1];
-        }
-    for (int l = 0; l < D; ++l) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int L = a.L, b = a.b;
+    T* tp = reinterpret_cast<T*>(smem_raw);        // psi tile
+    T* tl = tp + (1u << L);                         // lambda tile
+    T* smat = tl + (1u << L);
+    uint64_t* rowoff = reinterpret_cast<uint64_t*>(smat + a.mat_elems);
+    // the double2 accumulators need 16-byte alignment: round the offset up
+    double2* acc = reinterpret_cast<double2*>((reinterpret_cast<uintptr_t>(rowoff + (1u << (L - b))) + 15) &
+                                              ~(uintptr_t)15);
+    const uint32_t rowlen = 1u << b;
+    for (uint32_t i = threadIdx.x; i < a.mat_elems; i += blockDim.x) smat[i] = mats[i];
+    for (uint32_t h = threadIdx.x; h < (1u << (L - b)); h += blockDim.x) {
         uint64_t o = 0;
-        for (int i = 0; i < K; ++i)
-            if ((l >> (K - 1 - i)) & 1) o |= 1ull << qubits[i];
-        p.off[l] = o;
+        for (int i = b; i < L; ++i)
+            if ((h >> (i - b)) & 1) o |= 1ull << a.pos[i];
+        rowoff[h] = o;
     }
-    p.has_param = pauli != nullptr && slot >= 0;
-    p.slot = slot;
-    if (p.has_param) {
-        for (int r = 0; r < D; ++r) {
-            int c = 0;
-            while (c < D - 1 && pauli[2 * (r * D + c)] == 0.0 && pauli[2 * (r * D + c) + 1] == 0.0) ++c;
-            const double re = pauli[2 * (r * D + c)], im = pauli[2 * (r * D + c) + 1];
-            p.pcode[r] = re == 1.0 ? 0 : im == 1.0 ? 1 : re == -1.0 ? 2 : 3;
-            p.psrc[r] = p.off[c];
+    for (int i = threadIdx.x; i < 8 * a.ngates; i += blockDim.x) acc[i] = make_double2(0.0, 0.0);
+    __syncthreads();
+    for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+        uint64_t base = t;
+        for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
+        for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
+            const uint64_t gi = base + rowoff[e >> b] + (e & (rowlen - 1));
+            tp[e] = psi[gi];
+            tl[e] = lam[gi];
         }
+        __syncthreads();
+        for (int gi = 0; gi < a.ngates; ++gi) {
+            const AdjTileGate& ag = a.g[gi];
+            const TileGate& g = ag.g;
+            const T* m = smat + g.mat;
+            if (ag.slot >= 0 && g.k == 1) {
+                // fused: gradient and U^dagger in one sweep, one barrier
+                const int q = g.q[0];
+                R zr = 0, zi = 0;
+                adj_1q_grad_apply<T, R>(tp, tl, L, q, m, (ag.px >> q) & 1, (ag.pz >> q) & 1, ag.ny, zr, zi);
+                const double sr = warp_sum((double)zr), si = warp_sum((double)zi);
+                if ((threadIdx.x & 31) == 0) {
+                    double2& w = acc[gi * 8 + (threadIdx.x >> 5)];
+                    w.x += sr;
+                    w.y += si;
+                }
+                __syncthreads();
+                continue;
+            }
+            if (ag.slot >= 0) {
+                // <lambda| P |psi> on this tile: (P psi)_e = i^ny (-1)^popc((e^px) & pz) psi_{e^px};
+                // warp-reduced into this warp's accumulator (no block barrier)
+                R zr = 0, zi = 0;
+                for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
+                    const uint32_t f = e ^ ag.px;
+                    const T v = rot_i(tp[f], ag.ny + 2 * (__popc(f & ag.pz) & 1));
+                    const T l = tl[e];
+                    zr += l.x * v.x + l.y * v.y;
+                    zi += l.x * v.y - l.y * v.x;
+                }
+                const double sr = warp_sum((double)zr), si = warp_sum((double)zi);
+                if ((threadIdx.x & 31) == 0) {
+                    double2& w = acc[gi * 8 + (threadIdx.x >> 5)];
+                    w.x += sr;
+                    w.y += si;
+                }
+                __syncthreads();  // psi/lambda reads above finish before the gate rewrites them
+            }
+            if (g.kind == QS_GATE_DIAGONAL) {
+                adj_diag_both(tp, tl, L, g, m);
+            } else {
+                switch (g.k) {
+                    case 1: tile_dense<T, 1>(tp, L, g, m); tile_dense<T, 1>(tl, L, g, m); break;
+                    case 2: tile_dense<T, 2>(tp, L, g, m); tile_dense<T, 2>(tl, L, g, m); break;
+                    case 3: tile_dense<T, 3>(tp, L, g, m); tile_dense<T, 3>(tl, L, g, m); break;
+                    case 4: tile_dense<T, 4>(tp, L, g, m); tile_dense<T, 4>(tl, L, g, m); break;
+                    default: break;
+                }
+            }
+            __syncthreads();
+        }
+        for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
+            const uint64_t gi = base + rowoff[e >> b] + (e & (rowlen - 1));
+            psi[gi] = tp[e];
+            lam[gi] = tl[e];
+        }
+        __syncthreads();
     }
-    for (int i = 0; i < K; ++i) p.sorted[i] = qubits[i];
-    std::sort(p.sorted, p.sorted + K);
-    p.units = 1ull << (n - K);
-    k_adjoint<R, K><<<reduce_blocks(), 256, 0, st>>>((T*)psi, (T*)lam, p, partials);
-    return cudaGetLastError();
+    __syncthreads();
+    for (int gi = threadIdx.x; gi < a.ngates; gi += blockDim.x) {
+        const int slot = a.g[gi].slot;
+        if (slot < 0) continue;
+        double sr = 0.0, si = 0.0;
+        for (int w = 0; w < 8; ++w) {  // fixed order: deterministic
+            sr += acc[gi * 8 + w].x;
+            si += acc[gi * 8 + w].y;
+        }
+        partials[((size_t)slot * gridDim.x + blockIdx.x) * 2] = sr;
+        partials[((size_t)slot * gridDim.x + blockIdx.x) * 2 + 1] = si;
+    }
 }
 
-cudaError_t launch_adjoint_gate(void* psi, void* lam, int n, qs_dtype dt, int k, const int* qubits,
-                                const double* udag, const double* pauli, double* partials, int slot,
-                                cudaStream_t st) {
-#define QS_ADJ_CASE(KK)                                                                           \
-    case KK:                                                                                      \
-        return dt == QS_C64 ? adjoint_k<float, KK>(psi, lam, n, qubits, udag, pauli, partials, slot, st) \
-                            : adjoint_k<double, KK>(psi, lam, n, qubits, udag, pauli, partials, slot, st);
-    switch (k) {
-        QS_ADJ_CASE(1)
-        QS_ADJ_CASE(2)
-        QS_ADJ_CASE(3)
-        QS_ADJ_CASE(4)
+cudaError_t launch_adjoint_tile(void* psi, void* lam, int n, qs_dtype dt, int L, const int* pos,
+                                const std::vector<AdjTileGate>& gates, const void* dmats, size_t mat_elems,
+                                double* partials, int nblocks, cudaStream_t st) {
+    if ((int)gates.size() > kMaxTileGates || L < 1 || L > 13) return cudaErrorInvalidValue;
+    AdjTileArgs a{};
+    a.L = L;
+    int b = 0;
+    while (b < L && pos[b] == b) ++b;
+    a.b = b;
+    a.ngates = (int)gates.size();
+    for (int i = 0; i < L; ++i) a.pos[i] = pos[i];
+    for (int i = 0; i < a.ngates; ++i) a.g[i] = gates[i];
+    a.mat_elems = (uint32_t)mat_elems;
+    a.ntiles = 1ull << (n - L);
+    const size_t esz = dt == QS_C64 ? 8 : 16;
+    const size_t smem = esz * (2 * (1u << L) + mat_elems) + sizeof(uint64_t) * (1u << (L - b)) + 16 +
+                        sizeof(double2) * 8 * a.ngates;   // one accumulator per warp (8 warps)
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (dt == QS_C64) {
+        e = cudaFuncSetAttribute(k_adj_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_adj_tile<float><<<nblocks, 256, smem, st>>>((float2*)psi, (float2*)lam, (const float2*)dmats, a, partials);
+    } else {
+        e = cudaFuncSetAttribute(k_adj_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_adj_tile<double><<<nblocks, 256, smem, st>>>((double2*)psi, (double2*)lam, (const double2*)dmats, a,
+                                                        partials);
     }
-#undef QS_ADJ_CASE
-    return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 }  // namespace qsgb

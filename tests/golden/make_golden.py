@@ -2,13 +2,13 @@
 oracle only (no CUDA code is imported).
 
 Circuit: the seeded grid generator with patterns ABCDCDAB and random fSim
-angles (theta ~ U(0, pi/2), phi ~ U(0, pi)), 14 cycles, seed 1, at n qubits
-on the near-square grid.  Stored per file: n, seed, cycles, the number of
+angles (theta ~ U(0, pi/2), phi ~ U(0, pi)), 14 (or the given number of)
+cycles, seed 1, at n qubits on the near-square grid.  Stored per file: n, seed, cycles, the number of
 gates, 512 seeded sample indices with their amplitudes, the first 64
 amplitudes, and two whole-state sums (sum |a|^2 and sum |a|^4) that depend
 on every amplitude.
 
-Usage:  python tests/golden/make_golden.py 26 [28 ...]
+Usage:  python tests/golden/make_golden.py 26 [28 28:20 ...]   (n[:cycles], default 14 cycles)
 """
 
 import json
@@ -32,16 +32,17 @@ def sample_indices(n, count=512, seed=7):
     return sorted({rng.next_u64() % (1 << n) for _ in range(count)})
 
 
-def main(ns):
-    for n in ns:
+def main(specs):
+    for spec in specs:
+        n, cycles = (int(x) for x in (spec.split(":") + ["14"])[:2])
         t0 = time.time()
-        circ = C.scale_grid_circuit(n, 14, seed=1)
+        circ = C.scale_grid_circuit(n, cycles, seed=1)
         psi = oracle.simulate(n, circ.gates)
         idx = sample_indices(n)
         p = np.abs(psi) ** 2
         out = {
             "what": "FP64 oracle amplitudes of the scale grid circuit (ABCDCDAB, random fSim)",
-            "n": n, "cycles": 14, "seed": 1, "num_gates": len(circ.gates),
+            "n": n, "cycles": cycles, "seed": 1, "num_gates": len(circ.gates),
             "indices": idx,
             "amplitudes": [[float(psi[i].real), float(psi[i].imag)] for i in idx],
             "first64": [[float(a.real), float(a.imag)] for a in psi[:64]],
@@ -49,11 +50,11 @@ def main(ns):
             "sum_p2": math.fsum((p * p).tolist()),
             "oracle_seconds": time.time() - t0,
         }
-        path = os.path.join(HERE, f"grid{n}_c14_seed1.json")
+        path = os.path.join(HERE, f"grid{n}_c{cycles}_seed1.json")
         with open(path, "w") as f:
             json.dump(out, f, indent=0)
         print(path, f"{time.time() - t0:.0f}s", flush=True)
 
 
 if __name__ == "__main__":
-    main([int(a) for a in sys.argv[1:]] or [26])
+    main(sys.argv[1:] or ["26"])

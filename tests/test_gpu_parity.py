@@ -188,3 +188,27 @@ def test_bad_arguments_return_status(qs):
     with pytest.raises(B.QsError):
         p.execute(s)   # plan for 12 qubits on a 5-qubit state
     s.close()
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_adjoint_gradient_12q_20_layers_sampled(qs, dtype):
+    """The differentiation workload's check size: 12 qubits, 20 layers (480
+    parameters).  The adjoint gradient against exact parameter shift on a
+    seeded sample of 48 parameters, and against central differences (h=1e-4,
+    FP64 oracle) on 6 of them; energy against the oracle."""
+    n, layers = 12, 20
+    theta = C.ansatz_theta(n, layers, seed=1)
+    terms = C.ising_hamiltonian(n)
+    build = lambda t: C.ansatz_circuit(n, layers, t).gates
+    rng = Xoshiro256ss(12)
+    sample = sorted({rng.randint(theta.size) for _ in range(60)})[:48]
+    ps = oracle.parameter_shift_gradient(n, build, theta, terms, params=sample)
+    fd = oracle.central_fd_gradient(n, build, theta, terms, h=1e-4, params=sample[:6])
+    c = B.circuit_from(C.ansatz_circuit(n, layers, theta))
+    h = B.PauliSum(n, terms)
+    psi, lam = B.State(n, dtype), B.State(n, dtype)
+    e, g = B.adjoint_gradient(c, theta, h, psi, lam)
+    tol = 1e-4 if dtype == "c64" else 1e-10
+    assert abs(e - oracle.energy(n, build, theta, terms)) < tol * max(1.0, abs(e))
+    assert np.linalg.norm(g[sample] - ps) / np.linalg.norm(ps) < tol
+    assert np.max(np.abs(g[sample[:6]] - fd)) < (1e-4 if dtype == "c64" else 1e-7)
