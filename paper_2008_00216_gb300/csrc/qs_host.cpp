@@ -719,10 +719,25 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     // units whose generator is diagonal also commute with each other.
     const int nb = reduce_blocks();
     const int rows = std::max(num_params, 1);
+    // runs of consecutive fixed gates are fused first (<= 4 qubits, FP64
+    // products): the reverse sweep then applies one U^dagger per block
+    std::vector<GateRec> fwd;
+    for (size_t l = 0; l < c->gates.size();) {
+        if (c->gates[l].param >= 0) {
+            fwd.push_back(c->gates[l++]);
+            continue;
+        }
+        std::vector<GateRec> run;
+        while (l < c->gates.size() && c->gates[l].param < 0) run.push_back(c->gates[l++]);
+        std::vector<GateRec> blocks;
+        st = fuse_gates(c->n, run, 4, blocks);
+        if (st != QS_OK) return st;
+        fwd.insert(fwd.end(), blocks.begin(), blocks.end());
+    }
     std::vector<GateRec> units;
     std::vector<int> appl_kind;
-    for (int l = (int)c->gates.size() - 1; l >= 0; --l) {
-        const GateRec& g = c->gates[l];
+    for (int l = (int)fwd.size() - 1; l >= 0; --l) {
+        const GateRec& g = fwd[l];
         if (g.k > 4 && g.kind != QS_GATE_DIAGONAL)
             return fail(QS_ERR_UNSUPPORTED, "adjoint sweep supports dense gates on up to 4 qubits");
         GateRec u = g;
@@ -774,6 +789,20 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
             for (int i = 0; i < g.k; ++i) a.g.q[i] = (uint8_t)local_of[g.qubits[i]];
             a.g.mat = (uint32_t)(ap.mats.size() / 2);
             ap.mats.insert(ap.mats.end(), g.m.begin(), g.m.end());
+            if (appl_kind[u] == QS_GATE_DIAGONAL) {  // all phases +-1 / +-i: no multiplies
+                a.mulfree = 1;
+                const int d = 1 << g.k;
+                for (int r = 0; r < d; ++r) {
+                    const double re = g.m[2 * (r * d + r)], im = g.m[2 * (r * d + r) + 1];
+                    const bool q = (re == 0.0 && (im == 1.0 || im == -1.0)) || (im == 0.0 && (re == 1.0 || re == -1.0));
+                    if (!q) a.mulfree = 0;
+                }
+            }
+            if (g.k == 1) {
+                bool real = true;
+                for (int i = 0; i < 4; ++i) real = real && g.m[2 * i + 1] == 0.0;
+                a.form = appl_kind[u] == QS_GATE_DIAGONAL ? 1 : real ? 2 : 0;
+            }
             a.slot = g.param;
             for (int i = 0; g.param >= 0 && i < g.k; ++i) {
                 const uint32_t bit = 1u << local_of[g.qubits[i]];

@@ -185,7 +185,10 @@ struct AdjTileGate {
     TileGate g;            // U^dagger on local qubits
     int slot;              // parameter, or -1
     uint32_t px, pz;       // Pauli generator on local bits: flip mask, sign mask
-    int ny;                // number of Y factors
+    uint8_t ny;            // number of Y factors
+    uint8_t mulfree;       // diagonal with every phase in {+-1, +-i}
+    uint8_t form;          // single-qubit U^dagger: 0 complex, 1 diagonal, 2 real
+    uint8_t pad;
 };
 cudaError_t launch_adjoint_tile(void* psi, void* lam, int n, qs_dtype dt, int L, const int* pos,
                                 const std::vector<AdjTileGate>& gates, const void* dmats, size_t mat_elems,

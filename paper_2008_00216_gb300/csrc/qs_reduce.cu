@@ -309,40 +309,80 @@ cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, doubl
 // <lambda|P|psi> and apply U^dagger to psi and lambda in the same sweep --
 // the thread holds both amplitudes of each pair of both states.  P is the
 // unit's Pauli letter: flip fx (X, Y), sign fz (Z, Y), ny factors of i.
-template <typename T, typename R>
-__device__ __forceinline__ void adj_1q_grad_apply(T* tp, T* tl, int L, int q, const T* m, int fx, int fz, int ny,
-                                                  R& zr, R& zi) {
+// Matrix structure of a single-qubit U^dagger, chosen on the host: general
+// complex, diagonal (RZ-like: one complex multiply per amplitude) or real
+// (RY-like: two real multiplies per output component).
+enum { ADJ1_DENSE = 0, ADJ1_DIAG = 1, ADJ1_REAL = 2 };
+
+template <typename T, typename R, int FORM>
+__device__ __forceinline__ void adj_1q_grad_apply_f(T* tp, T* tl, int L, int q, const T* m, int fx, int fz, int ny,
+                                                    R& zr, R& zi) {
     const T m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
     for (uint32_t s = threadIdx.x; s < (1u << (L - 1)); s += blockDim.x) {
         const uint32_t i0 = insert_zero32(s, q), i1 = i0 | (1u << q);
-        T a0 = tp[i0], a1 = tp[i1], b0 = tl[i0], b1 = tl[i1];
+        const T a0 = tp[i0], a1 = tp[i1], b0 = tl[i0], b1 = tl[i1];
         // (P a)_e = i^ny (-1)^((e ^ fx) & fz) a_(e ^ fx), e = bit q of the index
         const T p0 = rot_i(fx ? a1 : a0, ny + 2 * (fx & fz));
         const T p1 = rot_i(fx ? a0 : a1, ny + 2 * ((1 ^ fx) & fz));
         zr += b0.x * p0.x + b0.y * p0.y + b1.x * p1.x + b1.y * p1.y;
         zi += b0.x * p0.y - b0.y * p0.x + b1.x * p1.y - b1.y * p1.x;
-        T o0, o1;
-        o0.x = o0.y = o1.x = o1.y = 0;
-        cmac(o0, m00, a0); cmac(o0, m01, a1); cmac(o1, m10, a0); cmac(o1, m11, a1);
+        T o0, o1, c0, c1;
+        if constexpr (FORM == ADJ1_DIAG) {
+            o0 = cmul(m00, a0);
+            o1 = cmul(m11, a1);
+            c0 = cmul(m00, b0);
+            c1 = cmul(m11, b1);
+        } else if constexpr (FORM == ADJ1_REAL) {
+            o0.x = m00.x * a0.x + m01.x * a1.x;
+            o0.y = m00.x * a0.y + m01.x * a1.y;
+            o1.x = m10.x * a0.x + m11.x * a1.x;
+            o1.y = m10.x * a0.y + m11.x * a1.y;
+            c0.x = m00.x * b0.x + m01.x * b1.x;
+            c0.y = m00.x * b0.y + m01.x * b1.y;
+            c1.x = m10.x * b0.x + m11.x * b1.x;
+            c1.y = m10.x * b0.y + m11.x * b1.y;
+        } else {
+            o0.x = o0.y = o1.x = o1.y = 0;
+            cmac(o0, m00, a0); cmac(o0, m01, a1); cmac(o1, m10, a0); cmac(o1, m11, a1);
+            c0.x = c0.y = c1.x = c1.y = 0;
+            cmac(c0, m00, b0); cmac(c0, m01, b1); cmac(c1, m10, b0); cmac(c1, m11, b1);
+        }
         tp[i0] = o0;
         tp[i1] = o1;
-        o0.x = o0.y = o1.x = o1.y = 0;
-        cmac(o0, m00, b0); cmac(o0, m01, b1); cmac(o1, m10, b0); cmac(o1, m11, b1);
-        tl[i0] = o0;
-        tl[i1] = o1;
+        tl[i0] = c0;
+        tl[i1] = c1;
     }
 }
 
-// diagonal U^dagger on both tiles in one sweep
+// Single-qubit unit with a parameter: accumulate <lambda|P|psi> and apply
+// U^dagger to psi and lambda in the same sweep (the thread holds both
+// amplitudes of each pair of both states).  P's letter: flip fx (X, Y),
+// sign fz (Z, Y), ny factors of i.
+template <typename T, typename R>
+__device__ __forceinline__ void adj_1q_grad_apply(T* tp, T* tl, int L, int q, const T* m, int form, int fx, int fz,
+                                                  int ny, R& zr, R& zi) {
+    if (form == ADJ1_DIAG) adj_1q_grad_apply_f<T, R, ADJ1_DIAG>(tp, tl, L, q, m, fx, fz, ny, zr, zi);
+    else if (form == ADJ1_REAL) adj_1q_grad_apply_f<T, R, ADJ1_REAL>(tp, tl, L, q, m, fx, fz, ny, zr, zi);
+    else adj_1q_grad_apply_f<T, R, ADJ1_DENSE>(tp, tl, L, q, m, fx, fz, ny, zr, zi);
+}
+
+// diagonal U^dagger on both tiles in one sweep; phases +-1 / +-i (CZ, S,
+// Z, ...) are applied as swaps and negations without multiplications
 template <typename T>
-__device__ __forceinline__ void adj_diag_both(T* tp, T* tl, int L, const TileGate& g, const T* m) {
+__device__ __forceinline__ void adj_diag_both(T* tp, T* tl, int L, const TileGate& g, const T* m, bool mulfree) {
     const int k = g.k, D = 1 << k;
     for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
         int l = 0;
         for (int i = 0; i < k; ++i) l = (l << 1) | ((e >> g.q[i]) & 1);
         const T ph = m[l * D + l];
-        tp[e] = cmul(ph, tp[e]);
-        tl[e] = cmul(ph, tl[e]);
+        if (mulfree) {
+            const int code = ph.x == 1 ? 0 : ph.y == 1 ? 1 : ph.x == -1 ? 2 : 3;
+            tp[e] = rot_i(tp[e], code);
+            tl[e] = rot_i(tl[e], code);
+        } else {
+            tp[e] = cmul(ph, tp[e]);
+            tl[e] = cmul(ph, tl[e]);
+        }
     }
 }
 
@@ -395,7 +435,7 @@ __global__ void __launch_bounds__(256) k_adj_tile(typename C2<R>::T* __restrict_
                 // fused: gradient and U^dagger in one sweep, one barrier
                 const int q = g.q[0];
                 R zr = 0, zi = 0;
-                adj_1q_grad_apply<T, R>(tp, tl, L, q, m, (ag.px >> q) & 1, (ag.pz >> q) & 1, ag.ny, zr, zi);
+                adj_1q_grad_apply<T, R>(tp, tl, L, q, m, ag.form, (ag.px >> q) & 1, (ag.pz >> q) & 1, ag.ny, zr, zi);
                 const double sr = warp_sum((double)zr), si = warp_sum((double)zi);
                 if ((threadIdx.x & 31) == 0) {
                     double2& w = acc[gi * 8 + (threadIdx.x >> 5)];
@@ -425,7 +465,7 @@ __global__ void __launch_bounds__(256) k_adj_tile(typename C2<R>::T* __restrict_
                 __syncthreads();  // psi/lambda reads above finish before the gate rewrites them
             }
             if (g.kind == QS_GATE_DIAGONAL) {
-                adj_diag_both(tp, tl, L, g, m);
+                adj_diag_both(tp, tl, L, g, m, ag.mulfree != 0);
             } else {
                 switch (g.k) {
                     case 1: tile_dense<T, 1>(tp, L, g, m); tile_dense<T, 1>(tl, L, g, m); break;
