@@ -31,6 +31,16 @@ sys.path.insert(0, ROOT)
 METRIC = "circuit wall time & HBM GB/s at 30–32q; adjoint-gradient time vs forward"
 FALLBACK_HBM_GBS = 6800.0
 
+# DRAM bytes (read + write) per amplitude of one launch, from the ncu
+# captures summarised in profiles/ (26-qubit complex64 cases; traffic grows
+# in proportion to the amplitudes, so a launch at n qubits moves
+# bytes_per_amp * 2^n).  Must be cleared when the kernel changes.
+NCU_TRAFFIC_PER_AMP_C64 = {
+    "tensor": (536.995328e6 + 474.646016e6) / (1 << 26),   # k_gemm6_grid26_3xtf32.md
+    "tile": None,
+    "dense": None,
+}
+
 
 def parse_args(argv=None):
     ap = argparse.ArgumentParser()
@@ -47,6 +57,10 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="auto",
                     help="fp32 | 3xtf32 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of fp32 and 3xtf32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--unfused", action="store_true", help="one pass per gate (no fusion, no tiles)")
+    ap.add_argument("--circuit", choices=["grid", "grid_fixed", "ansatz"], default="grid",
+                    help="grid: random fSim angles; grid_fixed: fSim(pi/2, pi/6) everywhere (permutation-with-"
+                         "phase gates); ansatz: RY/RZ layers with CZ ladders (diagonal gates)")
     ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "precision"], default="grid",
                     help="grid: the headline circuit; adjoint: gradient vs forward on the ansatz; "
                          "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q")
@@ -56,6 +70,10 @@ def parse_args(argv=None):
 
 
 def workload_name(a):
+    if a.circuit == "ansatz":
+        return f"ansatz{a.n}_L{a.layers}_seed{a.seed}_{a.dtype}"
+    if a.circuit == "grid_fixed":
+        return f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_pi2_pi6_seed{a.seed}_{a.dtype}"
     return f"grid{a.n}_5x6_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}" if a.n == 30 else \
         f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}"
 
@@ -188,13 +206,23 @@ def run_own(a):
     pkg.load()
     esz = 8 if a.dtype == "c64" else 16
     state_bytes = (1 << a.n) * esz
-    circ = C.scale_grid_circuit(a.n, a.cycles, a.seed)
+    if a.circuit == "ansatz":
+        circ = C.ansatz_circuit(a.n, a.layers, C.ansatz_theta(a.n, a.layers, a.seed))
+    elif a.circuit == "grid_fixed":
+        circ = C.grid_circuit(a.n, a.cycles, a.seed, fixed_fsim=(math.pi / 2, math.pi / 6))
+    else:
+        circ = C.scale_grid_circuit(a.n, a.cycles, a.seed)
     c = B.circuit_from(circ)
     state = B.State(a.n, a.dtype)
     stream = torch.cuda.current_stream()
 
+    def plan_for(circuit, k, prec):
+        if a.unfused:
+            return B.Plan(circuit, a.dtype, k_max=1, fuse=False, use_tile=False, precision=prec)
+        return B.Plan(circuit, a.dtype, k_max=k, tile_qubits=a.tile, use_tile=True, precision=prec)
+
     def make_plan(k, prec):
-        return B.Plan(c, a.dtype, k_max=k, tile_qubits=a.tile, use_tile=True, precision=prec)
+        return plan_for(c, k, prec)
 
     # pick (k_max, precision) by timing one execution of each candidate
     # (excluded from the timed region); only modes at FP32-level accuracy
@@ -207,7 +235,7 @@ def run_own(a):
             if pr != "fp32" and k < 5:
                 continue
             cands.append((k, pr))
-    if len(cands) == 1:
+    if len(cands) == 1 or a.unfused:
         k_best, prec_best = cands[0]
     else:
         best = None
@@ -294,8 +322,7 @@ def run_own(a):
         h2d = d2h = 0
         for _ in range(e2e_steps):
             cc = B.circuit_from(circ)                    # host gate list -> library
-            pp = B.Plan(cc, a.dtype, k_max=k_best, tile_qubits=a.tile, use_tile=True,
-                        precision=prec_best)             # fuse + upload
+            pp = plan_for(cc, k_best, prec_best)        # fuse + upload
             state.init_basis(0)
             pp.execute(state)
             nrm = state.norm()                           # D2H 8 bytes
@@ -330,9 +357,13 @@ def run_own(a):
             "hbm_gbs_effective": step_bytes / (ms_step * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": None, "avg_launch_ms": avg_ms,
+                         "traffic": (NCU_TRAFFIC_PER_AMP_C64[dom] * (1 << a.n)
+                                     if a.dtype == "c64" and NCU_TRAFFIC_PER_AMP_C64.get(dom) else None),
+                         "avg_launch_ms": avg_ms,
                          "algorithmic_bytes_per_launch": 2 * state_bytes},
-            "pass_time_ms": {k: {"launches_per_step": v[1] / a.steps, "total_ms_per_step": v[0] / a.steps}
+            "pass_time_ms": {k: {"launches_per_step": v[1] / a.steps, "total_ms_per_step": v[0] / a.steps,
+                                 "avg_launch_ms": v[0] / v[1],
+                                 "hbm_frac": 2 * state_bytes / (v[0] / v[1] * 1e-3) / 1e9 / peak}
                              for k, v in by_kind.items()},
             "norm_last": norms[-1],
             "gpu_launches": a.steps * (1 + npass + 2),

@@ -82,14 +82,19 @@ typedef struct qs_pauli_sum qs_pauli_sum;
  *                 otherwise 6..13 (c64) / 6..12 (c128).
  *   use_tile    : 1 = group consecutive gates on tile qubits into one pass.
  *   precision   : qs_precision for dense k >= 5 gates on complex64.
- *   fuse        : 1 = run qs_fuse(k_max) inside qs_plan_create.          */
+ *   fuse        : 1 = run qs_fuse(k_max) inside qs_plan_create.
+ *   inject_wait_timeout : testing only, batches: 1 = the last pass of the
+ *                 last wide circuit waits for a count that is never reached,
+ *                 so its bounded device wait runs out (~2 s) and
+ *                 qs_batch_sync reports QS_ERR_TIMEOUT.  0 in normal use.  */
 typedef struct qs_options {
     int k_max;
     int tile_qubits;
     int use_tile;
     int precision;
     int fuse;
-    int reserved[8];
+    int inject_wait_timeout;
+    int reserved[7];
 } qs_options;
 
 const char* qs_version(void);

@@ -33,7 +33,8 @@ class QsError(RuntimeError):
 
 class Options(ct.Structure):
     _fields_ = [("k_max", ct.c_int), ("tile_qubits", ct.c_int), ("use_tile", ct.c_int),
-                ("precision", ct.c_int), ("fuse", ct.c_int), ("reserved", ct.c_int * 8)]
+                ("precision", ct.c_int), ("fuse", ct.c_int), ("inject_wait_timeout", ct.c_int),
+                ("reserved", ct.c_int * 7)]
 
 
 _P = ct.c_void_p
@@ -144,9 +145,10 @@ def _stream_ptr(stream=None) -> int:
 
 
 def options(k_max: int = 4, tile_qubits: int = 0, use_tile: bool = True, precision="fp32",
-            fuse: bool = True) -> Options:
+            fuse: bool = True, inject_wait_timeout: bool = False) -> Options:
     o = Options()
     _call("qs_options_default", ct.byref(o))
+    o.inject_wait_timeout = 1 if inject_wait_timeout else 0
     o.k_max = int(k_max)
     o.tile_qubits = int(tile_qubits)
     o.use_tile = 1 if use_tile else 0

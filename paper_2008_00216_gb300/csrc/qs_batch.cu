@@ -338,6 +338,15 @@ qs_status qs_batch_create(const qs_circuit* const* circuits, int count, qs_dtype
         }
         circs[c].npass = (int)tp.size();
     }
+    if (opt.inject_wait_timeout) {
+        // testing: the last pass of the last wide circuit waits for a count
+        // that is never reached, so its bounded wait runs out
+        for (int c = count - 1; c >= 0; --c)
+            if (circs[c].npass > 1) {
+                passes[circs[c].pass0 + circs[c].npass - 1].items_before = 0xFFFFFFFFu;
+                break;
+            }
+    }
     // queue: the whole-in-one-CTA circuits, most expensive first, then the
     // wide circuits' items pass-major across circuits
     std::sort(small_cost.begin(), small_cost.end(), [](auto& x, auto& y) { return x.first > y.first; });

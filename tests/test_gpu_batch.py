@@ -60,3 +60,22 @@ def test_batch_autotune(qs):
     bt.run(); bt.sync()
     s = specs[-1]
     assert rel_l2(bt.state(len(specs) - 1).cpu().numpy(), oracle.simulate(s.n, s.gates)) < 2e-5
+
+
+def test_bounded_wait_timeout_is_reported(qs):
+    """A work item whose dependency count is never reached (injected through
+    the testing option) gives up after its bounded wait; the host reads
+    QS_ERR_TIMEOUT and the context stays usable."""
+    specs = _workload(6, 11, (10, 12), (3, 5))
+    circs = [B.circuit_from(s) for s in specs]
+    bad = B.Batch(circs, "c64", k_max=2, tile_qubits=8, inject_wait_timeout=True)
+    bad.run()
+    with pytest.raises(B.QsError) as e:
+        bad.sync()
+    assert e.value.status == 5
+    bad.close()
+    good = B.Batch(circs, "c64", k_max=2, tile_qubits=8)
+    good.run()
+    good.sync()
+    s = specs[0]
+    assert rel_l2(good.state(0).cpu().numpy(), oracle.simulate(s.n, s.gates)) < 2e-5
