@@ -2,24 +2,32 @@
 //
 // A fused k-qubit gate applies the same 2^k x 2^k complex matrix U to each
 // of the 2^(n-k) disjoint sets of 2^k amplitudes (Section 3), i.e. it is the
-// product U X with X = 2^k x 2^(n-k).  With real arithmetic:
-//   D = [Re U; Im U] (128 x 64)  x  B^T,   B = [re x_s; im x_s] per set s,
-//   y_s = (D_re-rows . re-col - D_im-rows . im-col) + i (...).
-// A (the gate, split into hi/lo parts) stays resident in tensor memory for
-// the whole kernel; B (K-major, K = the gate's 64 local indices, 128-byte
-// swizzle) is streamed through shared memory; the accumulator D (128 lanes x
-// 64 FP32 columns per tile of 32 sets) is double-buffered in tensor memory.  Precision modes on complex64 states:
+// product Y = X U^T with X = the 2^(n-k) x 2^k matrix whose rows are the
+// sets.  In real arithmetic, for a tile of 64 sets:
+//   D = A G^T,  A = [re x_s ; im x_s] (128 rows: set s, re/im; K = the 64
+//   local indices),  G = [Re U row r ; Im U row r] (128 rows n = 2r + h),
+//   y_s[r] = (D[s,re][2r] - D[s,im][2r+1]) + i (D[s,im][2r] + D[s,re][2r+1]).
+// The state tile is the A operand and lives in tensor memory: producers
+// write it there from registers (tcgen05.st), so the state never passes
+// through shared memory on its way in.  The gate (split into hi/lo parts)
+// is the B operand, resident in shared memory (128-byte swizzle, K-major)
+// for the whole kernel.  D (128 lanes x 128 FP32 columns) is read back by
+// the epilogue, which combines real and imaginary rows with one exchange
+// between lane pairs and stores each set's outputs straight to HBM.
+// Precision modes on complex64 states:
 //   TF32     one product, operands rounded to TF32
-//   3xTF32   A_hi B_hi + A_hi B_lo + A_lo B_hi, hi = TF32(x), lo = x - hi
+//   3xTF32   A_lo G_hi + A_hi G_lo + A_hi G_hi, hi = TF32(x), lo = x - hi
 //   3xBF16   the same split with bfloat16 parts
 // all with FP32 accumulation.
 //
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-3  epilogue: tensor memory -> registers -> recombine -> HBM
-//   warps 4-11 producer: cp.async gathers of 32 sets x 64 amplitudes
-//              (coalesced) several tiles ahead into a raw ring, then the
-//              hi/lo split into the swizzled shared-memory stages
+//   warps 0-3  epilogue: warp q owns TMEM lanes 32q..32q+31 (sets 16q..16q+15)
+//   warps 4-11 producer: warp w owns the lanes of quadrant w % 4 and half of
+//              the local indices; it gathers them with cp.async (16-byte
+//              pairs, coalesced) several tiles ahead into its own slice of a
+//              shared-memory ring, then rounds/splits them into tensor memory
 //   warp 12    one thread issues the MMAs and commits to mbarriers
+// Tensor memory: two A buffers (hi | lo) and two accumulators, 512 columns.
 // Every mbarrier wait is bounded (about two seconds of clock64); on timeout
 // the CTA sets the error flag, drains its MMAs, frees tensor memory, exits.
 #include <cuda_bf16.h>
@@ -33,17 +41,14 @@
 namespace qsgb {
 namespace tc {
 
-constexpr int kSets = 32;          // sets (N/2) per tile
-constexpr int kRowsB = 2 * kSets;  // B rows: (set, re/im)
-constexpr int kStages = 2;         // split, swizzled B stages
+constexpr int kSets = 64;          // sets per tile: TMEM lane 32q + 16c + j = (set 16q + j, re/im c)
+constexpr int kN = 128;            // MMA N: gate rows (r, Re/Im)
 constexpr int kEpiWarps = 4, kProdWarps = 8;
-constexpr int kProdThreads = 32 * kProdWarps;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
-// tensor memory: A_hi | A_lo (64 columns each for TF32, 32 for packed BF16)
-// then two 64-column FP32 accumulators
-constexpr int kTmemCols = 256;
-constexpr int kTmemD = 128;
+constexpr int kTmemCols = 512;
+constexpr int kTmemABuf = 128;     // columns per A buffer (hi | lo)
+constexpr int kTmemD = 256;        // two accumulators of kN columns
 constexpr long long kTimeout = 4ll << 30;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -82,16 +87,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-// Barrier among the threads of one role (init count = role size), built on an
-// mbarrier so a wait is bounded: a role whose member left on an error path
-// times out instead of hanging.  The result is made warp-uniform.
-__device__ __forceinline__ bool group_sync(uint64_t* bar, uint32_t& phase, int* err, volatile int* abort_flag) {
-    mbar_arrive(bar);
-    const bool ok = mbar_wait(bar, phase, err, abort_flag);
-    phase ^= 1u;
-    return __all_sync(0xffffffffu, ok);
-}
-
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart (SBO); the leading offset is unused for this layout
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
@@ -104,15 +99,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
 }
 
 // instruction descriptor: FP32 accumulate, A/B TF32 (kind 0) or BF16
-// (kind 1), both K-major, M = 128, N = 64
+// (kind 1), both K-major, M = 128, N = kN
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc() {
-    return (1u << 4) | ((KIND == 0 ? 2u : 1u) << 7) | ((KIND == 0 ? 2u : 1u) << 10) | ((uint32_t)(kRowsB >> 3) << 17) |
+    return (1u << 4) | ((KIND == 0 ? 2u : 1u) << 7) | ((KIND == 0 ? 2u : 1u) << 10) | ((uint32_t)(kN >> 3) << 17) |
            ((uint32_t)(128 >> 4) << 24);
 }
 
-// D[tmem] (+)= A[tmem] * B[smem]^T: A is read from tensor memory (row m in
-// lane m, K along columns), so only B is streamed from shared memory
+// D[tmem] (+)= A[tmem] * B[smem]^T: A (the state tile) is read from tensor
+// memory (row m in lane m, K along columns), B (the gate) from shared memory
 template <int KIND>
 __device__ __forceinline__ void umma_ts(uint32_t d, uint32_t a_tmem, uint64_t b, uint32_t acc) {
     if constexpr (KIND == 0) {
@@ -155,10 +150,19 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* r) {
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// x rounded to TF32 (10 explicit mantissa bits), to nearest with ties away
+// from zero: add half of the lowest kept bit to the magnitude, clear the 13
+// dropped bits (a carry into the exponent is the correct result).  Same as
+// cvt.rna.tf32.f32 for finite x, in two integer operations.
+__device__ __forceinline__ float tf32_round(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// index of the first amplitude of set x (zero bits inserted at the targets)
+__device__ __forceinline__ uint64_t set_base(uint64_t x, const int* sorted) {
+#pragma unroll
+    for (int b = 0; b < 6; ++b) x = insert_zero(x, sorted[b]);
+    return x;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -175,29 +179,31 @@ struct Args {
     uint64_t off[64];   // offset of local index l; the gate's qubits are in
                         // descending order, so local bit b is the b-th lowest target
     int sorted[6];      // target bits ascending
-    uint64_t ntiles;    // 2^(n-6) / 32
+    uint64_t ntiles;    // 2^(n-6) / 64
 };
 
-// Q0T: qubit 0 is a target.  Then amplitude pairs (l, l+1), l even, are
-// adjacent in memory; otherwise set pairs (s, s+1), s even, are.  Either way
-// every gather and write-back moves 16-byte pairs.
 template <int SPLITS, int KIND>
 struct Layout {
-    static constexpr int kAtomsK = KIND == 0 ? 2 : 1;           // 64 K elements
-    static constexpr int kBBytes = kAtomsK * kRowsB * 128;       // one B split, one stage
     static constexpr int SPLITS_A = SPLITS == 3 ? 2 : 1;        // stored parts (hi, lo)
     static constexpr int kACols = KIND == 0 ? 64 : 32;          // TMEM columns of one A part
-    static constexpr int kB = 0;
-    static constexpr int kStageBytes = SPLITS_A * kBBytes;
-    static constexpr int kRaw = 6;                               // gathered tiles in flight
-    static constexpr int kRawBytes = 32 * 66 * 8;                // [64][32] or [32][66] float2
-    static constexpr int kR = kB + kStages * kStageBytes;
-    static constexpr int kY = kR + kRaw * kRawBytes;             // [64][34] or [32][66] float2
-    static constexpr int kYBytes = 32 * 68 * 8;
-    static constexpr int kOff = kY + kYBytes;                    // offsets (64 x u64)
-    static constexpr int kBar = kOff + 64 * 8;                   // barriers
+    static constexpr int kAtomsK = KIND == 0 ? 2 : 1;           // 128-byte atoms along K
+    static constexpr int kGBytes = kAtomsK * kN * 128;          // one gate part
+    static constexpr int kG = 0;
+    static constexpr int kRaw = 4;                               // gathered tiles in flight
+    // one producer warp's slice of a raw slot: 16 sets x 32 local indices,
+    // [32 l][16 sets] float2, or with qubit 0 a target [16 sets][34] float2
+    // (the padding spreads the rows over the banks)
+    static constexpr int kWarpRaw = 16 * 34 * 8;
+    static constexpr int kSlot = kProdWarps * kWarpRaw;
+    static constexpr int kR = kG + SPLITS_A * kGBytes;
+    static constexpr int kBar = kR + kRaw * kSlot;               // barriers
     static constexpr int kTotal = kBar + 128;
 };
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    tmem_ld16(taddr, v);
+    tmem_ld16(taddr + 16, v + 16);
+}
 
 template <int SPLITS, int KIND, bool Q0T>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -207,31 +213,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    uint64_t* full = reinterpret_cast<uint64_t*>(sm + LY::kBar);
-    uint64_t* empty = full + kStages;
-    uint64_t* dfull = empty + kStages;
+    uint64_t* afull = reinterpret_cast<uint64_t*>(sm + LY::kBar);
+    uint64_t* aempty = afull + 2;
+    uint64_t* dfull = aempty + 2;
     uint64_t* dempty = dfull + 2;
     uint64_t* drain = dempty + 2;
-    uint64_t* prodbar = drain + 1;
-    uint64_t* epibar = prodbar + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(epibar + 1);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    uint64_t* soff = reinterpret_cast<uint64_t*>(sm + LY::kOff);
-    float2* ystage = reinterpret_cast<float2*>(sm + LY::kY);
 
-    for (int i = threadIdx.x; i < 64; i += blockDim.x) soff[i] = a.off[i];
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], kProdThreads);
-            mbar_init(&empty[s], 1);
-        }
-        for (int s = 0; s < 2; ++s) {
-            mbar_init(&dfull[s], 1);
-            mbar_init(&dempty[s], 32 * kEpiWarps);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&afull[b], kProdWarps);
+            mbar_init(&aempty[b], 1);
+            mbar_init(&dfull[b], 1);
+            mbar_init(&dempty[b], kEpiWarps);
         }
         mbar_init(drain, 1);
-        mbar_init(prodbar, kProdThreads);
-        mbar_init(epibar, 32 * kEpiWarps);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -241,193 +238,164 @@ __global__ void __launch_bounds__(kThreads, 1)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // ---- the gate into shared memory: row n = 2r + h holds (h ? Im : Re) U[r][:],
+    // hi part then lo part, K-major with the 128-byte swizzle
+    for (int idx = threadIdx.x; idx < kN * 64; idx += blockDim.x) {
+        const int n = idx >> 6, k = idx & 63, r = n >> 1, h = n & 1;
+        const float v = h ? U[r * 64 + k].y : U[r * 64 + k].x;
+        if constexpr (KIND == 0) {
+            const uint32_t o = (uint32_t)((k >> 5) * (kN * 128)) + swz(n, (k & 31) >> 2) + 4u * (uint32_t)(k & 3);
+            const float hi = tf32_round(v);
+            *reinterpret_cast<float*>(sm + LY::kG + o) = hi;
+            if constexpr (SPLITS == 3) *reinterpret_cast<float*>(sm + LY::kG + LY::kGBytes + o) = tf32_round(v - hi);
+        } else {
+            const uint32_t o = swz(n, k >> 3) + 2u * (uint32_t)(k & 7);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(sm + LY::kG + o) = hi;
+            if constexpr (SPLITS == 3)
+                *reinterpret_cast<__nv_bfloat16*>(sm + LY::kG + LY::kGBytes + o) = __float2bfloat16_rn(v - __bfloat162float(hi));
+        }
+    }
+    fence_async_smem();
     tc_before();
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
 
-    // ---- A into tensor memory: row m = 32q + 16h + rr holds (h ? Im : Re)
-    // U[16q + rr][:], so each epilogue warp owns the real and imaginary rows
-    // of 16 outputs.  Warp q writes lanes 32q..32q+31, 16 columns at a time.
-    if (warp < kEpiWarps) {
-        const int m = threadIdx.x;
-        const int r = 16 * (m >> 5) + (m & 15), h = (m >> 4) & 1;
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+    if (warp >= kEpiWarps && warp < kMmaWarp) {
+        // ================= producer: TMEM quadrant q, local indices 32kh..32kh+31
+        const int pw = warp - kEpiWarps, q = warp & 3, kh = pw >> 2;
+        const int j = lane & 15, c = lane >> 4;  // this lane's TMEM row: set 16q + j, part c
+        unsigned char* slice = sm + LY::kR + pw * LY::kWarpRaw;
+        // per-lane constant part of the eight gather addresses and their
+        // destinations (float2 units within the warp's slice)
+        uint64_t goff[8];
+        int gdst[8];
+        if constexpr (Q0T) {
+            // lane -> set 16q + (lane & 15); copy i moves the pair (l, l+1),
+            // l = 32kh + 2p, p = (lane >> 4) + 2i
+            const uint64_t pj = set_base((uint64_t)(16 * q + j), a.sorted);
 #pragma unroll
-        for (int part = 0; part < LY::SPLITS_A; ++part) {
+            for (int i = 0; i < 8; ++i) {
+                const int p = c + 2 * i;
+                goff[i] = pj + a.off[32 * kh + 2 * p];
+                gdst[i] = j * 34 + 2 * p;
+            }
+        } else {
+            // lane -> the set pair 16q + 2sp, +1 of one l = 32kh + kl,
+            // kl = (lane >> 3) + 4i
+            const int sp = lane & 7;
+            const uint64_t pj = set_base((uint64_t)(16 * q + 2 * sp), a.sorted);
 #pragma unroll
-            for (int cb = 0; cb < LY::kACols / 16; ++cb) {
-                uint32_t w16[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    if constexpr (KIND == 0) {
-                        const int l = 16 * cb + c;
-                        const float v = h ? U[r * 64 + l].y : U[r * 64 + l].x;
-                        const float hi = tf32_rna(v);
-                        w16[c] = __float_as_uint(part == 0 ? hi : tf32_rna(v - hi));
-                    } else {  // two bf16 per column, lower K index in the low half
-                        const int l = 2 * (16 * cb + c);
-                        const float v0 = h ? U[r * 64 + l].y : U[r * 64 + l].x;
-                        const float v1 = h ? U[r * 64 + l + 1].y : U[r * 64 + l + 1].x;
-                        __nv_bfloat16 b0 = __float2bfloat16_rn(v0), b1 = __float2bfloat16_rn(v1);
-                        if (part == 1) {
-                            b0 = __float2bfloat16_rn(v0 - __bfloat162float(b0));
-                            b1 = __float2bfloat16_rn(v1 - __bfloat162float(b1));
-                        }
-                        w16[c] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-                    }
-                }
-                tmem_st16(lane_base + (uint32_t)(part * LY::kACols + 16 * cb), w16);
+            for (int i = 0; i < 8; ++i) {
+                const int kl = (lane >> 3) + 4 * i;
+                goff[i] = pj + a.off[32 * kh + kl];
+                gdst[i] = kl * 16 + 2 * sp;
             }
         }
-        tmem_st_wait();
-    }
-    tc_before();
-    __syncthreads();
-    tc_after();
-
-    if (warp >= kEpiWarps && warp < kMmaWarp) {
-        // ================= producer
-        // (1) cp.async gathers tile it+kRaw-1 into a raw ring slot while
-        // (2) tile it, already in shared memory, is split and written into
-        //     the swizzled stage the MMA reads.
-        const int ptid = threadIdx.x - 32 * kEpiWarps, pw = ptid >> 5;
-        unsigned char* raw = sm + LY::kR;
         auto issue = [&](uint64_t itx) {
             const uint64_t tt = blockIdx.x + itx * gridDim.x;
             if (tt < a.ntiles) {
-                float2* slot = reinterpret_cast<float2*>(raw + (itx % LY::kRaw) * LY::kRawBytes);
-                if constexpr (Q0T) {
-                    // pairs (l, l+1) of one set; a warp reads one whole set
-                    const int lp = ptid & 31;
+                float2* dstp = reinterpret_cast<float2*>(slice + (itx % LY::kRaw) * LY::kSlot);
+                const float2* src = psi + set_base(tt * kSets, a.sorted);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int jj = (ptid >> 5) + 8 * i;
-                        uint64_t base = tt * kSets + jj;
-#pragma unroll
-                        for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
-                        cp_async16(slot + jj * 66 + 2 * lp, psi + base + soff[2 * lp]);
-                    }
-                } else {
-                    // pairs (s, s+1) of one local index; a warp reads 2 rows
-                    const int sp = ptid & 15;
-                    uint64_t base = tt * kSets + 2 * sp;
-#pragma unroll
-                    for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const int l = (ptid >> 4) + 16 * i;
-                        cp_async16(slot + l * 32 + 2 * sp, psi + base + soff[l]);
-                    }
-                }
+                for (int i = 0; i < 8; ++i) cp_async16(dstp + gdst[i], src + goff[i]);
             }
             cp_async_commit();  // one group per tile, possibly empty
         };
         for (int p = 0; p < LY::kRaw - 1; ++p) issue((uint64_t)p);
-        // conversion unit: (set j, chunk Q of 4 (TF32) or 8 (BF16) local indices)
-        const int j = (ptid & 15) + 16 * (pw & 1), lsel = (ptid >> 4) & 1, lg = pw >> 1;
-        uint32_t gph = 0;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
         for (uint64_t it = 0;; ++it) {
             const uint64_t t = blockIdx.x + it * gridDim.x;
             if (t >= a.ntiles) break;
             issue(it + LY::kRaw - 1);
             cp_async_wait<LY::kRaw - 1>();
-            // every producer's copies of tile `it` have landed
-            if (!group_sync(prodbar, gph, err, abort_flag)) break;
-            const int stage = (int)(it % kStages);
-            const uint32_t ph = (uint32_t)((it / kStages) & 1);
-            if (!__all_sync(0xffffffffu, mbar_wait(&empty[stage], ph ^ 1, err, abort_flag))) break;
-            const float2* rs = reinterpret_cast<const float2*>(raw + (it % LY::kRaw) * LY::kRawBytes);
-            auto rawat = [&](int l) { return Q0T ? rs[j * 66 + l] : rs[l * 32 + j]; };
-            unsigned char* bst = sm + LY::kB + stage * LY::kStageBytes;
-            if constexpr (KIND == 0) {
+            __syncwarp();  // the warp's copies of tile `it` are visible to all its lanes
+            const int b = (int)(it & 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(&aempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag))) break;
+            tc_after();
+            const float2* rs = reinterpret_cast<const float2*>(slice + (it % LY::kRaw) * LY::kSlot);
+            float v[32];  // part c of x[set][32kh + kl], kl = 0..31
+            if constexpr (Q0T) {
 #pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const int Q = lsel + 2 * lg + 8 * i;  // 4 consecutive local indices
-                    float2 x[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) x[e] = rawat(4 * Q + e);
-                    const int atom = Q >> 3, q = Q & 7;
-                    float4 rh, ih, rl, il;
-                    rh.x = tf32_rna(x[0].x); rh.y = tf32_rna(x[1].x); rh.z = tf32_rna(x[2].x); rh.w = tf32_rna(x[3].x);
-                    ih.x = tf32_rna(x[0].y); ih.y = tf32_rna(x[1].y); ih.z = tf32_rna(x[2].y); ih.w = tf32_rna(x[3].y);
-                    const uint32_t o_re = atom * (kRowsB * 128) + swz(2 * j, q);
-                    const uint32_t o_im = atom * (kRowsB * 128) + swz(2 * j + 1, q);
-                    *reinterpret_cast<float4*>(bst + o_re) = rh;
-                    *reinterpret_cast<float4*>(bst + o_im) = ih;
-                    if constexpr (SPLITS == 3) {
-                        rl.x = tf32_rna(x[0].x - rh.x); rl.y = tf32_rna(x[1].x - rh.y);
-                        rl.z = tf32_rna(x[2].x - rh.z); rl.w = tf32_rna(x[3].x - rh.w);
-                        il.x = tf32_rna(x[0].y - ih.x); il.y = tf32_rna(x[1].y - ih.y);
-                        il.z = tf32_rna(x[2].y - ih.z); il.w = tf32_rna(x[3].y - ih.w);
-                        *reinterpret_cast<float4*>(bst + LY::kBBytes + o_re) = rl;
-                        *reinterpret_cast<float4*>(bst + LY::kBBytes + o_im) = il;
-                    }
+                for (int p = 0; p < 16; ++p) {
+                    const float4 pr = *reinterpret_cast<const float4*>(rs + j * 34 + 2 * p);
+                    v[2 * p] = c ? pr.y : pr.x;
+                    v[2 * p + 1] = c ? pr.w : pr.z;
                 }
             } else {
-                const int Q = lsel + 2 * lg;  // 8 consecutive local indices
-                float2 x[8];
 #pragma unroll
-                for (int e = 0; e < 8; ++e) x[e] = rawat(8 * Q + e);
-                uint32_t rh[4], ih[4], rl[4], il[4];
-#pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const __nv_bfloat16 r0 = __float2bfloat16_rn(x[2 * e].x), r1 = __float2bfloat16_rn(x[2 * e + 1].x);
-                    const __nv_bfloat16 i0 = __float2bfloat16_rn(x[2 * e].y), i1 = __float2bfloat16_rn(x[2 * e + 1].y);
-                    rh[e] = (uint32_t)__bfloat16_as_ushort(r0) | ((uint32_t)__bfloat16_as_ushort(r1) << 16);
-                    ih[e] = (uint32_t)__bfloat16_as_ushort(i0) | ((uint32_t)__bfloat16_as_ushort(i1) << 16);
-                    if constexpr (SPLITS == 3) {
-                        const __nv_bfloat16 a0 = __float2bfloat16_rn(x[2 * e].x - __bfloat162float(r0));
-                        const __nv_bfloat16 a1 = __float2bfloat16_rn(x[2 * e + 1].x - __bfloat162float(r1));
-                        const __nv_bfloat16 b0 = __float2bfloat16_rn(x[2 * e].y - __bfloat162float(i0));
-                        const __nv_bfloat16 b1 = __float2bfloat16_rn(x[2 * e + 1].y - __bfloat162float(i1));
-                        rl[e] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(a1) << 16);
-                        il[e] = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
-                    }
-                }
-                const uint32_t o_re = swz(2 * j, Q), o_im = swz(2 * j + 1, Q);
-                *reinterpret_cast<uint4*>(bst + o_re) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-                *reinterpret_cast<uint4*>(bst + o_im) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-                if constexpr (SPLITS == 3) {
-                    *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_re) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-                    *reinterpret_cast<uint4*>(bst + LY::kBBytes + o_im) = make_uint4(il[0], il[1], il[2], il[3]);
+                for (int kl = 0; kl < 32; ++kl) {
+                    const float2 xv = rs[kl * 16 + j];
+                    v[kl] = c ? xv.y : xv.x;
                 }
             }
-            fence_async_smem();
-            mbar_arrive(&full[stage]);
-            // raw slot of tile `it` is free for tile it+kRaw
-            if (!group_sync(prodbar, gph, err, abort_flag)) break;
+            const uint32_t acol = lane_base + (uint32_t)(b * kTmemABuf);
+            if constexpr (KIND == 0) {
+#pragma unroll
+                for (int hf = 0; hf < 2; ++hf) {
+                    uint32_t hw[16], lw[16];
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const float hi = tf32_round(v[16 * hf + e]);
+                        hw[e] = __float_as_uint(hi);
+                        if constexpr (SPLITS == 3) lw[e] = __float_as_uint(tf32_round(v[16 * hf + e] - hi));
+                    }
+                    tmem_st16(acol + (uint32_t)(32 * kh + 16 * hf), hw);
+                    if constexpr (SPLITS == 3) tmem_st16(acol + (uint32_t)(LY::kACols + 32 * kh + 16 * hf), lw);
+                }
+            } else {  // two bf16 per column, lower K index in the low half
+                uint32_t hw[16], lw[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+                    hw[e] = *reinterpret_cast<const uint32_t*>(&hb);
+                    if constexpr (SPLITS == 3) {
+                        const float2 hf = __bfloat1622float2(hb);
+                        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
+                        lw[e] = *reinterpret_cast<const uint32_t*>(&lb);
+                    }
+                }
+                tmem_st16(acol + (uint32_t)(16 * kh), hw);
+                if constexpr (SPLITS == 3) tmem_st16(acol + (uint32_t)(LY::kACols + 16 * kh), lw);
+            }
+            tmem_st_wait();
+            tc_before();
+            __syncwarp();  // all lanes' tensor-memory writes done; raw slot `it` free again
+            if (lane == 0) mbar_arrive(&afull[b]);
         }
         cp_async_wait<0>();  // nothing of ours still in flight at exit
     } else if (warp == kMmaWarp) {
         // ================= MMA issuer
         if (lane == 0) {
             constexpr int ksteps = KIND == 0 ? 8 : 4;
+            const uint32_t g_base = su32(sm + LY::kG);
             bool issued = false;
             for (uint64_t it = 0;; ++it) {
                 const uint64_t t = blockIdx.x + it * gridDim.x;
                 if (t >= a.ntiles) break;
-                const int stage = (int)(it % kStages), acc = (int)(it & 1);
-                if (!mbar_wait(&full[stage], (uint32_t)((it / kStages) & 1), err, abort_flag)) break;
-                if (!mbar_wait(&dempty[acc], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag)) break;
+                const int b = (int)(it & 1);
+                const uint32_t ph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(&afull[b], ph, err, abort_flag)) break;
+                if (!mbar_wait(&dempty[b], ph ^ 1, err, abort_flag)) break;
                 tc_after();
-                const uint32_t b_base = su32(sm + LY::kB + stage * LY::kStageBytes);
-                const uint32_t d = tmem + (uint32_t)(kTmemD + acc * kRowsB);
-                // products, small terms first: (A_lo, B_hi), (A_hi, B_lo), (A_hi, B_hi)
+                const uint32_t d = tmem + (uint32_t)(kTmemD + b * kN);
+                // products, small terms first: (A_lo, G_hi), (A_hi, G_lo), (A_hi, G_hi)
                 constexpr int nprod = SPLITS == 3 ? 3 : 1;
+#pragma unroll
                 for (int pr = 0; pr < nprod; ++pr) {
                     const int asel = (SPLITS == 3 && pr == 0) ? 1 : 0;
-                    const int bsel = (SPLITS == 3 && pr == 1) ? 1 : 0;
+                    const int gsel = (SPLITS == 3 && pr == 1) ? 1 : 0;
 #pragma unroll
                     for (int kk = 0; kk < ksteps; ++kk) {
                         // 8 TMEM columns per K step (8 TF32, or 16 packed BF16)
-                        const uint32_t a_t = tmem + (uint32_t)(asel * LY::kACols + 8 * kk);
-                        const uint32_t boff = KIND == 0 ? (kk >> 2) * (kRowsB * 128) + (kk & 3) * 32 : kk * 32;
-                        umma_ts<KIND>(d, a_t, sdesc(b_base + bsel * LY::kBBytes + boff), (pr > 0 || kk > 0) ? 1u : 0u);
+                        const uint32_t a_t = tmem + (uint32_t)(b * kTmemABuf + asel * LY::kACols + 8 * kk);
+                        const uint32_t goff = KIND == 0 ? (kk >> 2) * (kN * 128) + (kk & 3) * 32 : kk * 32;
+                        umma_ts<KIND>(d, a_t, sdesc(g_base + gsel * LY::kGBytes + goff), (pr > 0 || kk > 0) ? 1u : 0u);
                     }
                 }
-                umma_commit(&empty[stage]);
-                umma_commit(&dfull[acc]);
+                umma_commit(&aempty[b]);
+                umma_commit(&dfull[b]);
                 issued = true;
             }
             if (issued) {  // drain: wait (bounded, even after an abort) for every MMA issued above
@@ -442,75 +410,58 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // ================= epilogue: warp q owns TMEM lanes 32q..32q+31 =
-        // real rows (lanes 0-15) and imaginary rows (16-31) of outputs
-        // r = 16q + (lane & 15)
-        const int tid = threadIdx.x;  // 0..127
-        const int h = lane >> 4, r = 16 * warp + (lane & 15);
-        uint32_t gph = 0;
+        // ================= epilogue: warp q reads TMEM lanes 32q..32q+31;
+        // lane (c, j) holds row (set 16q + j, part c) of D.  Per chunk of 16
+        // outputs r, the real-part lane finishes the first 8, the imaginary-
+        // part lane the last 8, after one exchange of 16 values.
+        const int q = warp, j = lane & 15, c = lane >> 4;
         for (uint64_t it = 0;; ++it) {
             const uint64_t t = blockIdx.x + it * gridDim.x;
             if (t >= a.ntiles) break;
-            const int acc = (int)(it & 1);
-            if (!__all_sync(0xffffffffu, mbar_wait(&dfull[acc], (uint32_t)((it >> 1) & 1), err, abort_flag))) break;
+            const int b = (int)(it & 1);
+            if (!__all_sync(0xffffffffu, mbar_wait(&dfull[b], (uint32_t)((it >> 1) & 1), err, abort_flag))) break;
             tc_after();
-            float v[64];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kTmemD + acc * kRowsB);
+            float2* dst = psi + set_base(t * kSets + (uint64_t)(16 * q + j), a.sorted);
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTmemD + b * kN);
 #pragma unroll
-            for (int c = 0; c < 4; ++c) tmem_ld16(taddr + 16 * c, v + 16 * c);
-            tmem_ld_wait();
-            tc_before();
-            mbar_arrive(&dempty[acc]);
-            // lane h=0 (real row) finishes sets 0..15, lane h=1 (imaginary row) sets 16..31
-            float w[32];
-#pragma unroll
-            for (int c = 0; c < 32; ++c) w[c] = __shfl_xor_sync(0xffffffffu, h ? v[c] : v[32 + c], 16);
-            float2 y[16];
-            if (h == 0) {  // own = Re-row (sets 0..15), w = Im-row columns 0..31
-#pragma unroll
-                for (int si = 0; si < 16; ++si) {
-                    y[si].x = v[2 * si] - w[2 * si + 1];
-                    y[si].y = v[2 * si + 1] + w[2 * si];
+            for (int ch = 0; ch < 4; ++ch) {
+                float d[32];  // d[2rr + h] = D[row][2(16ch + rr) + h]
+                tmem_ld32(taddr + (uint32_t)(32 * ch), d);
+                tmem_ld_wait();
+                if (ch == 3) {  // the accumulator is free for tile it+2
+                    tc_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&dempty[b]);
                 }
-            } else {       // own = Im-row (sets 16..31), w = Re-row columns 32..63
+                float rcv[16];
 #pragma unroll
-                for (int si = 0; si < 16; ++si) {
-                    y[si].x = w[2 * si] - v[32 + 2 * si + 1];
-                    y[si].y = w[2 * si + 1] + v[32 + 2 * si];
+                for (int e = 0; e < 16; ++e) rcv[e] = __shfl_xor_sync(0xffffffffu, c ? d[e] : d[16 + e], 16);
+                float2 y[8];
+#pragma unroll
+                for (int rr = 0; rr < 8; ++rr) {
+                    if (c == 0) {  // own: D[re][.]; partner: D[im][.] of outputs 16ch + rr
+                        y[rr].x = d[2 * rr] - rcv[2 * rr + 1];
+                        y[rr].y = rcv[2 * rr] + d[2 * rr + 1];
+                    } else {       // own: D[im][.]; partner: D[re][.] of outputs 16ch + 8 + rr
+                        y[rr].x = rcv[2 * rr] - d[16 + 2 * rr + 1];
+                        y[rr].y = d[16 + 2 * rr] + rcv[2 * rr + 1];
+                    }
                 }
-            }
+                if constexpr (Q0T) {
+                    // pairs (r, r+1) are adjacent amplitudes
 #pragma unroll
-            for (int si = 0; si < 16; ++si) {
-                const int s = 16 * h + si;
-                if constexpr (Q0T) ystage[s * 66 + r] = y[si];
-                else ystage[r * 34 + s] = y[si];
-            }
-            if (!group_sync(epibar, gph, err, abort_flag)) break;
-            // coalesced 16-byte write-back
-            if constexpr (Q0T) {
-                const int lp = tid & 31;
+                    for (int rr = 0; rr < 8; rr += 2) {
+                        const uint64_t o = c ? a.off[16 * ch + 8 + rr] : a.off[16 * ch + rr];
+                        *reinterpret_cast<float4*>(dst + o) = make_float4(y[rr].x, y[rr].y, y[rr + 1].x, y[rr + 1].y);
+                    }
+                } else {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int s = (tid >> 5) + 4 * i;
-                    uint64_t base = t * kSets + s;
-#pragma unroll
-                    for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
-                    const float4 y2 = *reinterpret_cast<const float4*>(ystage + s * 66 + 2 * lp);
-                    *reinterpret_cast<float4*>(psi + base + soff[2 * lp]) = y2;
-                }
-            } else {
-                const int sp = tid & 15;
-                uint64_t base = t * kSets + 2 * sp;
-#pragma unroll
-                for (int b = 0; b < 6; ++b) base = insert_zero(base, a.sorted[b]);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int l = (tid >> 4) + 8 * i;
-                    const float4 y2 = *reinterpret_cast<const float4*>(ystage + l * 34 + 2 * sp);
-                    *reinterpret_cast<float4*>(psi + base + soff[l]) = y2;
+                    for (int rr = 0; rr < 8; ++rr) {
+                        const uint64_t o = c ? a.off[16 * ch + 8 + rr] : a.off[16 * ch + rr];
+                        dst[o] = y[rr];
+                    }
                 }
             }
-            if (!group_sync(epibar, gph, err, abort_flag)) break;
         }
     }
 
@@ -540,7 +491,8 @@ static cudaError_t run(float2* psi, const float2* U, const Args& a, int* err, cu
 
 }  // namespace tc
 
-bool gemm_supported(int n, int k) { return k == 6 && n >= 11; }
+// at least one tile of 64 sets
+bool gemm_supported(int n, int k) { return k == 6 && n >= 12; }
 
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat, int precision, int* err,
                         cudaStream_t st) {

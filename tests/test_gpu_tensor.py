@@ -84,3 +84,32 @@ def test_no_device_timeout_flag(qs):
     s = B.State(n, "c64")
     p.execute(s)
     s.sync()   # raises QsError(status 5) if a bounded device wait had timed out
+
+
+@pytest.mark.parametrize("n", [12, 13, 15, 21])
+def test_tile_counts(qs, n):
+    """One tile of 64 sets (n = 12), a grid smaller than the SM count, and
+    several tiles per CTA (n = 21: 512 tiles on at most 152 CTAs)."""
+    rng = Xoshiro256ss(90 + n)
+    psi0 = random_state(n, n)
+    for qubits in ([n - 1, n - 3, 6, 4, 2, 0], [n - 2, 9, 8, 5, 3, 1]):
+        m = random_unitary(6, rng)
+        ref = oracle.apply_gate(psi0, n, qubits, m)
+        got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision="3xtf32",
+                             use_tile=False)
+        assert info["per_kind"] == {"tensor": 1}, info
+        assert rel_l2(got, ref) < GATE_TOL["3xtf32"], (qubits, rel_l2(got, ref))
+
+
+def test_below_one_tile_uses_cuda_cores(qs):
+    """Fewer than 64 sets (n = 11): the planner keeps the 6-qubit block on
+    the FP32 CUDA-core path."""
+    n = 11
+    rng = Xoshiro256ss(91)
+    psi0 = random_state(n, 5)
+    qubits = [10, 8, 6, 4, 2, 0]
+    m = random_unitary(6, rng)
+    got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision="3xtf32",
+                         use_tile=False)
+    assert "tensor" not in info["per_kind"], info
+    assert rel_l2(got, oracle.apply_gate(psi0, n, qubits, m)) < 2e-6
