@@ -216,8 +216,10 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
 static void pad_to_six(int n, Pass& p) {
     uint64_t used = 0;
     for (int i = 0; i < p.k; ++i) used |= 1ull << p.qubits[i];
-    int extra = 0;
-    while (extra < n && ((used >> extra) & 1)) ++extra;
+    // the highest unused qubit: it leaves the low, contiguous index bits to
+    // the sets (and qubit 0 out of the targets when the block leaves it out)
+    int extra = n - 1;
+    while (extra > 0 && ((used >> extra) & 1)) --extra;
     const int d = 1 << p.k, D = 2 * d;
     std::vector<double> m(2 * D * D, 0.0);
     for (int b = 0; b < 2; ++b)
@@ -299,6 +301,7 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
     const int b = std::min(low_bits(dt), L);
     const uint64_t lowmask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
     std::vector<char> placed(blocks.size(), 0);
+    const bool tensor = dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6);
     for (int start = 0; start < (int)blocks.size(); ++start) {
         if (placed[start]) continue;
         std::vector<int> taken;
@@ -329,10 +332,12 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
             p.mats = g.m;
             if (g.kind == QS_GATE_DIAGONAL) p.kind = PASS_DIAG;
             else if (g.kind == QS_GATE_MONOMIAL) p.kind = PASS_MONO;
-            else if (g.k <= 4) p.kind = PASS_DENSE;
-            else if (dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6)) {
+            else if (g.k <= 3 || (g.k == 4 && !tensor)) p.kind = PASS_DENSE;
+            else if (tensor) {
+                // the tensor-core pass is 6-qubit only; a 4-qubit block is
+                // also cheaper there than on the FP32 CUDA cores (64 FMA per amplitude)
                 p.kind = PASS_GEMM;
-                if (g.k == 5) pad_to_six(n, p);  // the tensor-core pass is 6-qubit only
+                while (p.k < 6) pad_to_six(n, p);
                 sort_qubits_descending(p);
             } else p.kind = PASS_DENSE_SMEM;
         } else {

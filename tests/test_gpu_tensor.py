@@ -41,12 +41,15 @@ def test_single_6q_gate_all_placements(qs, prec):
 
 
 @pytest.mark.parametrize("prec", ["3xtf32", "3xbf16"])
-def test_single_5q_gate_padded(qs, prec):
+@pytest.mark.parametrize("k", [4, 5])
+def test_single_gate_padded_to_six(qs, prec, k):
+    """4- and 5-qubit dense blocks are padded with the highest unused qubits
+    (identity on them) and run on the 6-qubit tensor pass."""
     n = 13
-    rng = Xoshiro256ss(78)
+    rng = Xoshiro256ss(78 + k)
     psi0 = random_state(n, 4)
-    for qubits in ([0, 1, 2, 3, 4], [12, 3, 7, 0, 9]):
-        m = random_unitary(5, rng)
+    for qubits in ([0, 1, 2, 3, 4][:k], [12, 3, 7, 0, 9][:k], [11, 12, 5, 6, 1][:k]):
+        m = random_unitary(k, rng)
         ref = oracle.apply_gate(psi0, n, qubits, m)
         got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision=prec,
                              use_tile=False)
