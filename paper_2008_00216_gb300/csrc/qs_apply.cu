@@ -484,8 +484,7 @@ __global__ void __launch_bounds__(256) k_tile(typename C2<R>::T* __restrict__ ps
         uint64_t base = t;
         for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
         // load: rows of 2^b contiguous amplitudes
-        for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x)
-            tile[e] = psi[base + rowoff[e >> b] + (e & (rowlen - 1))];
+        tile_gather(tile, psi, base, rowoff, b, L);
         __syncthreads();
         for (int gi = 0; gi < a.ngates; ++gi) {
             const TileGate& g = a.g[gi];

@@ -107,8 +107,7 @@ __global__ void __launch_bounds__(256) k_batch(typename C2<R>::T* __restrict__ s
                     tile[e] = v;
                 }
             } else {
-                for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x)
-                    tile[e] = __ldcg(psi + base + rowoff[e >> b] + (e & (rowlen - 1)));
+                tile_gather<T, true>(tile, psi, base, rowoff, b, L);
             }
             __syncthreads();
             for (int gi = 0; gi < p.ngates; ++gi) {

@@ -22,6 +22,60 @@ __device__ __forceinline__ uint32_t insert_zero32(uint32_t x, int p) {
     return ((x >> p) << (p + 1)) | lo;
 }
 
+// Gather a 2^L-amplitude tile into shared memory: local index e lives at
+// base + rowoff[e >> b] + (e & (2^b - 1)) (rows of 2^b contiguous
+// amplitudes).  Each thread issues 8 independent loads before storing any,
+// so a block keeps enough loads in flight to cover the HBM latency.  With
+// CG the loads bypass L1 (data written by other blocks of the same launch).
+template <typename T, bool CG = false>
+__device__ __forceinline__ void tile_gather(T* tile, const T* __restrict__ src, uint64_t base, const uint64_t* rowoff,
+                                            int b, int L) {
+    const uint32_t n = 1u << L, mask = (1u << b) - 1u;
+    for (uint32_t e0 = threadIdx.x; e0 < n; e0 += 8u * blockDim.x) {
+        T v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+            if (e < n) {
+                const T* p = src + base + rowoff[e >> b] + (e & mask);
+                v[k] = CG ? __ldcg(p) : *p;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+            if (e < n) tile[e] = v[k];
+        }
+    }
+}
+
+// The same for two states sharing the tile layout (4 + 4 loads in flight).
+template <typename T>
+__device__ __forceinline__ void tile_gather2(T* ta, T* tb, const T* __restrict__ a, const T* __restrict__ b_,
+                                             uint64_t base, const uint64_t* rowoff, int b, int L) {
+    const uint32_t n = 1u << L, mask = (1u << b) - 1u;
+    for (uint32_t e0 = threadIdx.x; e0 < n; e0 += 4u * blockDim.x) {
+        T va[4], vb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+            if (e < n) {
+                const uint64_t gi = base + rowoff[e >> b] + (e & mask);
+                va[k] = a[gi];
+                vb[k] = b_[gi];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t e = e0 + (uint32_t)k * blockDim.x;
+            if (e < n) {
+                ta[e] = va[k];
+                tb[e] = vb[k];
+            }
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ T cmul(T m, T x) {
     T r;

@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <complex>
 #include <map>
 #include <memory>
 #include <new>
@@ -670,67 +671,126 @@ qs_status qs_apply_pauli_sum(const qs_state* psi, const qs_pauli_sum* h, qs_stat
 
 // -------------------------------------------------------------- gradients
 
-qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params, const qs_pauli_sum* h,
-                              qs_state* psi, qs_state* lam, double* energy, double* grad) {
-    if (!c || !h || !psi || !lam || !energy || (num_params > 0 && !grad))
-        return fail(QS_ERR_ARG, "null argument");
-    qs_status st = check_state(psi);
-    if (st != QS_OK) return st;
-    st = check_state(lam);
-    if (st != QS_OK) return st;
-    if (psi->n != c->n || lam->n != c->n || h->n != c->n || psi->dt != lam->dt)
-        return fail(QS_ERR_ARG, "circuit, states and Hamiltonian disagree on n or dtype");
-    if (psi->data == lam->data) return fail(QS_ERR_ARG, "psi and lambda must be distinct");
-    if (num_params != c->num_params)
-        return fail(QS_ERR_ARG, "circuit has %d parameters, %d given", c->num_params, num_params);
-    for (const GateRec& g : c->gates)
-        if (g.param >= 0)
-            for (const GateRec& g2 : c->gates)
-                if (&g2 != &g && g2.param == g.param)
-                    return fail(QS_ERR_UNSUPPORTED, "parameter %d is shared by several gates", g.param);
-    if (num_params) {
-        st = qs_circuit_set_params(c, theta, num_params);
-        if (st != QS_OK) return st;
+}  // extern "C"
+
+// ------------------------------------------------------------ adjoint sweep
+//
+// The reverse sweep visits the gates last to first.  A maximal run of
+// pairwise-commuting gates (disjoint qubits, or all diagonal with diagonal
+// generators) is a stage: every gate of the run can be moved to the run's
+// end, so all of its gradients Im <lambda|P|psi> come from the current
+// (psi, lambda), after which the run's inverse is applied.  Runs of at least
+// kStageMin gates take the stage path:
+//   all diagonal  one k_diag_stage pass over psi and lambda (gradients, then
+//                 the inverse as per-8-qubit phase tables and cross gates)
+//   otherwise     read-only k_grad_pairs passes for the gradients, then the
+//                 inverse as a fused plan (6-qubit blocks) on each state
+// Shorter runs are merged into segments that take the per-gate tile sweep
+// (k_adj_tile: each gate's gradient, then its inverse, in shared memory).
+namespace {
+
+constexpr int kStageMin = 8;
+
+struct SweepUnit {
+    int fwd = 0;               // index of the gate in the circuit
+    uint64_t qm = 0;
+    bool diag = false;         // diagonal, and its generator (if any) is diagonal
+};
+
+struct AdjPass {
+    int L = 0;
+    int pos[16] = {0};
+    std::vector<AdjTileGate> tg;
+    std::vector<double> mats;  // U^dagger, interleaved
+    size_t mat0 = 0;
+};
+
+struct GradLaunch {
+    int L = 0;
+    int pos[16] = {0};
+    std::vector<StageGen> gens;
+};
+
+struct DiagLaunch {
+    int nchunks = 0;
+    std::vector<DiagCross> cross;
+    size_t tab0 = 0;           // element offset in the tables buffer
+    uint32_t tab_elems = 0;
+    std::vector<uint64_t> zm;
+    std::vector<int> slots;
+    bool apply = false;
+};
+
+struct SweepOp {
+    int type = 0;              // 0 tile pass, 1 gradient pass, 2 diagonal stage, 3 plan on both states
+    int index = 0;
+};
+
+}  // namespace
+
+struct AdjointSweep {
+    std::vector<AdjPass> tile;
+    std::vector<GradLaunch> grad;
+    std::vector<DiagLaunch> diag;
+    std::vector<qs_plan*> plans;
+    std::vector<SweepOp> ops;
+    std::vector<double> allm, tables;
+    double* partials = nullptr;
+    double* sums = nullptr;
+    void* dmats = nullptr;
+    void* dtables = nullptr;
+    cudaStream_t stream = nullptr;
+    std::vector<char> hostm, hostt;   // kept until the stream has consumed them
+    void release() {
+        if (stream) {
+            cudaStreamSynchronize(stream);
+            if (partials) cudaFreeAsync(partials, stream);
+            if (sums) cudaFreeAsync(sums, stream);
+            if (dmats) cudaFreeAsync(dmats, stream);
+            if (dtables) cudaFreeAsync(dtables, stream);
+        }
+        partials = sums = nullptr;
+        dmats = dtables = nullptr;
+        for (qs_plan* p : plans) qs_plan_destroy(p);
+        plans.clear();
     }
-    cudaStream_t sm = psi->stream;
-    if (lam->stream != sm) return fail(QS_ERR_ARG, "psi and lambda must share a stream");
-    // forward: psi = U |0>
-    QS_CUDA(launch_init_basis(psi->data, psi->n, psi->dt, 0, sm));
-    {
-        qs_options opt;
-        qs_options_default(&opt);
-        qs_plan* p = nullptr;
-        st = qs_plan_create(c, psi->dt, &opt, &p);
-        if (st != QS_OK) return st;
-        st = qs_plan_execute(psi, p);
-        cudaError_t e = cudaStreamSynchronize(sm);
-        qs_plan_destroy(p);
-        if (st != QS_OK) return st;
-        if (e != cudaSuccess) return cuda_fail(e, "forward pass");
-    }
-    // lambda = H psi; E = <psi|lambda>
-    QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
-    double* res = result_area(psi);
-    QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
-    // reverse sweep: units (gradient of the gate's parameter, then U^dag)
-    // grouped into tile passes over psi and lambda together.  A unit
-    // commutes with units on disjoint qubits, which leaves every
-    // <lambda|P|psi> unchanged (P acts on the unit's own qubits); diagonal
-    // units whose generator is diagonal also commute with each other.
-    const int nb = reduce_blocks();
-    const int rows = std::max(num_params, 1);
-    // runs of consecutive fixed gates are fused first (<= 4 qubits, FP64
-    // products): the reverse sweep then applies one U^dagger per block
+};
+
+static void conj_transpose(const GateRec& g, GateRec& u) {
+    u = g;
+    const int d = 1 << g.k;
+    for (int r = 0; r < d; ++r)
+        for (int col = 0; col < d; ++col) {
+            u.m[2 * (r * d + col)] = g.m[2 * (col * d + r)];
+            u.m[2 * (r * d + col) + 1] = -g.m[2 * (col * d + r) + 1];
+        }
+    u.kind = classify_matrix(g.k, u.m.data());
+}
+
+static bool generator_diagonal(const GateRec& g) {
+    for (int i = 0; g.param >= 0 && i < g.k; ++i)
+        if (g.paulis[i] == 'X' || g.paulis[i] == 'Y') return false;
+    return true;
+}
+
+// Tile-sweep passes for the gates `rev` (circuit indices in sweep order,
+// i.e. the reverse of a valid circuit order); runs of fixed gates are fused
+// to <= 4 qubits first.  Appended to sw.tile / sw.ops.
+static qs_status add_tile_segment(const qs_circuit& c, const std::vector<int>& rev, int n, qs_dtype dt,
+                                  AdjointSweep& sw) {
     std::vector<GateRec> fwd;
-    for (size_t l = 0; l < c->gates.size();) {
-        if (c->gates[l].param >= 0) {
-            fwd.push_back(c->gates[l++]);
+    const int cnt = (int)rev.size();
+    for (int l = cnt - 1; l >= 0;) {
+        const GateRec& g0 = c.gates[rev[l]];
+        if (g0.param >= 0) {
+            fwd.push_back(g0);
+            --l;
             continue;
         }
         std::vector<GateRec> run;
-        while (l < c->gates.size() && c->gates[l].param < 0) run.push_back(c->gates[l++]);
+        while (l >= 0 && c.gates[rev[l]].param < 0) run.push_back(c.gates[rev[l--]]);
         std::vector<GateRec> blocks;
-        st = fuse_gates(c->n, run, 4, blocks);
+        qs_status st = fuse_gates(n, run, 4, blocks);
         if (st != QS_OK) return st;
         fwd.insert(fwd.end(), blocks.begin(), blocks.end());
     }
@@ -739,44 +799,24 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     for (int l = (int)fwd.size() - 1; l >= 0; --l) {
         const GateRec& g = fwd[l];
         if (g.k > 4 && g.kind != QS_GATE_DIAGONAL)
-            return fail(QS_ERR_UNSUPPORTED, "adjoint sweep supports dense gates on up to 4 qubits");
-        GateRec u = g;
-        const int d = 1 << g.k;
-        for (int r = 0; r < d; ++r)
-            for (int col = 0; col < d; ++col) {
-                u.m[2 * (r * d + col)] = g.m[2 * (col * d + r)];
-                u.m[2 * (r * d + col) + 1] = -g.m[2 * (col * d + r) + 1];
-            }
-        u.kind = classify_matrix(g.k, u.m.data());
+            return fail(QS_ERR_UNSUPPORTED, "adjoint tile sweep supports dense gates on up to 4 qubits");
+        GateRec u;
+        conj_transpose(g, u);
         appl_kind.push_back(u.kind);
-        if (g.param >= 0)
-            for (int i = 0; i < g.k; ++i)
-                if (g.paulis[i] == 'X' || g.paulis[i] == 'Y') u.kind = QS_GATE_DENSE;  // generator mixes amplitudes
+        if (!generator_diagonal(g)) u.kind = QS_GATE_DENSE;  // generator mixes amplitudes
         units.push_back(std::move(u));
     }
-    const int L = auto_tile_qubits(psi->n, psi->dt);
-    const int lowb = std::min(psi->dt == QS_C64 ? 5 : 4, L);
+    const int L = auto_tile_qubits(n, dt);
+    const int lowb = std::min(dt == QS_C64 ? 5 : 4, L);
     std::vector<std::vector<int>> groups = group_for_tiles(units, L, lowb, 3072);
-    // phase 1 (host): every pass's tile layout, gradient slots and
-    // matrices; phase 2: one upload, then the passes back to back
-    struct AdjPass {
-        int L = 0;
-        int pos[16] = {0};
-        std::vector<AdjTileGate> tg;
-        std::vector<double> mats;  // U^dagger, interleaved
-        size_t mat0 = 0;
-    };
-    std::vector<AdjPass> aps(groups.size());
-    std::vector<double> allm;
-    for (size_t gi = 0; gi < groups.size(); ++gi) {
-        const auto& gr = groups[gi];
-        AdjPass& ap = aps[gi];
+    for (const auto& gr : groups) {
+        AdjPass ap;
         uint64_t S = (1ull << lowb) - 1;
         for (int u : gr)
             for (int i = 0; i < units[u].k; ++i) S |= 1ull << units[u].qubits[i];
-        for (int q = 0; q < psi->n && __builtin_popcountll(S) < L; ++q) S |= 1ull << q;
+        for (int q = 0; q < n && __builtin_popcountll(S) < L; ++q) S |= 1ull << q;
         int local_of[kMaxQubits];
-        for (int q = 0; q < psi->n; ++q)
+        for (int q = 0; q < n; ++q)
             if ((S >> q) & 1) {
                 local_of[q] = ap.L;
                 ap.pos[ap.L++] = q;
@@ -812,42 +852,354 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
             }
             ap.tg.push_back(a);
         }
-        ap.mat0 = allm.size() / 2;
-        allm.insert(allm.end(), ap.mats.begin(), ap.mats.end());
+        ap.mat0 = sw.allm.size() / 2;
+        sw.allm.insert(sw.allm.end(), ap.mats.begin(), ap.mats.end());
+        sw.ops.push_back({0, (int)sw.tile.size()});
+        sw.tile.push_back(std::move(ap));
     }
-    const size_t esz = psi->amp_bytes();
-    std::vector<char> hostm(allm.size() / 2 * esz);  // kept until the final synchronisation
-    for (size_t i = 0; i < allm.size(); ++i) {
-        if (psi->dt == QS_C64) ((float*)hostm.data())[i] = (float)allm[i];
-        else ((double*)hostm.data())[i] = allm[i];
+    return QS_OK;
+}
+
+// Gradient passes for the parameterised gates among `gates` (generators on
+// global qubits): batches of <= kStageGradGens whose qubits fit one tile.
+static void add_gradient_passes(const std::vector<const GateRec*>& gates, int n, qs_dtype dt, AdjointSweep& sw) {
+    const int L = std::min(n, dt == QS_C64 ? 12 : 11);
+    const int lowb = std::min(dt == QS_C64 ? 5 : 4, L);
+    const uint64_t low = (1ull << lowb) - 1;
+    struct G { uint64_t x, z; int ny, slot; };
+    std::vector<G> gens;
+    for (const GateRec* g : gates) {
+        if (g->param < 0) continue;
+        G e{0, 0, 0, g->param};
+        for (int i = 0; i < g->k; ++i) {
+            const uint64_t bit = 1ull << g->qubits[i];
+            if (g->paulis[i] == 'X' || g->paulis[i] == 'Y') e.x |= bit;
+            if (g->paulis[i] == 'Z' || g->paulis[i] == 'Y') e.z |= bit;
+            if (g->paulis[i] == 'Y') e.ny++;
+        }
+        gens.push_back(e);
     }
-    double* partials = nullptr;
-    double* sums = nullptr;
-    void* dmats = nullptr;
-    QS_CUDA(cudaMallocAsync(&partials, sizeof(double) * 2 * nb * (size_t)rows, sm));
-    QS_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2 * rows, sm));
-    QS_CUDA(cudaMallocAsync(&dmats, std::max<size_t>(hostm.size(), 16), sm));
-    QS_CUDA(cudaMemsetAsync(partials, 0, sizeof(double) * 2 * nb * (size_t)rows, sm));
-    QS_CUDA(cudaMemcpyAsync(dmats, hostm.data(), hostm.size(), cudaMemcpyHostToDevice, sm));
-    for (const AdjPass& ap : aps) {
-        const void* dm = (const char*)dmats + ap.mat0 * esz;
-        cudaError_t e = launch_adjoint_tile(psi->data, lam->data, psi->n, psi->dt, ap.L, ap.pos, ap.tg, dm,
-                                            ap.mats.size() / 2, partials, nb, sm);
-        if (e != cudaSuccess) {
-            cudaFreeAsync(partials, sm);
-            cudaFreeAsync(sums, sm);
-            cudaFreeAsync(dmats, sm);
-            return cuda_fail(e, "adjoint pass");
+    // group by the highest qubit touched, so neighbours share a tile
+    std::stable_sort(gens.begin(), gens.end(), [](const G& a, const G& b) {
+        const uint64_t ma = a.x | a.z, mb = b.x | b.z;
+        return (ma ? 63 - __builtin_clzll(ma) : -1) > (mb ? 63 - __builtin_clzll(mb) : -1);
+    });
+    size_t i = 0;
+    while (i < gens.size()) {
+        uint64_t S = low;
+        std::vector<G> batch;
+        while (i < gens.size() && (int)batch.size() < kStageGradGens &&
+               __builtin_popcountll(S | gens[i].x | gens[i].z) <= L) {
+            S |= gens[i].x | gens[i].z;
+            batch.push_back(gens[i++]);
+        }
+        for (int q = 0; q < n && __builtin_popcountll(S) < L; ++q) S |= 1ull << q;
+        GradLaunch gl;
+        int local_of[kMaxQubits];
+        for (int q = 0; q < n; ++q)
+            if ((S >> q) & 1) {
+                local_of[q] = gl.L;
+                gl.pos[gl.L++] = q;
+            }
+        for (const G& e : batch) {
+            StageGen sg{0, 0, e.ny, e.slot};
+            for (int q = 0; q < n; ++q) {
+                if ((e.x >> q) & 1) sg.px |= 1u << local_of[q];
+                if ((e.z >> q) & 1) sg.pz |= 1u << local_of[q];
+            }
+            gl.gens.push_back(sg);
+        }
+        sw.ops.push_back({1, (int)sw.grad.size()});
+        sw.grad.push_back(std::move(gl));
+    }
+}
+
+// A run of diagonal gates: its Z-generator gradients and its inverse.
+static void add_diag_stage(const std::vector<const GateRec*>& gates, int n, AdjointSweep& sw) {
+    const int nchunks = (n + 7) / 8;
+    DiagLaunch dl;
+    dl.nchunks = nchunks;
+    std::vector<std::complex<double>> tab(256 * (size_t)nchunks, 1.0), cross;
+    for (const GateRec* g : gates) {
+        GateRec u;
+        conj_transpose(*g, u);
+        const int k = u.k, d = 1 << k;
+        const int c0 = u.qubits[0] >> 3;
+        bool one_chunk = true;
+        for (int i = 1; i < k; ++i) one_chunk = one_chunk && (u.qubits[i] >> 3) == c0;
+        if (one_chunk) {
+            for (int j = 0; j < 256; ++j) {
+                int l = 0;
+                for (int i = 0; i < k; ++i) l = (l << 1) | ((j >> (u.qubits[i] - 8 * c0)) & 1);
+                tab[256 * c0 + j] *= std::complex<double>(u.m[2 * (l * d + l)], u.m[2 * (l * d + l) + 1]);
+            }
+        } else {
+            DiagCross x{};
+            x.k = (uint8_t)k;
+            for (int i = 0; i < k; ++i) x.q[i] = (uint8_t)u.qubits[i];
+            x.tab = (uint32_t)(256 * nchunks + cross.size());
+            for (int l = 0; l < d; ++l) cross.emplace_back(u.m[2 * (l * d + l)], u.m[2 * (l * d + l) + 1]);
+            dl.cross.push_back(x);
+        }
+        if (g->param >= 0) {
+            uint64_t zm = 0;
+            for (int i = 0; i < g->k; ++i)
+                if (g->paulis[i] == 'Z') zm |= 1ull << g->qubits[i];
+            dl.zm.push_back(zm);
+            dl.slots.push_back(g->param);
         }
     }
-    QS_CUDA(launch_sum_partials(partials, rows, nb, sums, sm));
+    tab.insert(tab.end(), cross.begin(), cross.end());
+    dl.tab0 = sw.tables.size() / 2;
+    dl.tab_elems = (uint32_t)tab.size();
+    for (const auto& z : tab) {
+        sw.tables.push_back(z.real());
+        sw.tables.push_back(z.imag());
+    }
+    dl.apply = true;
+    sw.ops.push_back({2, (int)sw.diag.size()});
+    sw.diag.push_back(std::move(dl));
+}
+
+// Host phase: stages, segments and every launch's arguments.  Stages are
+// formed by the scan of Section 4.5 over the reversed gate list: from the
+// first unplaced gate, a later gate joins when it commutes with every member
+// and with every gate skipped so far (disjoint qubits, or both diagonal);
+// a skipped gate obstructs its qubits.
+static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, const qs_options& fast, AdjointSweep& sw) {
+    const int G = (int)c.gates.size();
+    std::vector<SweepUnit> units;  // reverse order
+    for (int l = G - 1; l >= 0; --l) {
+        const GateRec& g = c.gates[l];
+        SweepUnit u;
+        u.fwd = l;
+        for (int i = 0; i < g.k; ++i) u.qm |= 1ull << g.qubits[i];
+        GateRec ud;
+        conj_transpose(g, ud);
+        u.diag = ud.kind == QS_GATE_DIAGONAL && generator_diagonal(g);
+        units.push_back(u);
+    }
+    const int nchunks = (n + 7) / 8;
+    auto crosses = [&](const SweepUnit& u) {
+        const GateRec& g = c.gates[u.fwd];
+        for (int q = 1; q < g.k; ++q)
+            if ((g.qubits[q] >> 3) != (g.qubits[0] >> 3)) return true;
+        return false;
+    };
+    const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
+    std::vector<char> placed(units.size(), 0);
+    std::vector<int> segment;  // pending tile-sweep gates (circuit indices, sweep order)
+    auto flush_segment = [&]() -> qs_status {
+        if (segment.empty()) return QS_OK;
+        qs_status st = add_tile_segment(c, segment, n, dt, sw);
+        segment.clear();
+        return st;
+    };
+    for (size_t s0 = 0; s0 < units.size(); ++s0) {
+        if (placed[s0]) continue;
+        std::vector<size_t> stage{s0};
+        placed[s0] = 1;
+        uint64_t st_any = units[s0].diag ? 0 : units[s0].qm, st_diag = units[s0].diag ? units[s0].qm : 0;
+        uint64_t bl_any = 0, bl_diag = 0;
+        bool all_diag = units[s0].diag;
+        // Z generators on one qubit / on several, as one diagonal-stage launch counts them
+        auto zkind = [&](const SweepUnit& u) {
+            const GateRec& g = c.gates[u.fwd];
+            if (g.param < 0) return 0;
+            int z = 0;
+            for (int i = 0; i < g.k; ++i) z += g.paulis[i] == 'Z';
+            return z == 1 ? 1 : 2;
+        };
+        int nsingle = zkind(units[s0]) == 1, nmulti = zkind(units[s0]) == 2, ncross = crosses(units[s0]);
+        size_t entries = 256 * (size_t)nchunks + (ncross ? (1u << c.gates[units[s0].fwd].k) : 0);
+        int scanned = 0;
+        for (size_t j = s0 + 1; j < units.size() && scanned < 4096; ++j) {
+            if (placed[j]) continue;
+            ++scanned;
+            const SweepUnit& u = units[j];
+            const bool with_skipped = (u.qm & bl_any) == 0 && (u.diag || (u.qm & bl_diag) == 0);
+            const bool with_stage = (u.qm & st_any) == 0 && (u.diag || (u.qm & st_diag) == 0);
+            bool join = with_skipped && with_stage;
+            if (join && all_diag && u.diag) {  // capacity of one diagonal-stage launch
+                const int zk = zkind(u);
+                const bool cr = crosses(u);
+                const size_t ent = cr ? (1u << c.gates[u.fwd].k) : 0;
+                if (nsingle + (zk == 1) > kStageDiagGens || nmulti + (zk == 2) > kStageDiagMulti ||
+                    ncross + (int)cr > kStageDiagCross || entries + ent > kStageDiagTabElems)
+                    join = false;
+                else {
+                    nsingle += zk == 1;
+                    nmulti += zk == 2;
+                    ncross += cr;
+                    entries += ent;
+                }
+            }
+            if (join) {
+                stage.push_back(j);
+                placed[j] = 1;
+                if (u.diag) st_diag |= u.qm;
+                else st_any |= u.qm;
+                all_diag = all_diag && u.diag;
+            } else if (u.diag) {
+                bl_diag |= u.qm;
+            } else {
+                bl_any |= u.qm;
+            }
+            if ((bl_any & all) == all) break;  // every qubit obstructed: nothing more can join
+        }
+        // the gradient tile pass needs 2^8 amplitudes (one per thread)
+        if ((int)stage.size() < kStageMin || (!all_diag && n < 8)) {
+            for (size_t j : stage) segment.push_back(units[j].fwd);
+            continue;
+        }
+        qs_status st = flush_segment();
+        if (st != QS_OK) return st;
+        std::vector<const GateRec*> gates;
+        for (size_t j : stage) gates.push_back(&c.gates[units[j].fwd]);
+        if (all_diag) {
+            add_diag_stage(gates, n, sw);
+        } else {
+            add_gradient_passes(gates, n, dt, sw);
+            qs_circuit inv;
+            inv.n = n;
+            for (const GateRec* g : gates) {  // sweep order; the members commute
+                GateRec u;
+                conj_transpose(*g, u);
+                u.param = -1;
+                u.paulis[0] = 0;
+                inv.gates.push_back(std::move(u));
+            }
+            qs_plan* p = nullptr;
+            st = qs_plan_create(&inv, dt, &fast, &p);
+            if (st != QS_OK) return st;
+            sw.ops.push_back({3, (int)sw.plans.size()});
+            sw.plans.push_back(p);
+        }
+    }
+    return flush_segment();
+}
+
+// Device phase: one upload of the tile-sweep matrices and the phase tables,
+// then every launch in order on the states' stream.
+static qs_status run_reverse_sweep(AdjointSweep& sw, qs_state* psi, qs_state* lam, int nb, int rows, cudaStream_t sm) {
+    sw.stream = sm;
+    const size_t esz = psi->amp_bytes();
+    auto convert = [&](const std::vector<double>& v, std::vector<char>& out) {
+        out.resize(v.size() / 2 * esz);
+        for (size_t i = 0; i < v.size(); ++i) {
+            if (psi->dt == QS_C64) ((float*)out.data())[i] = (float)v[i];
+            else ((double*)out.data())[i] = v[i];
+        }
+    };
+    convert(sw.allm, sw.hostm);
+    convert(sw.tables, sw.hostt);
+    QS_CUDA(cudaMallocAsync(&sw.partials, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    QS_CUDA(cudaMallocAsync(&sw.sums, sizeof(double) * 2 * rows, sm));
+    QS_CUDA(cudaMallocAsync(&sw.dmats, std::max<size_t>(sw.hostm.size(), 16), sm));
+    QS_CUDA(cudaMallocAsync(&sw.dtables, std::max<size_t>(sw.hostt.size(), 16), sm));
+    QS_CUDA(cudaMemsetAsync(sw.partials, 0, sizeof(double) * 2 * nb * (size_t)rows, sm));
+    if (!sw.hostm.empty()) QS_CUDA(cudaMemcpyAsync(sw.dmats, sw.hostm.data(), sw.hostm.size(), cudaMemcpyHostToDevice, sm));
+    if (!sw.hostt.empty()) QS_CUDA(cudaMemcpyAsync(sw.dtables, sw.hostt.data(), sw.hostt.size(), cudaMemcpyHostToDevice, sm));
+    for (const SweepOp& op : sw.ops) {
+        cudaError_t e = cudaSuccess;
+        if (op.type == 0) {
+            const AdjPass& ap = sw.tile[op.index];
+            const void* dm = (const char*)sw.dmats + ap.mat0 * esz;
+            e = launch_adjoint_tile(psi->data, lam->data, psi->n, psi->dt, ap.L, ap.pos, ap.tg, dm, ap.mats.size() / 2,
+                                    sw.partials, nb, sm);
+        } else if (op.type == 1) {
+            const GradLaunch& gl = sw.grad[op.index];
+            e = launch_grad_pairs(psi->data, lam->data, psi->n, psi->dt, gl.L, gl.pos, gl.gens, sw.partials, nb, sm);
+        } else if (op.type == 2) {
+            const DiagLaunch& dl = sw.diag[op.index];
+            e = launch_diag_stage(psi->data, lam->data, psi->n, psi->dt, dl.nchunks, dl.cross,
+                                  (const char*)sw.dtables + dl.tab0 * esz, dl.tab_elems, dl.zm, dl.slots, dl.apply,
+                                  sw.partials, nb, sm);
+        } else {
+            qs_status st = qs_plan_execute(psi, sw.plans[op.index]);
+            if (st == QS_OK) st = qs_plan_execute(lam, sw.plans[op.index]);
+            if (st != QS_OK) return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep launch");
+    }
+    return QS_OK;
+}
+
+extern "C" {
+
+qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params, const qs_pauli_sum* h,
+                              qs_state* psi, qs_state* lam, double* energy, double* grad) {
+    if (!c || !h || !psi || !lam || !energy || (num_params > 0 && !grad))
+        return fail(QS_ERR_ARG, "null argument");
+    qs_status st = check_state(psi);
+    if (st != QS_OK) return st;
+    st = check_state(lam);
+    if (st != QS_OK) return st;
+    if (psi->n != c->n || lam->n != c->n || h->n != c->n || psi->dt != lam->dt)
+        return fail(QS_ERR_ARG, "circuit, states and Hamiltonian disagree on n or dtype");
+    if (psi->data == lam->data) return fail(QS_ERR_ARG, "psi and lambda must be distinct");
+    if (num_params != c->num_params)
+        return fail(QS_ERR_ARG, "circuit has %d parameters, %d given", c->num_params, num_params);
+    for (const GateRec& g : c->gates)
+        if (g.param >= 0)
+            for (const GateRec& g2 : c->gates)
+                if (&g2 != &g && g2.param == g.param)
+                    return fail(QS_ERR_UNSUPPORTED, "parameter %d is shared by several gates", g.param);
+    if (num_params) {
+        st = qs_circuit_set_params(c, theta, num_params);
+        if (st != QS_OK) return st;
+    }
+    cudaStream_t sm = psi->stream;
+    if (lam->stream != sm) return fail(QS_ERR_ARG, "psi and lambda must share a stream");
+    // forward: psi = U |0>, with the fastest exact plan (6-qubit blocks, on
+    // the tensor cores for complex64)
+    qs_options fast;
+    qs_options_default(&fast);
+    if (psi->dt == QS_C64 && gemm_supported(psi->n, 6)) {
+        fast.k_max = 6;
+        fast.precision = QS_PREC_3XTF32;
+    }
+    QS_CUDA(launch_init_basis(psi->data, psi->n, psi->dt, 0, sm));
+    {
+        qs_plan* p = nullptr;
+        st = qs_plan_create(c, psi->dt, &fast, &p);
+        if (st != QS_OK) return st;
+        st = qs_plan_execute(psi, p);
+        cudaError_t e = cudaStreamSynchronize(sm);
+        qs_plan_destroy(p);
+        if (st != QS_OK) return st;
+        if (e != cudaSuccess) return cuda_fail(e, "forward pass");
+    }
+    // lambda = H psi; E = <psi|lambda>
+    QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
+    double* res = result_area(psi);
+    QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
+    AdjointSweep sw;
+    st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sw);
+    if (st != QS_OK) {
+        sw.release();
+        return st;
+    }
+    const int nb = reduce_blocks();
+    const int rows = std::max(num_params, 1);
+    st = run_reverse_sweep(sw, psi, lam, nb, rows, sm);
+    if (st != QS_OK) {
+        sw.release();
+        return st;
+    }
     std::vector<double> host(2 * rows + 2);
-    QS_CUDA(cudaMemcpyAsync(host.data(), sums, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, sm));
-    QS_CUDA(cudaMemcpyAsync(host.data() + 2 * rows, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, sm));
-    QS_CUDA(cudaStreamSynchronize(sm));
-    cudaFreeAsync(partials, sm);
-    cudaFreeAsync(sums, sm);
-    cudaFreeAsync(dmats, sm);
+    cudaError_t e = launch_sum_partials(sw.partials, rows, nb, sw.sums, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host.data(), sw.sums, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, sm);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host.data() + 2 * rows, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, sm);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    sw.release();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep");
+    st = check_device_flag(psi);
+    if (st != QS_OK) return st;
+    st = check_device_flag(lam);
+    if (st != QS_OK) return st;
     *energy = host[2 * rows];
     for (int p = 0; p < num_params; ++p) grad[p] = host[2 * p + 1];  // Im <lambda|P|psi>
     return QS_OK;

@@ -194,6 +194,33 @@ cudaError_t launch_adjoint_tile(void* psi, void* lam, int n, qs_dtype dt, int L,
                                 const std::vector<AdjTileGate>& gates, const void* dmats, size_t mat_elems,
                                 double* partials, int nblocks, cudaStream_t st);
 
+// Stage steps of the adjoint reverse sweep (a run of pairwise-commuting
+// gates: all gradients from one (psi, lambda), then the run's inverse).
+constexpr int kStageGradGens = 16;    // generators per k_grad_pairs launch
+constexpr int kStageDiagGens = 32;    // one-qubit Z generators per k_diag_stage launch
+constexpr int kStageDiagMulti = 8;    // multi-qubit Z generators per k_diag_stage launch
+constexpr int kStageDiagCross = 32;   // gates spanning two 8-qubit chunks
+constexpr uint32_t kStageDiagTabElems = 3072;
+struct StageGen {
+    uint32_t px, pz;       // generator on the tile's local bits: flip mask, sign mask
+    int ny;                // number of Y factors
+    int slot;              // parameter
+};
+struct DiagCross {
+    uint8_t k;
+    uint8_t q[kMaxK];      // global qubits, q[0] the most significant local bit
+    uint32_t tab;          // offset of its 2^k diagonal entries in the tables
+};
+// <lambda|P_g|psi> partial sums for each generator (tile over pos[0..L-1]).
+cudaError_t launch_grad_pairs(const void* psi, const void* lam, int n, qs_dtype dt, int L, const int* pos,
+                              const std::vector<StageGen>& gens, double* partials, int nblocks, cudaStream_t st);
+// Z-generator gradients of a diagonal run, and (apply) its inverse on psi and
+// lambda: tables = nchunks x 256 chunk phases, then the cross gates' entries.
+cudaError_t launch_diag_stage(void* psi, void* lam, int n, qs_dtype dt, int nchunks, const std::vector<DiagCross>& cross,
+                              const void* dtables, uint32_t tab_elems, const std::vector<uint64_t>& zmasks,
+                              const std::vector<int>& slots, bool apply, double* partials, int nblocks,
+                              cudaStream_t st);
+
 int num_sms();
 
 }  // namespace qsgb

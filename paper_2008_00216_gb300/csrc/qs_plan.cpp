@@ -99,7 +99,9 @@ static inline uint64_t qmask(const GateRec& g) {
 
 // Multiply gate g (on its qubits) into the block matrix `acc` whose local
 // bit b corresponds to qubit bq[K-1-b] (bq listed most significant first):
-// acc <- E(g) acc, column by column.
+// acc <- E(g) acc.  For each row set r (the gate's bits zero) the 2^k rows
+// r | l mix as (g.m) x (those rows), for all D columns at once; complex
+// products are written out in real arithmetic.
 static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector<cd>& acc) {
     const int D = 1 << K, d = 1 << g.k;
     int lpos[kMaxK];  // local bit of each gate qubit
@@ -110,29 +112,35 @@ static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector
     }
     uint64_t gmask = 0;
     for (int i = 0; i < g.k; ++i) gmask |= 1ull << lpos[i];
-    std::vector<cd> col(D), out(D);
-    for (int c = 0; c < D; ++c) {
-        for (int r = 0; r < D; ++r) col[r] = acc[r * D + c];
-        for (int r = 0; r < D; ++r) {
-            if (r & gmask) continue;  // r = set base (gate bits zero)
-            cd a[1 << kMaxK];
-            for (int l = 0; l < d; ++l) {
-                int idx = r;
-                for (int i = 0; i < g.k; ++i)
-                    if ((l >> (g.k - 1 - i)) & 1) idx |= 1 << lpos[i];
-                a[l] = col[idx];
-            }
-            for (int lo = 0; lo < d; ++lo) {
-                cd s = 0.0;
-                for (int li = 0; li < d; ++li)
-                    s += cd(g.m[2 * (lo * d + li)], g.m[2 * (lo * d + li) + 1]) * a[li];
-                int idx = r;
-                for (int i = 0; i < g.k; ++i)
-                    if ((lo >> (g.k - 1 - i)) & 1) idx |= 1 << lpos[i];
-                out[idx] = s;
+    int rowof[1 << kMaxK];  // offset of local gate index l within a row set
+    for (int l = 0; l < d; ++l) {
+        int idx = 0;
+        for (int i = 0; i < g.k; ++i)
+            if ((l >> (g.k - 1 - i)) & 1) idx |= 1 << lpos[i];
+        rowof[l] = idx;
+    }
+    const double* m = g.m.data();
+    double* A = reinterpret_cast<double*>(acc.data());  // interleaved, row-major D x D
+    std::vector<double> in(2 * (size_t)d * D);
+    for (int r = 0; r < D; ++r) {
+        if (r & gmask) continue;
+        for (int l = 0; l < d; ++l)
+            std::copy(A + 2 * (size_t)(r | rowof[l]) * D, A + 2 * (size_t)((r | rowof[l]) + 1) * D,
+                      in.begin() + 2 * (size_t)l * D);
+        for (int lo = 0; lo < d; ++lo) {
+            double* out = A + 2 * (size_t)(r | rowof[lo]) * D;
+            for (int c = 0; c < D; ++c) {
+                double sr = 0.0, si = 0.0;
+                for (int li = 0; li < d; ++li) {
+                    const double mr = m[2 * (lo * d + li)], mi = m[2 * (lo * d + li) + 1];
+                    const double xr = in[2 * ((size_t)li * D + c)], xi = in[2 * ((size_t)li * D + c) + 1];
+                    sr += mr * xr - mi * xi;
+                    si += mr * xi + mi * xr;
+                }
+                out[2 * c] = sr;
+                out[2 * c + 1] = si;
             }
         }
-        for (int r = 0; r < D; ++r) acc[r * D + c] = out[r];
     }
 }
 

@@ -186,7 +186,9 @@ __global__ void __launch_bounds__(256) k_apply_pauli(const typename C2<R>::T* __
     using T = typename C2<R>::T;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < p.size; y += stride) {
-        double accr = 0.0, acci = 0.0;
+        // in the state's precision: the result is stored in it, and FP64 is
+        // a slow pipe on this GPU for complex64 states
+        R accr = 0, acci = 0;
         if (p.accumulate) {
             const T o = out[y];
             accr = o.x;
@@ -195,23 +197,20 @@ __global__ void __launch_bounds__(256) k_apply_pauli(const typename C2<R>::T* __
         for (int g = 0; g < p.ngroups; ++g) {
             const uint64_t x = y ^ p.xmask[g];
             // w = sum_t c_t i^ny (-1)^popc(x & Z_t)
-            double wr = 0.0, wi = 0.0;
+            R wr = 0, wi = 0;
             for (int t = p.first[g]; t < p.first[g + 1]; ++t) {
-                const double c = (__popcll(x & p.zmask[t]) & 1) ? -p.coeff[t] : p.coeff[t];
-                switch (p.ny[t] & 3) {
-                    case 0: wr += c; break;
-                    case 1: wi += c; break;
-                    case 2: wr -= c; break;
-                    default: wi -= c; break;
-                }
+                const R c = (__popcll(x & p.zmask[t]) & 1) ? -(R)p.coeff[t] : (R)p.coeff[t];
+                const int q = p.ny[t] & 3;
+                wr += (q == 0) ? c : (q == 2) ? -c : (R)0;
+                wi += (q == 1) ? c : (q == 3) ? -c : (R)0;
             }
             const T a = psi[x];
-            accr += wr * (double)a.x - wi * (double)a.y;
-            acci += wr * (double)a.y + wi * (double)a.x;
+            accr += wr * a.x - wi * a.y;
+            acci += wr * a.y + wi * a.x;
         }
         T o;
-        o.x = (R)accr;
-        o.y = (R)acci;
+        o.x = accr;
+        o.y = acci;
         out[y] = o;
     }
 }
@@ -421,11 +420,7 @@ __global__ void __launch_bounds__(256) k_adj_tile(typename C2<R>::T* __restrict_
     for (uint64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
         uint64_t base = t;
         for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
-        for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
-            const uint64_t gi = base + rowoff[e >> b] + (e & (rowlen - 1));
-            tp[e] = psi[gi];
-            tl[e] = lam[gi];
-        }
+        tile_gather2(tp, tl, psi, lam, base, rowoff, b, L);
         __syncthreads();
         for (int gi = 0; gi < a.ngates; ++gi) {
             const AdjTileGate& ag = a.g[gi];
