@@ -14,7 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
+#include <thread>
 
 #include "qs_internal.h"
 
@@ -121,6 +123,21 @@ static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector
     }
     const double* m = g.m.data();
     double* A = reinterpret_cast<double*>(acc.data());  // interleaved, row-major D x D
+    if (g.kind == QS_GATE_DIAGONAL) {  // scale each row by its diagonal entry
+        for (int r = 0; r < D; ++r) {
+            int l = 0;
+            for (int i = 0; i < g.k; ++i) l = (l << 1) | ((r >> lpos[i]) & 1);
+            const double mr = m[2 * (l * d + l)], mi = m[2 * (l * d + l) + 1];
+            if (mr == 1.0 && mi == 0.0) continue;
+            double* row = A + 2 * (size_t)r * D;
+            for (int c = 0; c < D; ++c) {
+                const double xr = row[2 * c], xi = row[2 * c + 1];
+                row[2 * c] = mr * xr - mi * xi;
+                row[2 * c + 1] = mr * xi + mi * xr;
+            }
+        }
+        return;
+    }
     std::vector<double> in(2 * (size_t)d * D);
     for (int r = 0; r < D; ++r) {
         if (r & gmask) continue;
@@ -182,21 +199,31 @@ static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<ch
 qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out) {
     if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
     out.clear();
+    // 1. the scans (sequential: each one sees what the previous placed)
     std::vector<char> placed(in.size(), 0);
+    std::vector<std::vector<int>> groups;
     for (int start = 0; start < (int)in.size(); ++start) {
         if (placed[start]) continue;
         if (in[start].k > k_max) {  // wider than the bound: kept as it is
             placed[start] = 1;
-            GateRec b = in[start];
-            b.param = -1;
-            b.paulis[0] = 0;
-            out.push_back(b);
+            groups.push_back({-1 - start});
             continue;
         }
-        std::vector<int> taken = scan_group(in, placed, start, 0, k_max, 1 << 14);
+        groups.push_back(scan_group(in, placed, start, 0, k_max, 1 << 14));
+    }
+    // 2. the FP64 block products, independent per group: spread over host threads
+    out.resize(groups.size());
+    auto build = [&](size_t gi) {
+        const std::vector<int>& taken = groups[gi];
+        GateRec& b = out[gi];
+        if (taken[0] < 0) {
+            b = in[-1 - taken[0]];
+            b.param = -1;
+            b.paulis[0] = 0;
+            return;
+        }
         uint64_t support = 0;
         for (int t : taken) support |= qmask(in[t]);
-        GateRec b;
         b.k = __builtin_popcountll(support);
         int bq[kMaxK];
         int j = 0;
@@ -213,9 +240,22 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
             b.m[2 * i + 1] = acc[i].imag();
         }
         b.kind = classify_matrix(b.k, b.m.data());
-        out.push_back(std::move(b));
+    };
+    size_t work = 0;
+    for (const auto& g : groups) work += g.size();
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const unsigned nthreads = (unsigned)std::min<size_t>({(size_t)hw, (size_t)16, groups.size(), work / 64 + 1});
+    if (nthreads <= 1) {
+        for (size_t gi = 0; gi < groups.size(); ++gi) build(gi);
+    } else {
+        std::atomic<size_t> next(0);
+        std::vector<std::thread> pool;
+        for (unsigned t = 0; t < nthreads; ++t)
+            pool.emplace_back([&]() {
+                for (size_t gi = next++; gi < groups.size(); gi = next++) build(gi);
+            });
+        for (auto& th : pool) th.join();
     }
-    (void)n;
     return QS_OK;
 }
 
