@@ -61,11 +61,11 @@ def parse_args(argv=None):
     ap.add_argument("--circuit", choices=["grid", "grid_fixed", "ansatz"], default="grid",
                     help="grid: random fSim angles; grid_fixed: fSim(pi/2, pi/6) everywhere (permutation-with-"
                          "phase gates); ansatz: RY/RZ layers with CZ ladders (diagonal gates)")
-    ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "precision"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "batch_adjoint", "precision"], default="grid",
                     help="grid: the headline circuit; adjoint: gradient vs forward on the ansatz; "
                          "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q")
     ap.add_argument("--layers", type=int, default=20)
-    ap.add_argument("--count", type=int, default=512)
+    ap.add_argument("--count", type=int, default=None, help="circuits (batch: 512) or gradients (batch_adjoint: 256)")
     return ap.parse_args(argv)
 
 
@@ -457,6 +457,54 @@ def run_adjoint(a):
     print(json.dumps(out), flush=True)
 
 
+def run_batch_adjoint(a):
+    """256 adjoint gradients of 20-layer ansatz circuits, n ~ U{12..20}
+    (seeded), Ising H, complex64: one qs_adjoint_gradient_batch call (host
+    threads plan concurrently, each gradient on one of 16 streams) against a
+    loop of single qs_adjoint_gradient calls.  Wall-clock time of the calls,
+    which include all host planning and synchronise."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    from workloads.rng import Xoshiro256ss
+    pkg.load()
+    count = a.count or 256
+    rng = Xoshiro256ss(a.seed)
+    ns = [12 + rng.randint(9) for _ in range(count)]
+    streams = [torch.cuda.Stream() for _ in range(16)]
+    circs, thetas, hams, psis, lams = [], [], [], [], []
+    for i, n in enumerate(ns):
+        theta = C.ansatz_theta(n, 20, seed=a.seed + i)
+        circs.append(B.circuit_from(C.ansatz_circuit(n, 20, theta)))
+        thetas.append(theta)
+        hams.append(B.PauliSum(n, C.ising_hamiltonian(n)))
+        st = streams[i % len(streams)]
+        psis.append(B.State(n, a.dtype, stream=st))
+        lams.append(B.State(n, a.dtype, stream=st, init=None))
+    torch.cuda.synchronize()
+    for _ in range(max(1, a.warmup)):
+        B.adjoint_gradient_batch(circs, thetas, hams, psis, lams)
+    times = []
+    for _ in range(a.steps):
+        t0 = time.perf_counter()
+        B.adjoint_gradient_batch(circs, thetas, hams, psis, lams)
+        times.append(time.perf_counter() - t0)
+    batch_s = sorted(times)[len(times) // 2]
+    t0 = time.perf_counter()
+    for i in range(count):
+        B.adjoint_gradient(circs[i], thetas[i], hams[i], psis[i], lams[i])
+    loop_s = time.perf_counter() - t0
+    params = sum(t.size for t in thetas)
+    out = {"metric": "batched adjoint gradients/s vs looped single gradients", "workload": "batch_adjoint",
+           "value": count / batch_s, "unit": "gradients/s", "higher_is_better": True, "dtype": a.dtype,
+           "gradients": count, "params_total": int(params), "n_range": [min(ns), max(ns)], "layers": 20,
+           "batch_s": batch_s, "loop_s": loop_s, "loop_gradients_per_s": count / loop_s,
+           "speedup_vs_loop": loop_s / batch_s, "streams": len(streams), "steps": a.steps, "warmup": a.warmup,
+           "timing": "wall clock of the synchronous calls (host planning included)"}
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(a):
     """512 seeded grid circuits, n ~ U{10..22}, depth ~ U{8..24}: one batched
     graph launch against looping the single-circuit plans."""
@@ -465,6 +513,7 @@ def run_batch(a):
     from paper_2008_00216_gb300 import binding as B
     from workloads import circuits as C
     pkg.load()
+    a.count = a.count or 512
     specs = C.batched_workload(a.count, seed0=0)
     circs = [B.circuit_from(s) for s in specs]
     t0 = time.perf_counter()
@@ -552,6 +601,8 @@ def main():
         run_batch(a)
     elif a.workload == "precision":
         run_precision(a)
+    elif a.workload == "batch_adjoint":
+        run_batch_adjoint(a)
     else:
         run_own(a)
 

@@ -202,8 +202,10 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
  * amplitude pass (k, or the tile's L), and gates applied in it. */
 qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_gates);
 
-/* Convenience: plan with defaults (k_max 6 fusion) and the given precision,
- * execute, free the plan.  Asynchronous like qs_plan_execute. */
+/* Convenience: plan with the default options and the given precision (k_max
+ * 6 when `prec` is a tensor-core mode on a complex64 state, else k_max 4),
+ * execute, free the plan.  Asynchronous like qs_plan_execute: the plan's
+ * device memory is allocated and freed in the state's stream order. */
 qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec);
 
 /* ------------------------------------------------------------ read back */
@@ -261,12 +263,28 @@ qs_status qs_apply_pauli_sum(const qs_state* psi, const qs_pauli_sum* h, qs_stat
  * runs U on `psi` from |0...0>, forms lambda = H psi in `lam`, E = <psi|lam>,
  * then walks the gates backwards: at each parametrised gate
  * dE/dtheta = Im <lambda|P|psi>, then psi <- U_l^dag psi and
- * lambda <- U_l^dag lambda (no intermediate states stored).  `psi` and
- * `lam` are work states with the circuit's n and a common dtype;
- * grad has num_params entries (host).  Synchronises. */
+ * lambda <- U_l^dag lambda (no intermediate states stored).  Gates that
+ * commute pairwise are taken as one stage: all their gradients from the same
+ * (psi, lambda), then their inverse as fused passes.  `psi` and `lam` are
+ * work states with the circuit's n and a common dtype and stream; grad has
+ * num_params entries (host).  Synchronises the states' stream only. */
 qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params,
                               const qs_pauli_sum* h, qs_state* psi, qs_state* lam,
                               double* energy, double* grad);
+
+/* Many adjoint gradients at once (the differentiation workload's batched
+ * form): gradient i is qs_adjoint_gradient(circuits[i], thetas[i],
+ * num_params[i], hams[i], psi[i], lam[i], &energies[i], grads[i]).  Host
+ * threads plan the gradients concurrently and each gradient's work runs on
+ * the stream of its own states, so gradients whose states have distinct
+ * streams overlap on the GPU.  Every circuit and every state must be a
+ * distinct object (QS_ERR_ARG otherwise); all host arrays have `count`
+ * entries.  Returns the first failing gradient's status (message names its
+ * index); the others still run.  Synchronises every stream used. */
+qs_status qs_adjoint_gradient_batch(int count, qs_circuit* const* circuits, const double* const* thetas,
+                                    const int* num_params, const qs_pauli_sum* const* hams,
+                                    qs_state* const* psi, qs_state* const* lam, double* energies,
+                                    double* const* grads);
 
 /* ------------------------------------------------------------ batches */
 

@@ -80,6 +80,9 @@ _SIGS = {
     "qs_apply_pauli_sum": (ct.c_int, [_P, _P, _P]),
     "qs_adjoint_gradient": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int, _P, _P, _P,
                                        ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]),
+    "qs_adjoint_gradient_batch": (ct.c_int, [ct.c_int, ct.POINTER(_P), ct.POINTER(ct.POINTER(ct.c_double)),
+                                             ct.POINTER(ct.c_int), ct.POINTER(_P), ct.POINTER(_P), ct.POINTER(_P),
+                                             ct.POINTER(ct.c_double), ct.POINTER(ct.POINTER(ct.c_double))]),
     "qs_batch_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.c_int, ct.POINTER(Options), ct.POINTER(_P)]),
     "qs_batch_layout": (ct.c_int, [_P, ct.POINTER(ct.c_uint64)]),
     "qs_batch_info": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
@@ -422,6 +425,28 @@ def adjoint_gradient(circ: Circuit, theta, h: PauliSum, psi: State, lam: State):
     _call("qs_adjoint_gradient", circ.handle, _dbl(theta), int(theta.size), h.handle, psi.handle, lam.handle,
           ct.byref(e), g.ctypes.data_as(ct.POINTER(ct.c_double)))
     return e.value, g
+
+
+def adjoint_gradient_batch(circs: Sequence[Circuit], thetas, hams: Sequence[PauliSum], psis: Sequence[State],
+                           lams: Sequence[State]):
+    """Gradients of many circuits at once (qs_adjoint_gradient_batch).  Give
+    each (psi, lam) pair its own stream (State(..., stream=...)) so their work
+    overlaps.  Returns (energies, list of gradient arrays)."""
+    k = len(circs)
+    if not (len(thetas) == len(hams) == len(psis) == len(lams) == k):
+        raise ValueError("all sequences need one entry per gradient")
+    th = [np.ascontiguousarray(t, dtype=np.float64) for t in thetas]
+    grads = [np.zeros(t.size, dtype=np.float64) for t in th]
+    DP = ct.POINTER(ct.c_double)
+    for s in list(psis) + list(lams):
+        s.sync_stream()
+    energies = np.zeros(k, dtype=np.float64)
+    _call("qs_adjoint_gradient_batch", k, (_P * k)(*[c.handle for c in circs]),
+          (DP * k)(*[t.ctypes.data_as(DP) for t in th]), (ct.c_int * k)(*[t.size for t in th]),
+          (_P * k)(*[h.handle for h in hams]), (_P * k)(*[s.handle for s in psis]),
+          (_P * k)(*[s.handle for s in lams]), energies.ctypes.data_as(DP),
+          (DP * k)(*[g.ctypes.data_as(DP) for g in grads]))
+    return energies, grads
 
 
 # ---------------------------------------------------------------------- batches

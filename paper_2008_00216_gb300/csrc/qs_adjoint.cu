@@ -311,7 +311,7 @@ cudaError_t launch_grad_pairs(const void* psi, const void* lam, int n, qs_dtype 
     const size_t esz = dt == QS_C64 ? 8 : 16;
     const size_t smem = esz * ((size_t)1 << L) + 8 * ((size_t)1 << (L - b));
     auto go = [&](auto kern, auto* p, auto* l) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_max_dynamic_smem(kern);
         if (e != cudaSuccess) return e;
         kern<<<nblocks, 256, smem, st>>>(p, l, a, partials);
         return cudaGetLastError();

@@ -420,13 +420,8 @@ static cudaError_t dense_smem_k(void* psi, int n, const int* qubits, const void*
     p.nsets = 1ull << (n - K);
     p.nchunks = (p.nsets + 31) / 32;
     const size_t smem = sizeof(T) * (D * D + D * 32);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_dense_smem<R, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    cudaError_t e = allow_max_dynamic_smem(k_dense_smem<R, K>);
+    if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(p.nchunks, (uint64_t)num_sms() * 4);
     k_dense_smem<R, K><<<grid, 256, smem, st>>>((T*)psi, (const T*)dmat, p);
     return cudaGetLastError();
@@ -526,11 +521,11 @@ cudaError_t launch_tile(void* psi, int n, qs_dtype dt, const Pass& ps, const voi
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * 8);
     cudaError_t e;
     if (dt == QS_C64) {
-        e = cudaFuncSetAttribute(k_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_dynamic_smem(k_tile<float>);
         if (e != cudaSuccess) return e;
         k_tile<float><<<grid, 256, smem, st>>>((float2*)psi, (const float2*)dmats, a);
     } else {
-        e = cudaFuncSetAttribute(k_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_dynamic_smem(k_tile<double>);
         if (e != cudaSuccess) return e;
         k_tile<double><<<grid, 256, smem, st>>>((double2*)psi, (const double2*)dmats, a);
     }

@@ -380,10 +380,10 @@ qs_status qs_batch_create(const qs_circuit* const* circuits, int count, qs_dtype
     b->smem = esz * ((1u << Lmax) + 256) + sizeof(uint64_t) * (1u << (Lmax - 4));
     int per_sm = 0;
     if (dt == QS_C64) {
-        QS_CUDA(cudaFuncSetAttribute(batch::k_batch<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        QS_CUDA(allow_max_dynamic_smem(batch::k_batch<float>));
         QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch::k_batch<float>, 256, b->smem));
     } else {
-        QS_CUDA(cudaFuncSetAttribute(batch::k_batch<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem));
+        QS_CUDA(allow_max_dynamic_smem(batch::k_batch<double>));
         QS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch::k_batch<double>, 256, b->smem));
     }
     b->grid = std::max(1, std::min(b->nitems, num_sms() * std::max(1, per_sm)));

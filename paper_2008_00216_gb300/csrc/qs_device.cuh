@@ -6,6 +6,22 @@
 
 namespace qsgb {
 
+// Allow a kernel the device's whole opt-in shared memory (minus its static
+// shared memory).  The attribute is one value per kernel for the process,
+// so every caller sets the same value: launches from concurrent host
+// threads with different dynamic sizes cannot undercut each other.
+template <typename K>
+inline cudaError_t allow_max_dynamic_smem(K kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
+
 template <typename R> struct C2;
 template <> struct C2<float> { using T = float2; };
 template <> struct C2<double> { using T = double2; };

@@ -476,7 +476,7 @@ template <int SPLITS, int KIND, bool Q0T>
 static cudaError_t run_q(float2* psi, const float2* U, const Args& a, int* err, cudaStream_t st) {
     using LY = Layout<SPLITS, KIND>;
     const int smem = LY::kTotal + 1024;  // slack to align the base to 1024 bytes
-    cudaError_t e = cudaFuncSetAttribute(k_gemm6<SPLITS, KIND, Q0T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = allow_max_dynamic_smem(k_gemm6<SPLITS, KIND, Q0T>);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
     k_gemm6<SPLITS, KIND, Q0T><<<grid, kThreads, smem, st>>>(psi, U, a, err);

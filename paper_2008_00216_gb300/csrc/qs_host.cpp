@@ -6,7 +6,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
+#include <string>
+#include <thread>
 #include <map>
 #include <memory>
 #include <new>
@@ -403,6 +406,13 @@ qs_status qs_fuse(const qs_circuit* in, int k_max, qs_circuit** out) {
 // ------------------------------------------------------------------ plans
 
 qs_status qs_plan_create(const qs_circuit* c, qs_dtype dt, const qs_options* opt_in, qs_plan** out) {
+    return plan_create_on(c, dt, opt_in, nullptr, out);
+}
+
+}  // extern "C"
+
+qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt_in, cudaStream_t stream,
+                               qs_plan** out) {
     if (!c || !out) return fail(QS_ERR_ARG, "null argument");
     *out = nullptr;
     if (dt != QS_C64 && dt != QS_C128) return fail(QS_ERR_ARG, "bad dtype");
@@ -449,20 +459,36 @@ qs_status qs_plan_create(const qs_circuit* c, qs_dtype dt, const qs_options* opt
             }
             at += ps.mats.size() / 2;
         }
-        QS_CUDA(cudaMalloc(&p->dev_mats, total * esz));
-        cudaError_t e = cudaMemcpy(p->dev_mats, host.data(), total * esz, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-            cudaFree(p->dev_mats);
-            return cuda_fail(e, "plan matrix upload");
+        if (stream) {
+            // a pageable source is staged before the call returns, so `host` may go
+            p->stream = stream;
+            QS_CUDA(cudaMallocAsync(&p->dev_mats, total * esz, stream));
+            cudaError_t e = cudaMemcpyAsync(p->dev_mats, host.data(), total * esz, cudaMemcpyHostToDevice, stream);
+            if (e != cudaSuccess) {
+                cudaFreeAsync(p->dev_mats, stream);
+                return cuda_fail(e, "plan matrix upload");
+            }
+        } else {
+            QS_CUDA(cudaMalloc(&p->dev_mats, total * esz));
+            cudaError_t e = cudaMemcpy(p->dev_mats, host.data(), total * esz, cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(p->dev_mats);
+                return cuda_fail(e, "plan matrix upload");
+            }
         }
     }
     *out = p.release();
     return QS_OK;
 }
 
+extern "C" {
+
 qs_status qs_plan_destroy(qs_plan* p) {
     if (!p) return QS_OK;
-    if (p->dev_mats) cudaFree(p->dev_mats);
+    if (p->dev_mats) {
+        if (p->stream) cudaFreeAsync(p->dev_mats, p->stream);
+        else cudaFree(p->dev_mats);
+    }
     delete p;
     return QS_OK;
 }
@@ -533,14 +559,12 @@ qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec) 
     qs_options opt;
     qs_options_default(&opt);
     opt.precision = prec;
+    if (prec != QS_PREC_FP32 && s->dt == QS_C64) opt.k_max = 6;  // 6-qubit blocks on the tensor cores
     qs_plan* p = nullptr;
-    qs_status st = qs_plan_create(c, s->dt, &opt, &p);
+    // matrices allocated and freed in the state's stream order: no synchronisation
+    qs_status st = plan_create_on(c, s->dt, &opt, s->stream, &p);
     if (st != QS_OK) return st;
     st = qs_plan_execute(s, p);
-    if (st == QS_OK) {
-        cudaError_t e = cudaStreamSynchronize(s->stream);  // the plan's buffers are freed next
-        if (e != cudaSuccess) st = cuda_fail(e, "synchronise after circuit");
-    }
     qs_plan_destroy(p);
     return st;
 }
@@ -966,7 +990,8 @@ static void add_diag_stage(const std::vector<const GateRec*>& gates, int n, Adjo
 // first unplaced gate, a later gate joins when it commutes with every member
 // and with every gate skipped so far (disjoint qubits, or both diagonal);
 // a skipped gate obstructs its qubits.
-static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, const qs_options& fast, AdjointSweep& sw) {
+static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, const qs_options& fast,
+                                     cudaStream_t stream, AdjointSweep& sw) {
     const int G = (int)c.gates.size();
     std::vector<SweepUnit> units;  // reverse order
     for (int l = G - 1; l >= 0; --l) {
@@ -1070,7 +1095,7 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
                 inv.gates.push_back(std::move(u));
             }
             qs_plan* p = nullptr;
-            st = qs_plan_create(&inv, dt, &fast, &p);
+            st = plan_create_on(&inv, dt, &fast, stream, &p);
             if (st != QS_OK) return st;
             sw.ops.push_back({3, (int)sw.plans.size()});
             sw.plans.push_back(p);
@@ -1162,7 +1187,7 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     QS_CUDA(launch_init_basis(psi->data, psi->n, psi->dt, 0, sm));
     {
         qs_plan* p = nullptr;
-        st = qs_plan_create(c, psi->dt, &fast, &p);
+        st = plan_create_on(c, psi->dt, &fast, sm, &p);
         if (st != QS_OK) return st;
         st = qs_plan_execute(psi, p);
         cudaError_t e = cudaStreamSynchronize(sm);
@@ -1175,7 +1200,7 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     double* res = result_area(psi);
     QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
     AdjointSweep sw;
-    st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sw);
+    st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sm, sw);
     if (st != QS_OK) {
         sw.release();
         return st;
@@ -1202,6 +1227,51 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     if (st != QS_OK) return st;
     *energy = host[2 * rows];
     for (int p = 0; p < num_params; ++p) grad[p] = host[2 * p + 1];  // Im <lambda|P|psi>
+    return QS_OK;
+}
+
+qs_status qs_adjoint_gradient_batch(int count, qs_circuit* const* circuits, const double* const* thetas,
+                                    const int* num_params, const qs_pauli_sum* const* hams,
+                                    qs_state* const* psi, qs_state* const* lam, double* energies,
+                                    double* const* grads) {
+    if (count < 0) return fail(QS_ERR_ARG, "negative count");
+    if (count == 0) return QS_OK;
+    if (!circuits || !thetas || !num_params || !hams || !psi || !lam || !energies || !grads)
+        return fail(QS_ERR_ARG, "null array");
+    {  // distinct circuits (their parameters are set) and distinct states
+        std::vector<const void*> objs, mem;
+        for (int i = 0; i < count; ++i) {
+            if (!circuits[i] || !psi[i] || !lam[i]) return fail(QS_ERR_ARG, "null entry %d", i);
+            objs.push_back(circuits[i]);
+            mem.push_back(psi[i]->data);
+            mem.push_back(lam[i]->data);
+        }
+        std::sort(objs.begin(), objs.end());
+        std::sort(mem.begin(), mem.end());
+        if (std::adjacent_find(objs.begin(), objs.end()) != objs.end())
+            return fail(QS_ERR_ARG, "a circuit appears twice in the batch");
+        if (std::adjacent_find(mem.begin(), mem.end()) != mem.end())
+            return fail(QS_ERR_ARG, "a state appears twice in the batch");
+    }
+    std::vector<qs_status> status(count, QS_OK);
+    std::vector<std::string> msg(count);
+    std::atomic<int> next(0);
+    auto worker = [&]() {
+        for (int i = next++; i < count; i = next++) {
+            cudaSetDevice(psi[i]->device);
+            status[i] = qs_adjoint_gradient(circuits[i], thetas[i], num_params[i], hams[i], psi[i], lam[i],
+                                            &energies[i], grads[i]);
+            if (status[i] != QS_OK) msg[i] = qs_last_error();
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int nthreads = std::min(count, (int)std::min(16u, hw));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    for (int i = 0; i < count; ++i)
+        if (status[i] != QS_OK) return fail(status[i], "gradient %d: %s", i, msg[i].c_str());
     return QS_OK;
 }
 

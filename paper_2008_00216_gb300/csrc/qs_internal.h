@@ -122,11 +122,15 @@ struct qs_plan {
     void* dev_mats = nullptr;       // float2 or double2 matrices of all passes
     size_t dev_elems = 0;
     int device = 0;
+    cudaStream_t stream = nullptr;  // set: matrices allocated and freed in this stream's order
 };
 
 namespace qsgb {
 
 // ----------------------------------------------------------------- planner
+// qs_plan_create with the matrices uploaded and (at destruction) freed in the
+// order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
+qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
 qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);

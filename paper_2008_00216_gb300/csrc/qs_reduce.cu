@@ -513,11 +513,11 @@ cudaError_t launch_adjoint_tile(void* psi, void* lam, int n, qs_dtype dt, int L,
     if (smem > 220 * 1024) return cudaErrorInvalidValue;
     cudaError_t e;
     if (dt == QS_C64) {
-        e = cudaFuncSetAttribute(k_adj_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_dynamic_smem(k_adj_tile<float>);
         if (e != cudaSuccess) return e;
         k_adj_tile<float><<<nblocks, 256, smem, st>>>((float2*)psi, (float2*)lam, (const float2*)dmats, a, partials);
     } else {
-        e = cudaFuncSetAttribute(k_adj_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = allow_max_dynamic_smem(k_adj_tile<double>);
         if (e != cudaSuccess) return e;
         k_adj_tile<double><<<nblocks, 256, smem, st>>>((double2*)psi, (double2*)lam, (const double2*)dmats, a,
                                                         partials);

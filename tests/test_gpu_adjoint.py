@@ -87,3 +87,50 @@ def test_adjoint_mixed_circuit(qs, dtype, n, layers, nsample):
     tol = 1e-4 if dtype == "c64" else 1e-10
     assert abs(e - e_ref) < tol * max(1.0, abs(e_ref))
     assert np.linalg.norm(g[sample] - ps) / np.linalg.norm(ps) < tol, np.max(np.abs(g[sample] - ps))
+
+
+def test_adjoint_batch_matches_single_calls(qs):
+    """qs_adjoint_gradient_batch: gradients of several circuits (different n,
+    some sharing a stream) equal the single-call results; the small ones
+    also match parameter shift."""
+    import torch
+    # several 12-14 qubit circuits at once: the same kernels launched from
+    # concurrent host threads with different tile layouts and shared memory
+    specs = [(8, 3), (10, 2), (12, 2), (13, 1), (14, 1), (9, 4)] + [(12 + i % 3, 6) for i in range(12)]
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    circs, thetas, hams, psis, lams, refs = [], [], [], [], [], []
+    for i, (n, layers) in enumerate(specs):
+        theta = C.ansatz_theta(n, layers, seed=50 + i)
+        circs.append(B.circuit_from(C.ansatz_circuit(n, layers, theta)))
+        thetas.append(theta)
+        hams.append(B.PauliSum(n, C.ising_hamiltonian(n)))
+        st = streams[i % len(streams)]
+        psis.append(B.State(n, "c64", stream=st))
+        lams.append(B.State(n, "c64", stream=st, init=None))
+    for c, t, h in zip(circs, thetas, hams):
+        n = c.n
+        refs.append(B.adjoint_gradient(c, t, h, B.State(n, "c64"), B.State(n, "c64", init=None)))
+    energies, grads = B.adjoint_gradient_batch(circs, thetas, hams, psis, lams)
+    for i, (e_ref, g_ref) in enumerate(refs):
+        assert abs(energies[i] - e_ref) <= 1e-12 * max(1.0, abs(e_ref))
+        assert np.array_equal(grads[i], g_ref), i
+    for i in (0, 1):
+        n, layers = specs[i]
+        build = lambda t, n=n, layers=layers: C.ansatz_circuit(n, layers, t).gates
+        ps = oracle.parameter_shift_gradient(n, build, thetas[i], C.ising_hamiltonian(n))
+        assert np.linalg.norm(grads[i] - ps) / np.linalg.norm(ps) < 1e-4
+
+
+def test_adjoint_batch_rejects_shared_objects(qs):
+    n = 8
+    theta = C.ansatz_theta(n, 2, seed=1)
+    c = B.circuit_from(C.ansatz_circuit(n, 2, theta))
+    h = B.PauliSum(n, C.ising_hamiltonian(n))
+    s = [B.State(n, "c64") for _ in range(4)]
+    with pytest.raises(B.QsError) as e:
+        B.adjoint_gradient_batch([c, c], [theta, theta], [h, h], [s[0], s[1]], [s[2], s[3]])
+    assert e.value.status == 1
+    c2 = B.circuit_from(C.ansatz_circuit(n, 2, theta))
+    with pytest.raises(B.QsError) as e:
+        B.adjoint_gradient_batch([c, c2], [theta, theta], [h, h], [s[0], s[0]], [s[2], s[3]])
+    assert e.value.status == 1
