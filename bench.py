@@ -58,9 +58,13 @@ def parse_args(argv=None):
                     help="fp32 | 3xtf32 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of fp32 and 3xtf32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--unfused", action="store_true", help="one pass per gate (no fusion, no tiles)")
-    ap.add_argument("--circuit", choices=["grid", "grid_fixed", "ansatz"], default="grid",
+    ap.add_argument("--circuit", choices=["grid", "grid_fixed", "ansatz", "paper"], default="grid",
                     help="grid: random fSim angles; grid_fixed: fSim(pi/2, pi/6) everywhere (permutation-with-"
-                         "phase gates); ansatz: RY/RZ layers with CZ ladders (diagonal gates)")
+                         "phase gates); ansatz: RY/RZ layers with CZ ladders (diagonal gates); paper: the paper's "
+                         "gate set (H, CZ, T, sqrt X, sqrt Y), depth 1 + --depth + 1")
+    ap.add_argument("--depth", type=int, default=26, help="cycles of the paper-gate-set circuit")
+    ap.add_argument("--diag-clusters", choices=["auto", "on", "off"], default="auto",
+                    help="cluster diagonal gates of any width into one pass (Sections 4.2, 4.5); auto: timed choice")
     ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "batch_adjoint", "precision"], default="grid",
                     help="grid: the headline circuit; adjoint: gradient vs forward on the ansatz; "
                          "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q")
@@ -74,6 +78,8 @@ def workload_name(a):
         return f"ansatz{a.n}_L{a.layers}_seed{a.seed}_{a.dtype}"
     if a.circuit == "grid_fixed":
         return f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_pi2_pi6_seed{a.seed}_{a.dtype}"
+    if a.circuit == "paper":
+        return f"paper_gateset{a.n}_depth1+{a.depth}+1_seed{a.seed}_{a.dtype}"
     return f"grid{a.n}_5x6_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}" if a.n == 30 else \
         f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}"
 
@@ -210,19 +216,22 @@ def run_own(a):
         circ = C.ansatz_circuit(a.n, a.layers, C.ansatz_theta(a.n, a.layers, a.seed))
     elif a.circuit == "grid_fixed":
         circ = C.grid_circuit(a.n, a.cycles, a.seed, fixed_fsim=(math.pi / 2, math.pi / 6))
+    elif a.circuit == "paper":
+        circ = C.paper_circuit(a.n, a.depth, a.seed)
     else:
         circ = C.scale_grid_circuit(a.n, a.cycles, a.seed)
     c = B.circuit_from(circ)
     state = B.State(a.n, a.dtype)
     stream = torch.cuda.current_stream()
 
-    def plan_for(circuit, k, prec):
+    def plan_for(circuit, k, prec, dc=False):
         if a.unfused:
             return B.Plan(circuit, a.dtype, k_max=1, fuse=False, use_tile=False, precision=prec)
-        return B.Plan(circuit, a.dtype, k_max=k, tile_qubits=a.tile, use_tile=True, precision=prec)
+        return B.Plan(circuit, a.dtype, k_max=k, tile_qubits=a.tile, use_tile=True, precision=prec,
+                      diag_clusters=dc)
 
-    def make_plan(k, prec):
-        return plan_for(c, k, prec)
+    def make_plan(k, prec, dc=False):
+        return plan_for(c, k, prec, dc)
 
     # pick (k_max, precision) by timing one execution of each candidate
     # (excluded from the timed region); only modes at FP32-level accuracy
@@ -230,17 +239,19 @@ def run_own(a):
     precs = ["fp32", "3xtf32"] if a.precision == "auto" else [a.precision]
     if a.dtype == "c128":
         precs = ["fp32"]
+    dcs = {"auto": [False, True], "on": [True], "off": [False]}[a.diag_clusters]
     for k in ([a.k_max] if a.k_max else [2, 3, 4, 6]):
         for pr in precs:
             if pr != "fp32" and k < 5:
                 continue
-            cands.append((k, pr))
+            for dc in dcs:
+                cands.append((k, pr, dc))
     if len(cands) == 1 or a.unfused:
-        k_best, prec_best = cands[0]
+        k_best, prec_best, dc_best = cands[0]
     else:
         best = None
-        for k, pr in cands:
-            p = make_plan(k, pr)
+        for k, pr, dc in cands:
+            p = make_plan(k, pr, dc)
             p.execute(state)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -248,10 +259,10 @@ def run_own(a):
             torch.cuda.synchronize()
             dt = time.perf_counter() - t0
             if best is None or dt < best[0]:
-                best = (dt, k, pr)
+                best = (dt, k, pr, dc)
             p.close()
-        _, k_best, prec_best = best
-    plan = make_plan(k_best, prec_best)
+        _, k_best, prec_best, dc_best = best
+    plan = make_plan(k_best, prec_best, dc_best)
     passes = plan.passes()
     npass = len(passes)
 
@@ -322,7 +333,7 @@ def run_own(a):
         h2d = d2h = 0
         for _ in range(e2e_steps):
             cc = B.circuit_from(circ)                    # host gate list -> library
-            pp = plan_for(cc, k_best, prec_best)        # fuse + upload
+            pp = plan_for(cc, k_best, prec_best, dc_best)        # fuse + upload
             state.init_basis(0)
             pp.execute(state)
             nrm = state.norm()                           # D2H 8 bytes
@@ -350,7 +361,8 @@ def run_own(a):
             "dtype": a.dtype,
             "data": "synthetic (seeded grid circuit generator)",
             "config": {"workload": workload_name(a), "n": a.n, "cycles": a.cycles, "gates": len(circ.gates),
-                       "k_max": k_best, "precision": prec_best, "tile_qubits": a.tile or "auto", "passes": npass,
+                       "k_max": k_best, "precision": prec_best, "diag_clusters": dc_best,
+                       "tile_qubits": a.tile or "auto", "passes": npass,
                        "pass_kinds": plan.info()["per_kind"], "l2": "inputs larger than L2 (state 8 GB)",
                        "parallelism": f"replicas{world}"},
             "circuit_wall_ms": ms_step,

@@ -86,7 +86,12 @@ typedef struct qs_pauli_sum qs_pauli_sum;
  *   inject_wait_timeout : testing only, batches: 1 = the last pass of the
  *                 last wide circuit waits for a count that is never reached,
  *                 so its bounded device wait runs out (~2 s) and
- *                 qs_batch_sync reports QS_ERR_TIMEOUT.  0 in normal use.  */
+ *                 qs_batch_sync reports QS_ERR_TIMEOUT.  0 in normal use.
+ *   diag_clusters : 1 = cluster gates of a kind (Sections 4.2, 4.5):
+ *                 diagonal gates with diagonal gates, in clusters of any
+ *                 width (one wide diagonal pass each, pass kind 6), the
+ *                 other gates with each other up to k_max.  0 (default) =
+ *                 fuse any gates while their qubits fit k_max.  */
 typedef struct qs_options {
     int k_max;
     int tile_qubits;
@@ -94,7 +99,8 @@ typedef struct qs_options {
     int precision;
     int fuse;
     int inject_wait_timeout;
-    int reserved[7];
+    int diag_clusters;
+    int reserved[6];
 } qs_options;
 
 const char* qs_version(void);

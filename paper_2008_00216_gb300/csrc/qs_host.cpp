@@ -434,7 +434,8 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     std::vector<GateRec> blocks;
     qs_status st;
     if (opt.fuse) {
-        st = fuse_gates(c->n, c->gates, opt.k_max, blocks);
+        st = opt.diag_clusters ? fuse_by_kind(c->n, c->gates, opt.k_max, blocks)
+                               : fuse_gates(c->n, c->gates, opt.k_max, blocks);
         if (st != QS_OK) return st;
     } else {
         blocks = c->gates;
@@ -512,7 +513,7 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
     const Pass& ps = p->passes[i];
     if (kind) *kind = ps.kind;
     if (width) *width = ps.kind == PASS_TILE ? ps.L : ps.k;
-    if (num_gates) *num_gates = ps.kind == PASS_TILE ? (int)ps.tgates.size() : 1;
+    if (num_gates) *num_gates = ps.kind == PASS_TILE ? (int)ps.tgates.size() : ps.members;
     return QS_OK;
 }
 
@@ -544,6 +545,7 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
             case PASS_GEMM:
                 e = launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, p->opt.precision, s->errflag, s->stream);
                 break;
+            case PASS_DIAG_WIDE: e = launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream); break;
             case PASS_DENSE_SMEM:
                 e = launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
                 break;

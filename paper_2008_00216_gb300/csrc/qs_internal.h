@@ -34,6 +34,10 @@ struct GateRec {
     int kind = QS_GATE_DENSE;
     int param = -1;                 // >= 0: exp(-i theta P / 2)
     char paulis[kMaxK + 1] = {0};   // generator P (one letter per qubit)
+    // a cluster of diagonal gates of any width (k = 0, kind = diagonal): its
+    // member gates and the union of their qubits
+    std::vector<GateRec> parts;
+    uint64_t wide_mask = 0;
 };
 
 // Exact structural class of a 2^k x 2^k FP64 matrix.
@@ -87,8 +91,27 @@ enum PassKind {
     PASS_DIAG = 2,       // one diagonal gate (phase table), streaming
     PASS_MONO = 3,       // one permutation-with-phase gate
     PASS_GEMM = 4,       // one dense k in {5,6} gate on tensor cores
-    PASS_DENSE_SMEM = 5  // one dense gate via a shared-memory block GEMM (SIMT)
+    PASS_DENSE_SMEM = 5, // one dense gate via a shared-memory block GEMM (SIMT)
+    PASS_DIAG_WIDE = 6   // a cluster of diagonal gates of any width: per-chunk phase tables
 };
+
+struct DiagCross {
+    uint8_t k;
+    uint8_t q[kMaxK];      // global qubits, q[0] the most significant local bit
+    uint32_t tab;          // offset of its 2^k diagonal entries in the tables
+};
+
+// A wide diagonal pass: phase(x) = prod_c T_c[bits 8c..8c+7 of x] * prod_cross d_g(bits of g).
+// root8: every entry is exp(i pi m / 4); the tables then hold the integers m
+// (real parts) and the kernel adds exponents mod 8.
+struct WideDiag {
+    int nchunks = 0;
+    bool root8 = false;
+    std::vector<DiagCross> cross;   // tab = element offset after the chunk tables
+    uint32_t tab_elems = 0;
+};
+constexpr uint32_t kWideDiagTabElems = 3072;
+constexpr int kWideDiagCross = 48;
 
 struct TileGate {
     uint8_t k;
@@ -107,6 +130,8 @@ struct Pass {
     int L = 0;
     int pos[16] = {0};
     std::vector<TileGate> tgates;
+    WideDiag wide;                  // PASS_DIAG_WIDE
+    int members = 1;                // gates applied by a single-block pass
     // matrices (FP64 host copies; converted on upload)
     std::vector<double> mats;       // concatenated interleaved matrices
     size_t dev_offset = 0;          // element offset in the plan's device buffer
@@ -132,6 +157,11 @@ namespace qsgb {
 // order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
 qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
 qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
+// Clustering by kind (Sections 4.2, 4.5): diagonal gates join diagonal
+// clusters of any width (one wide pass each), the others fuse among
+// themselves up to k_max qubits.  Clusters on <= 6 qubits come back as
+// ordinary diagonal blocks.
+qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 int auto_tile_qubits(int n, qs_dtype dt);
@@ -155,6 +185,8 @@ cudaError_t launch_dense_smem(void* psi, int n, qs_dtype dt, int k, const int* q
                               const void* dmat, cudaStream_t st);
 cudaError_t launch_tile(void* psi, int n, qs_dtype dt, const Pass& p, const void* dmats,
                         cudaStream_t st);
+cudaError_t launch_diag_wide(void* psi, int n, qs_dtype dt, const WideDiag& w, const void* dtables,
+                             cudaStream_t st);
 // Tensor-core pass for a dense 6-qubit gate on a complex64 state (n >= 11);
 // `err` (device int) is set to 1 if a bounded device wait timed out.
 bool gemm_supported(int n, int k);
@@ -209,11 +241,6 @@ struct StageGen {
     uint32_t px, pz;       // generator on the tile's local bits: flip mask, sign mask
     int ny;                // number of Y factors
     int slot;              // parameter
-};
-struct DiagCross {
-    uint8_t k;
-    uint8_t q[kMaxK];      // global qubits, q[0] the most significant local bit
-    uint32_t tab;          // offset of its 2^k diagonal entries in the tables
 };
 // <lambda|P_g|psi> partial sums for each generator (tile over pos[0..L-1]).
 cudaError_t launch_grad_pairs(const void* psi, const void* lam, int n, qs_dtype dt, int L, const int* pos,

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <complex>
+#include <functional>
 #include <thread>
 
 #include "qs_internal.h"
@@ -94,6 +95,7 @@ void rotation_matrix(int k, const char* paulis, double theta, double* m) {
 }
 
 static inline uint64_t qmask(const GateRec& g) {
+    if (g.k == 0) return g.wide_mask;  // a wide diagonal cluster
     uint64_t m = 0;
     for (int i = 0; i < g.k; ++i) m |= 1ull << g.qubits[i];
     return m;
@@ -166,7 +168,8 @@ static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector
 // the size of non-diagonal members (diagonal ones may use up to kMaxK).
 static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<char>& placed,
                                    int start, uint64_t init_mask, int bound, int window,
-                                   int max_dense_k = kMaxK) {
+                                   int max_dense_k = kMaxK,
+                                   const std::function<bool(const GateRec&)>* accept = nullptr) {
     std::vector<int> taken;
     uint64_t support = init_mask | qmask(g[start]);
     taken.push_back(start);
@@ -181,7 +184,7 @@ static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<ch
         const bool commutes = (gm & blocked_any) == 0 && (gdiag || (gm & blocked_diag) == 0);
         const bool fits = __builtin_popcountll(support | gm) <= bound &&
                           (gdiag || g[j].k <= max_dense_k);
-        if (commutes && fits) {
+        if (commutes && fits && (!accept || (*accept)(g[j]))) {
             taken.push_back(j);
             placed[j] = 1;
             support |= gm;
@@ -196,20 +199,48 @@ static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<ch
     return taken;
 }
 
-qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out) {
+// by_kind = false: any gates fuse while their qubits fit k_max.  by_kind =
+// true: diagonal gates only with diagonal gates, in clusters of any width
+// (bounded by what one wide pass holds), the others only with each other.
+static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, std::vector<GateRec>& out) {
     if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
     out.clear();
     // 1. the scans (sequential: each one sees what the previous placed)
     std::vector<char> placed(in.size(), 0);
     std::vector<std::vector<int>> groups;
+    const int nchunks = (n + 7) / 8;
     for (int start = 0; start < (int)in.size(); ++start) {
         if (placed[start]) continue;
-        if (in[start].k > k_max) {  // wider than the bound: kept as it is
+        const bool diag = in[start].kind == QS_GATE_DIAGONAL;
+        if (in[start].k > k_max && !(by_kind && diag)) {  // wider than the bound: kept as it is
             placed[start] = 1;
             groups.push_back({-1 - start});
             continue;
         }
-        groups.push_back(scan_group(in, placed, start, 0, k_max, 1 << 14));
+        if (!by_kind) {
+            groups.push_back(scan_group(in, placed, start, 0, k_max, 1 << 14));
+        } else if (diag) {
+            // capacity of one wide pass: cross-chunk gates and table entries
+            size_t entries = 256 * (size_t)nchunks;
+            int ncross = 0;
+            auto fits = [&](const GateRec& g) {
+                bool cross = false;
+                for (int i = 1; i < g.k; ++i) cross = cross || (g.qubits[i] >> 3) != (g.qubits[0] >> 3);
+                if (!cross) return true;
+                if (ncross + 1 > kWideDiagCross || entries + (1u << g.k) > kWideDiagTabElems) return false;
+                ++ncross;
+                entries += 1u << g.k;
+                return true;
+            };
+            fits(in[start]);
+            std::function<bool(const GateRec&)> accept = [&](const GateRec& g) {
+                return g.kind == QS_GATE_DIAGONAL && fits(g);
+            };
+            groups.push_back(scan_group(in, placed, start, 0, 64, 1 << 14, kMaxK, &accept));
+        } else {
+            std::function<bool(const GateRec&)> accept = [](const GateRec& g) { return g.kind != QS_GATE_DIAGONAL; };
+            groups.push_back(scan_group(in, placed, start, 0, k_max, 1 << 14, kMaxK, &accept));
+        }
     }
     // 2. the FP64 block products, independent per group: spread over host threads
     out.resize(groups.size());
@@ -224,6 +255,17 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
         }
         uint64_t support = 0;
         for (int t : taken) support |= qmask(in[t]);
+        if (__builtin_popcountll(support) > kMaxK) {  // a wide diagonal cluster: keep its gates
+            b.k = 0;
+            b.kind = QS_GATE_DIAGONAL;
+            b.wide_mask = support;
+            for (int t : taken) {
+                b.parts.push_back(in[t]);
+                b.parts.back().param = -1;
+                b.parts.back().paulis[0] = 0;
+            }
+            return;
+        }
         b.k = __builtin_popcountll(support);
         int bq[kMaxK];
         int j = 0;
@@ -257,6 +299,71 @@ qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vect
         for (auto& th : pool) th.join();
     }
     return QS_OK;
+}
+
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out) {
+    return fuse_impl(n, in, k_max, false, out);
+}
+
+qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out) {
+    return fuse_impl(n, in, k_max, true, out);
+}
+
+// The phase tables of a wide diagonal cluster (FP64 on the host).
+static void build_wide_diag(int n, const GateRec& w, Pass& p) {
+    const int nchunks = (n + 7) / 8;
+    WideDiag& wd = p.wide;
+    wd.nchunks = nchunks;
+    // exponent m with entry = exp(i pi m / 4), or -1
+    auto root8 = [](double re, double im) {
+        for (int m = 0; m < 8; ++m) {
+            const double a = m * 0.78539816339744830962;
+            if (fabs(re - cos(a)) < 1e-14 && fabs(im - sin(a)) < 1e-14) return m;
+        }
+        return -1;
+    };
+    bool r8 = true;
+    for (const GateRec& g : w.parts) {
+        const int d = 1 << g.k;
+        for (int l = 0; l < d && r8; ++l) r8 = root8(g.m[2 * (l * d + l)], g.m[2 * (l * d + l) + 1]) >= 0;
+    }
+    wd.root8 = r8;
+    std::vector<cd> tab(256 * (size_t)nchunks, r8 ? cd(0.0) : cd(1.0)), cross;
+    for (const GateRec& g : w.parts) {
+        const int k = g.k, d = 1 << k;
+        const int c0 = g.qubits[0] >> 3;
+        bool one = true;
+        for (int i = 1; i < k; ++i) one = one && (g.qubits[i] >> 3) == c0;
+        auto entry = [&](int l) {
+            const double re = g.m[2 * (l * d + l)], im = g.m[2 * (l * d + l) + 1];
+            return r8 ? cd((double)root8(re, im), 0.0) : cd(re, im);
+        };
+        if (one) {
+            for (int jj = 0; jj < 256; ++jj) {
+                int l = 0;
+                for (int i = 0; i < k; ++i) l = (l << 1) | ((jj >> (g.qubits[i] - 8 * c0)) & 1);
+                cd& t = tab[256 * c0 + jj];
+                if (r8) t = cd(fmod(t.real() + entry(l).real(), 8.0), 0.0);
+                else t *= entry(l);
+            }
+        } else {
+            DiagCross x{};
+            x.k = (uint8_t)k;
+            for (int i = 0; i < k; ++i) x.q[i] = (uint8_t)g.qubits[i];
+            x.tab = (uint32_t)(256 * nchunks + cross.size());
+            for (int l = 0; l < d; ++l) cross.push_back(entry(l));
+            wd.cross.push_back(x);
+        }
+    }
+    tab.insert(tab.end(), cross.begin(), cross.end());
+    wd.tab_elems = (uint32_t)tab.size();
+    p.mats.clear();
+    for (const cd& z : tab) {
+        p.mats.push_back(z.real());
+        p.mats.push_back(z.imag());
+    }
+    p.k = __builtin_popcountll(w.wide_mask);
+    p.members = (int)w.parts.size();
 }
 
 // Widen a 5-qubit dense pass to 6 qubits: an identity on the lowest unused
@@ -353,10 +460,12 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
     for (int start = 0; start < (int)blocks.size(); ++start) {
         if (placed[start]) continue;
         std::vector<int> taken;
-        const bool start_ok = blocks[start].kind == QS_GATE_DIAGONAL || blocks[start].k <= kTileDenseK;
+        const bool start_ok = blocks[start].k > 0 &&
+                              (blocks[start].kind == QS_GATE_DIAGONAL || blocks[start].k <= kTileDenseK);
         if (opt.use_tile && start_ok && blocks[start].k <= L && (int)blocks.size() > 1) {
             std::vector<char> trial = placed;
-            taken = scan_group(blocks, trial, start, lowmask, L, 1 << 14, kTileDenseK);
+            std::function<bool(const GateRec&)> not_wide = [](const GateRec& g) { return g.k > 0; };
+            taken = scan_group(blocks, trial, start, lowmask, L, 1 << 14, kTileDenseK, &not_wide);
             // keep a prefix within the gate-count and shared-matrix budgets
             // (members are in circuit order, so any prefix is a valid group)
             size_t elems = 0, keep = 0;
@@ -372,7 +481,10 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
             placed[start] = 1;
         }
         Pass p;
-        if (taken.size() == 1) {
+        if (taken.size() == 1 && blocks[taken[0]].k == 0) {
+            p.kind = PASS_DIAG_WIDE;
+            build_wide_diag(n, blocks[taken[0]], p);
+        } else if (taken.size() == 1) {
             const GateRec& g = blocks[taken[0]];
             p.k = g.k;
             for (int i = 0; i < g.k; ++i) p.qubits[i] = g.qubits[i];

@@ -101,3 +101,31 @@ def test_batched_workload_ranges():
     ws = C.batched_workload(24, seed0=0)
     assert all(10 <= c.n <= 22 for c in ws)
     assert len({c.n for c in ws}) > 4
+
+
+def test_paper_circuit_rules():
+    """The paper's gate set, H layers first and last, at most one CZ per
+    qubit per cycle, T as a qubit's first gate after H, no repeated
+    one-qubit gate, seeded and deterministic."""
+    n, depth = 20, 16
+    c1 = C.paper_circuit(n, depth, seed=4)
+    c2 = C.paper_circuit(n, depth, seed=4)
+    assert [(g.qubits, g.name) for g in c1.gates] == [(g.qubits, g.name) for g in c2.gates]
+    assert {g.name for g in c1.gates} <= {"h", "cz", "t", "sqrt_x", "sqrt_y"}
+    assert [g.name for g in c1.gates[:n]] == ["h"] * n and [g.name for g in c1.gates[-n:]] == ["h"] * n
+    last = ["h"] * n
+    for g in c1.gates[n:-n]:
+        if g.name == "cz":
+            continue
+        q = g.qubits[0]
+        if last[q] == "h":
+            assert g.name == "t"
+        assert g.name != last[q]
+        last[q] = g.name
+    rows, cols = C.grid_shape(n)
+    for p in range(8):
+        pairs = C.paper_cz_layer(rows, cols, n, p)
+        qs = [q for pr in pairs for q in pr]
+        assert len(qs) == len(set(qs)) and pairs
+        for a, b in pairs:  # nearest neighbours on the grid
+            assert b - a in (1, cols) and (b - a != 1 or a // cols == b // cols)

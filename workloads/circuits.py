@@ -151,6 +151,68 @@ def scale_grid_circuit(n: int = 30, cycles: int = 14, seed: int = 1) -> Circuit:
 
 
 # --------------------------------------------------------------------------
+# circuits in the paper's benchmark gate set (H, CZ, T, sqrt(X), sqrt(Y))
+# --------------------------------------------------------------------------
+
+# CZ layer order: horizontal and vertical layers alternate
+PAPER_CZ_ORDER = (0, 4, 1, 5, 2, 6, 3, 7)
+
+
+def paper_cz_layer(rows: int, cols: int, n: int, p: int) -> List[Tuple[int, int]]:
+    """CZ layer p in 0..7 on the grid: p < 4 horizontal bonds (r,c)-(r,c+1),
+    p >= 4 vertical bonds (r,c)-(r+1,c); of those, the bonds with the moving
+    coordinate = p & 1 and the other coordinate = (p >> 1) & 1 (mod 2).  No
+    qubit is in two bonds of one layer."""
+    a, b = p & 1, (p >> 1) & 1
+    pairs = []
+    for r in range(rows):
+        for c in range(cols):
+            q = r * cols + c
+            if q >= n:
+                continue
+            if p < 4 and c % 2 == a and r % 2 == b and c + 1 < cols and q + 1 < n:
+                pairs.append((q, q + 1))
+            if p >= 4 and r % 2 == a and c % 2 == b and r + 1 < rows and q + cols < n:
+                pairs.append((q, q + cols))
+    return pairs
+
+
+def paper_circuit(n: int, depth: int = 26, seed: int = 1) -> Circuit:
+    """Depth 1 + depth + 1 in the paper's gate set: an H layer, `depth`
+    cycles, a final H layer.  Cycle c applies CZ layer PAPER_CZ_ORDER[c % 8];
+    a qubit that had a CZ in the previous cycle and has none in this one gets
+    a one-qubit gate: T the first time, afterwards a random choice among
+    {T, sqrt(X), sqrt(Y)} other than its previous one-qubit gate (seeded,
+    qubits in ascending order)."""
+    rows, cols = grid_shape(n)
+    rng = Xoshiro256ss(seed)
+    circ = Circuit(n)
+    for q in range(n):
+        circ.append((q,), G.H, "h")
+    last = ["h"] * n
+    prev_cz = set()
+    mats = {"t": G.T, "sqrt_x": G.SQRT_X, "sqrt_y": G.SQRT_Y}
+    for c in range(depth):
+        pairs = paper_cz_layer(rows, cols, n, PAPER_CZ_ORDER[c % 8])
+        now = {q for pr in pairs for q in pr}
+        for q in range(n):
+            if q in prev_cz and q not in now:
+                if last[q] == "h":
+                    g = "t"
+                else:
+                    choices = [x for x in ("t", "sqrt_x", "sqrt_y") if x != last[q]]
+                    g = choices[rng.randint(len(choices))]
+                circ.append((q,), mats[g], g)
+                last[q] = g
+        for a, b in pairs:
+            circ.append((a, b), G.CZ, "cz")
+        prev_cz = now
+    for q in range(n):
+        circ.append((q,), G.H, "h")
+    return circ
+
+
+# --------------------------------------------------------------------------
 # variational ansatz and Ising Hamiltonian
 # --------------------------------------------------------------------------
 
