@@ -122,6 +122,20 @@ __device__ __forceinline__ T rot_i(T x, int code) {
     }
     return r;
 }
+// complex128: the negations flip sign bits on the integer pipe, leaving the
+// FP64 pipe (the scarce one on this GPU) to real arithmetic
+__device__ __forceinline__ double flip_sign(double v, bool neg) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (neg ? (long long)0x8000000000000000ull : 0ll));
+}
+template <>
+__device__ __forceinline__ double2 rot_i<double2>(double2 x, int code) {
+    const int c = code & 3;
+    const bool swap = c & 1;
+    double2 r;
+    r.x = flip_sign(swap ? x.y : x.x, c == 1 || c == 2);
+    r.y = flip_sign(swap ? x.x : x.y, c >= 2);
+    return r;
+}
 
 // Error-free transformations on floats (Knuth's TwoSum, FMA-based TwoProd)
 // for a two-float accumulator: the "sum-of-two-values" representation that

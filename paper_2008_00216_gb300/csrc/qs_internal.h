@@ -101,16 +101,19 @@ struct DiagCross {
     uint32_t tab;          // offset of its 2^k diagonal entries in the tables
 };
 
-// A wide diagonal pass: phase(x) = prod_c T_c[bits 8c..8c+7 of x] * prod_cross d_g(bits of g).
-// root8: every entry is exp(i pi m / 4); the tables then hold the integers m
-// (real parts) and the kernel adds exponents mod 8.
+// A wide diagonal pass: phase(x) = prod_c T_c[chunk c of x] * prod_cross d_g(bits of g),
+// chunks of 8 index bits.  root8: every entry is exp(i pi m / 4); the
+// tables then hold the integers m (real parts), chunks are 10 bits wide, and
+// the kernel adds exponents mod 8.
 struct WideDiag {
     int nchunks = 0;
+    int chunk_bits = 8;             // 10 when root8
     bool root8 = false;
-    std::vector<DiagCross> cross;   // tab = element offset after the chunk tables
+    std::vector<DiagCross> cross;   // gates spanning chunks; tab = element offset after the chunk tables
     uint32_t tab_elems = 0;
 };
-constexpr uint32_t kWideDiagTabElems = 3072;
+constexpr uint32_t kWideDiagTabElems = 3072;       // complex tables (shared memory)
+constexpr uint32_t kWideDiagRoot8Elems = 8192;     // exponent tables (one byte each in shared memory)
 constexpr int kWideDiagCross = 48;
 
 struct TileGate {

@@ -224,8 +224,10 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
             size_t entries = 256 * (size_t)nchunks;
             int ncross = 0;
             auto fits = [&](const GateRec& g) {
+                // spans a chunk boundary of the complex (8-bit) or exponent (10-bit) tables
                 bool cross = false;
-                for (int i = 1; i < g.k; ++i) cross = cross || (g.qubits[i] >> 3) != (g.qubits[0] >> 3);
+                for (int i = 1; i < g.k; ++i)
+                    cross = cross || (g.qubits[i] >> 3) != (g.qubits[0] >> 3) || g.qubits[i] / 10 != g.qubits[0] / 10;
                 if (!cross) return true;
                 if (ncross + 1 > kWideDiagCross || entries + (1u << g.k) > kWideDiagTabElems) return false;
                 ++ncross;
@@ -311,9 +313,7 @@ qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::ve
 
 // The phase tables of a wide diagonal cluster (FP64 on the host).
 static void build_wide_diag(int n, const GateRec& w, Pass& p) {
-    const int nchunks = (n + 7) / 8;
     WideDiag& wd = p.wide;
-    wd.nchunks = nchunks;
     // exponent m with entry = exp(i pi m / 4), or -1
     auto root8 = [](double re, double im) {
         for (int m = 0; m < 8; ++m) {
@@ -328,21 +328,25 @@ static void build_wide_diag(int n, const GateRec& w, Pass& p) {
         for (int l = 0; l < d && r8; ++l) r8 = root8(g.m[2 * (l * d + l)], g.m[2 * (l * d + l) + 1]) >= 0;
     }
     wd.root8 = r8;
-    std::vector<cd> tab(256 * (size_t)nchunks, r8 ? cd(0.0) : cd(1.0)), cross;
+    const int cb = r8 ? 10 : 8, csz = 1 << cb;
+    wd.chunk_bits = cb;
+    const int nchunks = (n + cb - 1) / cb;
+    wd.nchunks = nchunks;
+    std::vector<cd> tab(csz * (size_t)nchunks, r8 ? cd(0.0) : cd(1.0)), cross;
     for (const GateRec& g : w.parts) {
         const int k = g.k, d = 1 << k;
-        const int c0 = g.qubits[0] >> 3;
+        const int c0 = g.qubits[0] / cb;
         bool one = true;
-        for (int i = 1; i < k; ++i) one = one && (g.qubits[i] >> 3) == c0;
+        for (int i = 1; i < k; ++i) one = one && g.qubits[i] / cb == c0;
         auto entry = [&](int l) {
             const double re = g.m[2 * (l * d + l)], im = g.m[2 * (l * d + l) + 1];
             return r8 ? cd((double)root8(re, im), 0.0) : cd(re, im);
         };
         if (one) {
-            for (int jj = 0; jj < 256; ++jj) {
+            for (int jj = 0; jj < csz; ++jj) {
                 int l = 0;
-                for (int i = 0; i < k; ++i) l = (l << 1) | ((jj >> (g.qubits[i] - 8 * c0)) & 1);
-                cd& t = tab[256 * c0 + jj];
+                for (int i = 0; i < k; ++i) l = (l << 1) | ((jj >> (g.qubits[i] - cb * c0)) & 1);
+                cd& t = tab[(size_t)csz * c0 + jj];
                 if (r8) t = cd(fmod(t.real() + entry(l).real(), 8.0), 0.0);
                 else t *= entry(l);
             }
@@ -350,7 +354,7 @@ static void build_wide_diag(int n, const GateRec& w, Pass& p) {
             DiagCross x{};
             x.k = (uint8_t)k;
             for (int i = 0; i < k; ++i) x.q[i] = (uint8_t)g.qubits[i];
-            x.tab = (uint32_t)(256 * nchunks + cross.size());
+            x.tab = (uint32_t)((size_t)csz * nchunks + cross.size());
             for (int l = 0; l < d; ++l) cross.push_back(entry(l));
             wd.cross.push_back(x);
         }
