@@ -240,7 +240,7 @@ def run_own(a):
     if a.dtype == "c128":
         precs = ["fp32"]
     dcs = {"auto": [False, True], "on": [True], "off": [False]}[a.diag_clusters]
-    for k in ([a.k_max] if a.k_max else [2, 3, 4, 6]):
+    for k in ([a.k_max] if a.k_max else [1, 2, 3, 4, 6]):
         for pr in precs:
             if pr != "fp32" and k < 5:
                 continue

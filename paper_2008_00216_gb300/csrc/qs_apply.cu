@@ -452,6 +452,10 @@ struct TileArgs {
     int pos[16];           // global bit of local bit i (ascending)
     uint32_t mat_elems;    // complex entries of all the pass's matrices
     uint64_t ntiles;
+    int scale_mode;        // 0 none, 1 mag * exp(i pi s / 4), 2 general complex
+    int scale_s;
+    double scale_mag;      // for mode 1: |scale|, times 1/sqrt(2) when s is odd
+    double scale_c[2];
     TileGate g[kMaxTileGates];
 };
 
@@ -486,6 +490,8 @@ __global__ void __launch_bounds__(256) k_tile(typename C2<R>::T* __restrict__ ps
             const T* m = smat + g.mat;
             if (g.kind == QS_GATE_DIAGONAL) {
                 tile_diag(tile, L, g, m);
+            } else if (g.kind == kTileMulfree) {
+                tile_mulfree1(tile, L, g, m);
             } else {  // dense or monomial, k <= 4, through registers
                 switch (g.k) {
                     case 1: tile_dense<T, 1>(tile, L, g, m); break;
@@ -497,8 +503,31 @@ __global__ void __launch_bounds__(256) k_tile(typename C2<R>::T* __restrict__ ps
             }
             __syncthreads();
         }
-        for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x)
-            psi[base + rowoff[e >> b] + (e & (rowlen - 1))] = tile[e];
+        if (a.scale_mode == 0) {
+            for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x)
+                psi[base + rowoff[e >> b] + (e & (rowlen - 1))] = tile[e];
+        } else {  // the scalars factored out of the pass's multiply-free gates
+            const R mag = (R)a.scale_mag;
+            T c;
+            c.x = (R)a.scale_c[0];
+            c.y = (R)a.scale_c[1];
+            for (uint32_t e = threadIdx.x; e < (1u << L); e += blockDim.x) {
+                T v = tile[e];
+                if (a.scale_mode == 1) {
+                    v = rot_i(v, a.scale_s >> 1);
+                    if (a.scale_s & 1) {  // times (1 + i) (the 1/sqrt(2) is in mag)
+                        const R re = v.x - v.y, im = v.x + v.y;
+                        v.x = re;
+                        v.y = im;
+                    }
+                    v.x *= mag;
+                    v.y *= mag;
+                } else {
+                    v = cmul(c, v);
+                }
+                psi[base + rowoff[e >> b] + (e & (rowlen - 1))] = v;
+            }
+        }
         __syncthreads();
     }
 }
@@ -515,6 +544,11 @@ cudaError_t launch_tile(void* psi, int n, qs_dtype dt, const Pass& ps, const voi
     for (int i = 0; i < a.ngates; ++i) a.g[i] = ps.tgates[i];
     a.ntiles = 1ull << (n - ps.L);
     a.mat_elems = (uint32_t)(ps.mats.size() / 2);
+    a.scale_mode = ps.scale_mode;
+    a.scale_s = ps.scale_s;
+    a.scale_mag = ps.scale_mag * ((ps.scale_s & 1) ? 0.70710678118654752440 : 1.0);
+    a.scale_c[0] = ps.scale_c[0];
+    a.scale_c[1] = ps.scale_c[1];
     const size_t esz = dt == QS_C64 ? 8 : 16;
     const size_t smem = esz * ((1u << ps.L) + a.mat_elems) + sizeof(uint64_t) * (1u << (ps.L - b));
     if (smem > 200 * 1024) return cudaErrorInvalidValue;

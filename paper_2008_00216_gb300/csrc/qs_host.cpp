@@ -442,6 +442,7 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     }
     st = build_passes(c->n, dt, blocks, opt, p->passes);
     if (st != QS_OK) return st;
+    for (Pass& ps : p->passes) factor_tile_scalars(ps);
     // upload every pass's matrices, converted to the state's precision
     size_t total = 0;
     for (Pass& ps : p->passes) {

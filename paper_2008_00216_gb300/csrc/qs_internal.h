@@ -118,10 +118,13 @@ constexpr int kWideDiagCross = 48;
 
 struct TileGate {
     uint8_t k;
-    uint8_t kind;         // QS_GATE_*
+    uint8_t kind;         // QS_GATE_*, or kTileMulfree
     uint8_t q[kMaxK];     // tile-local bit positions (Kronecker order)
     uint32_t mat;         // element offset of the matrix in the pass buffer
 };
+// tile gate kind: a one-qubit matrix with entries in {0, +-1, +-i} (its
+// scalar factor moved to the pass's scale), applied without multiplies
+constexpr uint8_t kTileMulfree = 8;
 
 struct Pass {
     int kind = PASS_DENSE;
@@ -135,6 +138,12 @@ struct Pass {
     std::vector<TileGate> tgates;
     WideDiag wide;                  // PASS_DIAG_WIDE
     int members = 1;                // gates applied by a single-block pass
+    // tile passes: product of the scalars factored out of kTileMulfree gates,
+    // applied at write-back.  mode 1: mag * exp(i pi s / 4); mode 2: scale_c
+    int scale_mode = 0;
+    int scale_s = 0;
+    double scale_mag = 1.0;
+    double scale_c[2] = {1.0, 0.0};
     // matrices (FP64 host copies; converted on upload)
     std::vector<double> mats;       // concatenated interleaved matrices
     size_t dev_offset = 0;          // element offset in the plan's device buffer
@@ -168,6 +177,10 @@ qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::ve
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 int auto_tile_qubits(int n, qs_dtype dt);
+// Section 4.1: one-qubit tile gates that are a scalar times a matrix with
+// entries in {0, +-1, +-i} (H, sqrt X, sqrt Y, X, Y, ...) become kTileMulfree
+// gates; the pass keeps the product of their scalars.
+void factor_tile_scalars(Pass& p);
 // Greedy commuting-reorder grouping of `units` (in order) into tiles of L
 // qubits that always contain the lowest `low_bits_in_tile` qubits; dense
 // members have k <= 4; each group's matrices fit `mat_budget` entries.

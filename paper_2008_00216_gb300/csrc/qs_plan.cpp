@@ -370,6 +370,58 @@ static void build_wide_diag(int n, const GateRec& w, Pass& p) {
     p.members = (int)w.parts.size();
 }
 
+void factor_tile_scalars(Pass& p) {
+    if (p.kind != PASS_TILE) return;
+    cd total = 1.0;
+    bool any = false;
+    for (TileGate& tg : p.tgates) {
+        if (tg.k != 1 || tg.kind == QS_GATE_DIAGONAL) continue;
+        const double* m = p.mats.data() + 2 * (size_t)tg.mat;
+        cd e[4], c = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            e[i] = cd(m[2 * i], m[2 * i + 1]);
+            if (c == 0.0 && std::abs(e[i]) > 0) c = e[i];
+        }
+        bool ok = true;
+        cd u[4];
+        for (int i = 0; i < 4 && ok; ++i) {
+            u[i] = e[i] / c;
+            const cd cand[5] = {0.0, 1.0, cd(0, 1), -1.0, cd(0, -1)};
+            bool hit = false;
+            for (const cd& z : cand)
+                if (std::abs(u[i] - z) < 1e-14) {
+                    u[i] = z;
+                    hit = true;
+                }
+            ok = hit;
+        }
+        if (!ok) continue;
+        double* w = p.mats.data() + 2 * (size_t)tg.mat;
+        for (int i = 0; i < 4; ++i) {
+            w[2 * i] = u[i].real();
+            w[2 * i + 1] = u[i].imag();
+        }
+        tg.kind = kTileMulfree;
+        total *= c;
+        any = true;
+    }
+    if (!any) return;
+    const double mag = std::abs(total);
+    const cd ph = total / mag;
+    for (int s = 0; s < 8; ++s) {
+        const double a = s * 0.78539816339744830962;
+        if (std::abs(ph - cd(cos(a), sin(a))) < 1e-13) {
+            p.scale_mode = 1;
+            p.scale_s = s;
+            p.scale_mag = mag;
+            return;
+        }
+    }
+    p.scale_mode = 2;
+    p.scale_c[0] = total.real();
+    p.scale_c[1] = total.imag();
+}
+
 // Widen a 5-qubit dense pass to 6 qubits: an identity on the lowest unused
 // qubit, placed first (most significant), so the matrix is kron(I2, M).
 static void pad_to_six(int n, Pass& p) {

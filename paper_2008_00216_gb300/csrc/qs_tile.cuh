@@ -8,6 +8,35 @@
 
 namespace qsgb {
 
+// One-qubit gate with entries in {0, +-1, +-i} (its scalar factored out):
+// out0 = u00 a + u01 b, out1 = u10 a + u11 b with each product a swap and
+// sign flips (Section 4.1), so a pair costs four additions.
+template <typename T>
+__device__ __forceinline__ int mulfree_code(T u) {  // -1: zero, else u = i^code
+    return (u.x == 0 && u.y == 0) ? -1 : u.x == 1 ? 0 : u.y == 1 ? 1 : u.x == -1 ? 2 : 3;
+}
+template <typename T>
+__device__ __forceinline__ T mulfree_sum(T a, int ca, T b, int cb) {
+    if (ca < 0) return rot_i(b, cb);
+    if (cb < 0) return rot_i(a, ca);
+    const T x = rot_i(a, ca), y = rot_i(b, cb);
+    T r;
+    r.x = x.x + y.x;
+    r.y = x.y + y.y;
+    return r;
+}
+template <typename T>
+__device__ __forceinline__ void tile_mulfree1(T* tile, int L, const TileGate& g, const T* m) {
+    const int c00 = mulfree_code(m[0]), c01 = mulfree_code(m[1]), c10 = mulfree_code(m[2]), c11 = mulfree_code(m[3]);
+    const int q = g.q[0];
+    for (uint32_t s = threadIdx.x; s < (1u << (L - 1)); s += blockDim.x) {
+        const uint32_t i0 = insert_zero32(s, q), i1 = i0 | (1u << q);
+        const T a = tile[i0], b = tile[i1];
+        tile[i0] = mulfree_sum(a, c00, b, c01);
+        tile[i1] = mulfree_sum(a, c10, b, c11);
+    }
+}
+
 // dense gate with K <= 4 on the shared tile, one set per thread iteration
 template <typename T, int K>
 __device__ __forceinline__ void tile_dense(T* tile, int L, const TileGate& g, const T* m) {

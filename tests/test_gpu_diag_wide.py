@@ -64,3 +64,26 @@ def test_clusters_with_tensor_passes(qs):
     ref = oracle.simulate(n, circ.gates)
     got, info = run_plan(circ, "c64", k_max=6, precision="3xtf32", diag_clusters=True)
     assert rel_l2(got, ref) < TOL["c64"], info
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [11, 15])
+def test_multiply_free_tile_gates(qs, dtype, n):
+    """Section 4.1: one-qubit gates that are a scalar times a {0, +-1, +-i}
+    matrix (H, sqrt X, sqrt Y, X, Y, and H times an arbitrary phase, whose
+    scalar is not an eighth root) run without multiplies in tile passes;
+    each pass multiplies the product of the scalars at write-back."""
+    rng = Xoshiro256ss(300 + n)
+    psi0 = random_state(n, 7 + n)
+    circ = C.Circuit(n)
+    odd_h = np.exp(0.3j) * G.H
+    pool = [G.H, G.SQRT_X, G.SQRT_Y, G.X, G.Y, odd_h]
+    for layer in range(6):
+        for q in range(n):
+            circ.append((q,), pool[rng.randint(len(pool))])
+        for q in range(layer % 2, n - 1, 2):
+            circ.append((q, q + 1), G.CZ)
+    ref = oracle.simulate(n, circ.gates, psi0)
+    for dc in (False, True):
+        got, info = run_plan(circ, dtype, psi0=psi0, k_max=1, diag_clusters=dc)
+        assert rel_l2(got, ref) < TOL[dtype], (dc, info)
