@@ -84,6 +84,23 @@ def workload_name(a):
         f"grid{a.n}_c{a.cycles}_ABCDCDAB_fsim_random_seed{a.seed}_{a.dtype}"
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum over ranks of per-rank values (the slowest
+    rank's times); the identity without an initialised process group."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    if dist.is_available() and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_throughput(world, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -297,11 +314,7 @@ def run_own(a):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks([ev0.elapsed_time(ev1)], "cuda")[0]
 
     # per-pass durations from the events recorded inside the timed region
     by_kind = {}
@@ -321,7 +334,7 @@ def run_own(a):
     peak, peak_src = measured_peaks()
     achieved = 2 * state_bytes / (avg_ms * 1e-3) / 1e9
     ms_step = elapsed_ms / a.steps
-    value = world * a.steps / (elapsed_ms * 1e-3)
+    value = replica_throughput(world, a.steps, elapsed_ms * 1e-3)
     step_bytes = (npass * 2 + 2) * state_bytes   # passes r+w, init write, norm read
 
     # end to end through the public API with host buffers
@@ -342,8 +355,8 @@ def run_own(a):
             d2h = 8 + 4096 * esz
             pp.close(); cc.close()
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
-        e2e = {"value": world / e2e_s, "unit": "circuits/s", "h2d_bytes_per_step": h2d,
+        e2e_s = max_over_ranks([(time.perf_counter() - t0) / e2e_steps], "cuda")[0]
+        e2e = {"value": replica_throughput(world, 1, e2e_s), "unit": "circuits/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3}
 
     if rank == 0:
