@@ -9,17 +9,25 @@ namespace qsgb {
 // Allow a kernel the device's whole opt-in shared memory (minus its static
 // shared memory).  The attribute is one value per kernel for the process,
 // so every caller sets the same value: launches from concurrent host
-// threads with different dynamic sizes cannot undercut each other.
+// threads with different dynamic sizes cannot undercut each other.  Done
+// once per kernel and device (the runtime calls cost microseconds).
+bool smem_attr_done(const void* kernel, int device);
+void smem_attr_mark(const void* kernel, int device);   // after the attribute is set
 template <typename K>
 inline cudaError_t allow_max_dynamic_smem(K kernel) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (smem_attr_done(reinterpret_cast<const void*>(kernel), dev)) return cudaSuccess;
+    // first callers on several threads may all get here: they set one value
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    if (e != cudaSuccess) return e;
-    int dev = 0, optin = 0;
-    e = cudaGetDevice(&dev);
+    e = cudaFuncGetAttributes(&fa, kernel);
+    int optin = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) smem_attr_mark(reinterpret_cast<const void*>(kernel), dev);
+    return e;
 }
 
 template <typename R> struct C2;

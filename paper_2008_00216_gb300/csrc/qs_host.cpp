@@ -11,6 +11,8 @@
 #include <string>
 #include <thread>
 #include <map>
+#include <mutex>
+#include <set>
 #include <memory>
 #include <new>
 
@@ -43,6 +45,34 @@ qs_status cuda_fail(cudaError_t e, const char* what) {
     set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return QS_ERR_OOM;
     return QS_ERR_CUDA;
+}
+
+// kernels whose dynamic shared-memory limit is already raised, per device
+static std::mutex g_attr_mu;
+static std::set<std::pair<const void*, int>> g_attr_done;
+
+bool smem_attr_done(const void* kernel, int device) {
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    return g_attr_done.count({kernel, device}) != 0;
+}
+
+void smem_attr_mark(const void* kernel, int device) {
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    g_attr_done.insert({kernel, device});
+}
+
+static thread_local unsigned g_thread_cap = 0;  // 0: none
+
+unsigned host_threads(unsigned cap) {
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    if (g_thread_cap) hw = std::min(hw, g_thread_cap);
+    return std::min(hw, cap);
+}
+
+unsigned set_host_thread_cap(unsigned cap) {
+    const unsigned prev = g_thread_cap;
+    g_thread_cap = cap;
+    return prev;
 }
 
 int num_sms() {
@@ -1016,6 +1046,7 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
     };
     const uint64_t all = n >= 64 ? ~0ull : (1ull << n) - 1;
     std::vector<char> placed(units.size(), 0);
+    std::vector<qs_circuit> invs;  // inverse of each general stage, planned at the end
     std::vector<int> segment;  // pending tile-sweep gates (circuit indices, sweep order)
     auto flush_segment = [&]() -> qs_status {
         if (segment.empty()) return QS_OK;
@@ -1080,8 +1111,8 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
             for (size_t j : stage) segment.push_back(units[j].fwd);
             continue;
         }
-        qs_status st = flush_segment();
-        if (st != QS_OK) return st;
+        qs_status fst = flush_segment();
+        if (fst != QS_OK) return fst;
         std::vector<const GateRec*> gates;
         for (size_t j : stage) gates.push_back(&c.gates[units[j].fwd]);
         if (all_diag) {
@@ -1097,14 +1128,34 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
                 u.paulis[0] = 0;
                 inv.gates.push_back(std::move(u));
             }
-            qs_plan* p = nullptr;
-            st = plan_create_on(&inv, dt, &fast, stream, &p);
-            if (st != QS_OK) return st;
-            sw.ops.push_back({3, (int)sw.plans.size()});
-            sw.plans.push_back(p);
+            sw.ops.push_back({3, (int)invs.size()});
+            invs.push_back(std::move(inv));
         }
     }
-    return flush_segment();
+    qs_status st = flush_segment();
+    if (st != QS_OK) return st;
+    // the stages' inverse plans are independent: fused on host threads
+    sw.plans.assign(invs.size(), nullptr);
+    std::vector<qs_status> sts(invs.size(), QS_OK);
+    std::vector<std::string> msgs(invs.size());
+    std::atomic<size_t> next(0);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (size_t i = next++; i < invs.size(); i = next++) {
+            sts[i] = plan_create_on(&invs[i], dt, &fast, stream, &sw.plans[i]);
+            if (sts[i] != QS_OK) msgs[i] = qs_last_error();
+        }
+    };
+    const size_t nthreads = std::min<size_t>((size_t)host_threads(8), invs.size());
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nthreads; ++t) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    for (size_t i = 0; i < invs.size(); ++i)
+        if (sts[i] != QS_OK) return fail(sts[i], "stage plan: %s", msgs[i].c_str());
+    return QS_OK;
 }
 
 // Device phase: one upload of the tile-sweep matrices and the phase tables,
@@ -1187,17 +1238,20 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
         fast.k_max = 6;
         fast.precision = QS_PREC_3XTF32;
     }
-    QS_CUDA(launch_init_basis(psi->data, psi->n, psi->dt, 0, sm));
-    {
-        qs_plan* p = nullptr;
-        st = plan_create_on(c, psi->dt, &fast, sm, &p);
-        if (st != QS_OK) return st;
-        st = qs_plan_execute(psi, p);
-        cudaError_t e = cudaStreamSynchronize(sm);
-        qs_plan_destroy(p);
-        if (st != QS_OK) return st;
-        if (e != cudaSuccess) return cuda_fail(e, "forward pass");
+    // forward and lambda are enqueued first; the reverse sweep is planned on
+    // the host while the GPU runs them (plan memory is stream-ordered, so
+    // nothing here synchronises)
+    qs_plan* fwd = nullptr;
+    st = plan_create_on(c, psi->dt, &fast, sm, &fwd);
+    if (st != QS_OK) return st;
+    cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
+    if (le != cudaSuccess) {
+        qs_plan_destroy(fwd);
+        return cuda_fail(le, "init");
     }
+    st = qs_plan_execute(psi, fwd);
+    qs_plan_destroy(fwd);  // freed in stream order, after the forward passes
+    if (st != QS_OK) return st;
     // lambda = H psi; E = <psi|lambda>
     QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
     double* res = result_area(psi);
@@ -1260,12 +1314,14 @@ qs_status qs_adjoint_gradient_batch(int count, qs_circuit* const* circuits, cons
     std::vector<std::string> msg(count);
     std::atomic<int> next(0);
     auto worker = [&]() {
+        const unsigned prev = set_host_thread_cap(1);  // the gradients themselves run in parallel
         for (int i = next++; i < count; i = next++) {
             cudaSetDevice(psi[i]->device);
             status[i] = qs_adjoint_gradient(circuits[i], thetas[i], num_params[i], hams[i], psi[i], lam[i],
                                             &energies[i], grads[i]);
             if (status[i] != QS_OK) msg[i] = qs_last_error();
         }
+        set_host_thread_cap(prev);
     };
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     const int nthreads = std::min(count, (int)std::min(16u, hw));

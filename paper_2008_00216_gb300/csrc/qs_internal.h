@@ -270,4 +270,10 @@ cudaError_t launch_diag_stage(void* psi, void* lam, int n, qs_dtype dt, int nchu
 
 int num_sms();
 
+// Host threads a planning step may use (fusion products, stage plans): the
+// hardware's, at most `cap`; workers that already run in parallel (batched
+// gradients) set the calling thread's cap to 1.
+unsigned host_threads(unsigned cap);
+unsigned set_host_thread_cap(unsigned cap);   // returns the previous cap
+
 }  // namespace qsgb

@@ -287,8 +287,7 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
     };
     size_t work = 0;
     for (const auto& g : groups) work += g.size();
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const unsigned nthreads = (unsigned)std::min<size_t>({(size_t)hw, (size_t)16, groups.size(), work / 64 + 1});
+    const unsigned nthreads = (unsigned)std::min<size_t>({(size_t)host_threads(16), groups.size(), work / 64 + 1});
     if (nthreads <= 1) {
         for (size_t gi = 0; gi < groups.size(); ++gi) build(gi);
     } else {
