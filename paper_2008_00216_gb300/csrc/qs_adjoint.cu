@@ -141,16 +141,6 @@ struct DiagStageArgs {
     int mslot[kDiagMulti];
 };
 
-template <typename T>
-__device__ __forceinline__ T cross_phase(const DiagCross* cg, int count, const T* tab, uint64_t x, T ph) {
-    for (int c = 0; c < count; ++c) {
-        uint32_t li = 0;
-        for (int i = 0; i < cg[c].k; ++i) li = (li << 1) | (uint32_t)((x >> cg[c].q[i]) & 1);
-        ph = cmul(ph, tab[cg[c].tab + li]);
-    }
-    return ph;
-}
-
 // Gradients: Im <lambda|Z_g|psi> = sum_x (-1)^popc(x & zm_g) Im(conj(lambda_x) psi_x).
 // Inverse: psi_x, lambda_x *= prod_c T_c[bits of chunk c] * prod_cross d_g[its bits].
 // For n >= 10 a warp walks blocks of 1024 amplitudes: lane = index bits 0-4,

@@ -108,6 +108,19 @@ __device__ __forceinline__ T cmul(T m, T x) {
     return r;
 }
 
+// ph times the diagonal entries of `count` gates at index x; gate c has k
+// qubits q[0..k) (q[0] the most significant local bit) and its 2^k entries
+// at tab[cg[c].tab].
+template <typename T, typename X>
+__device__ __forceinline__ T cross_phase(const X* cg, int count, const T* tab, uint64_t x, T ph) {
+    for (int c = 0; c < count; ++c) {
+        uint32_t li = 0;
+        for (int i = 0; i < cg[c].k; ++i) li = (li << 1) | (uint32_t)((x >> cg[c].q[i]) & 1);
+        ph = cmul(ph, tab[cg[c].tab + li]);
+    }
+    return ph;
+}
+
 // acc += m * x (complex), as four fused multiply-adds
 template <typename T>
 __device__ __forceinline__ void cmac(T& acc, T m, T x) {

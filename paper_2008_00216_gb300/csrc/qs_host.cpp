@@ -779,8 +779,16 @@ struct DiagLaunch {
 };
 
 struct SweepOp {
-    int type = 0;              // 0 tile pass, 1 gradient pass, 2 diagonal stage, 3 plan on both states
+    int type = 0;              // 0 tile pass, 1 gradient pass, 2 diagonal stage, 3 plan on both states,
+                               // 4 fused sweep pass
     int index = 0;
+};
+
+// A stage for the fused sweep pass: its non-diagonal one-qubit gates and its
+// diagonal gates (circuit indices).
+struct FusedStage {
+    std::vector<int> one;
+    std::vector<int> diag;
 };
 
 }  // namespace
@@ -789,6 +797,7 @@ struct AdjointSweep {
     std::vector<AdjPass> tile;
     std::vector<GradLaunch> grad;
     std::vector<DiagLaunch> diag;
+    std::vector<SweepPassDesc> fused;
     std::vector<qs_plan*> plans;
     std::vector<SweepOp> ops;
     std::vector<double> allm, tables;
@@ -1018,6 +1027,251 @@ static void add_diag_stage(const std::vector<const GateRec*>& gates, int n, Adjo
     sw.diag.push_back(std::move(dl));
 }
 
+// Cost of a stage's diagonal gates as one DIAG op of a fused pass: table
+// entries, gates spanning two 8-qubit chunks, Z generators.
+struct DiagCost {
+    uint32_t tab = 0;
+    int cross = 0, gens = 0;
+};
+static DiagCost fused_diag_cost(const qs_circuit& c, const std::vector<int>& diag, int n) {
+    DiagCost dc;
+    if (diag.empty()) return dc;
+    dc.tab = 256u * (uint32_t)((n + 7) / 8);
+    for (int gi : diag) {
+        const GateRec& g = c.gates[gi];
+        bool one_chunk = true;
+        for (int i = 1; i < g.k; ++i) one_chunk = one_chunk && (g.qubits[i] >> 3) == (g.qubits[0] >> 3);
+        if (!one_chunk) {
+            dc.cross++;
+            dc.tab += 1u << g.k;
+        }
+        dc.gens += g.param >= 0;
+    }
+    return dc;
+}
+
+// The DIAG op of `diag` for a pass whose registers hold the global qubits
+// `rq[0..RB)` (register bit k = rq[k]): chunk tables and cross gates of the
+// members' inverses appended to p.tabs / p.cross, Z generators to p.gens.
+static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag, int n, const int* rq, int RB,
+                               SweepPassDesc& p) {
+    const int nchunks = (n + 7) / 8;
+    uint64_t rmask = 0;
+    for (int k = 0; k < RB; ++k) rmask |= 1ull << rq[k];
+    SweepDiagRec d{};
+    d.nchunks = (uint8_t)nchunks;
+    for (int k = 0; k < RB; ++k) d.touched |= (uint8_t)(1u << (rq[k] >> 3));
+    d.tab = (uint32_t)(p.tabs.size() / 2);
+    std::vector<std::complex<double>> tab(256 * (size_t)nchunks, 1.0);
+    struct Cross { DiagCross x; std::vector<std::complex<double>> e; bool touched; };
+    std::vector<Cross> cross;
+    for (int gi : diag) {
+        GateRec u;
+        conj_transpose(c.gates[gi], u);
+        const int k = u.k, dd = 1 << k, c0 = u.qubits[0] >> 3;
+        bool one_chunk = true, touched = false;
+        for (int i = 0; i < k; ++i) {
+            one_chunk = one_chunk && (u.qubits[i] >> 3) == c0;
+            touched = touched || ((rmask >> u.qubits[i]) & 1);
+        }
+        if (one_chunk) {
+            for (int j = 0; j < 256; ++j) {
+                int l = 0;
+                for (int i = 0; i < k; ++i) l = (l << 1) | ((j >> (u.qubits[i] - 8 * c0)) & 1);
+                tab[256 * c0 + j] *= std::complex<double>(u.m[2 * (l * dd + l)], u.m[2 * (l * dd + l) + 1]);
+            }
+        } else {
+            Cross x{};
+            x.x.k = (uint8_t)k;
+            for (int i = 0; i < k; ++i) x.x.q[i] = (uint8_t)u.qubits[i];
+            for (int l = 0; l < dd; ++l) x.e.emplace_back(u.m[2 * (l * dd + l)], u.m[2 * (l * dd + l) + 1]);
+            x.touched = touched;
+            cross.push_back(std::move(x));
+        }
+    }
+    // the gates that hold a register qubit first: the kernel looks those up per amplitude
+    std::stable_partition(cross.begin(), cross.end(), [](const Cross& x) { return x.touched; });
+    d.cross0 = (uint16_t)p.cross.size();
+    for (const Cross& x : cross) {
+        d.nct += x.touched;
+        DiagCross dc = x.x;
+        dc.tab = (uint32_t)(p.tabs.size() / 2 + tab.size());
+        tab.insert(tab.end(), x.e.begin(), x.e.end());
+        p.cross.push_back(dc);
+        d.ncross++;
+    }
+    for (const auto& z : tab) {
+        p.tabs.push_back(z.real());
+        p.tabs.push_back(z.imag());
+    }
+    d.gen0 = (uint16_t)p.gens.size();
+    for (int gi : diag) {
+        const GateRec& g = c.gates[gi];
+        if (g.param < 0) continue;
+        uint64_t zm = 0;
+        for (int i = 0; i < g.k; ++i)
+            if (g.paulis[i] == 'Z') zm |= 1ull << g.qubits[i];
+        SweepZGen z{};
+        z.mthr = zm & ~rmask;
+        uint32_t zr = 0;  // register bits of the mask
+        for (int k = 0; k < RB; ++k)
+            if ((zm >> rq[k]) & 1) zr |= 1u << k;
+        if (zr == 0) {
+            z.kind = 0;
+        } else if ((zr & (zr - 1)) == 0) {
+            z.kind = (uint8_t)(__builtin_ctz(zr) + 1);
+        } else {
+            z.kind = (uint8_t)(RB + 1);
+            for (int j = 0; j < (1 << RB); ++j)
+                if (__builtin_popcount(j & zr) & 1) z.jmask |= (uint16_t)(1u << j);
+        }
+        p.gens.push_back(z);
+        p.slots.push_back(g.param);
+        d.ngen++;
+    }
+    p.ops.push_back({SWEEP_DIAG, 0, 0, 0, (uint32_t)p.diags.size()});
+    p.diags.push_back(d);
+}
+
+// A run of stages whose non-diagonal gates act on one qubit, as fused sweep
+// passes.  Each pass's tile holds the 5 lowest qubits (rows of 32 contiguous
+// amplitudes) and up to L - 5 others, taken as the pending stage's one-qubit
+// gates need them.  A pass finishes the current stage's one-qubit gates
+// whose qubits fit, and while a stage completes it carries on into the next
+// one (its diagonal op, then its one-qubit gates), so a layered circuit
+// needs about (qubits - 5) / (L - 5) passes per layer.
+static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage>& run, int n, qs_dtype dt,
+                               AdjointSweep& sw) {
+    const int L = dt == QS_C64 ? kSweepTileC64 : kSweepTileC128, RB = L - 8, lowb = 5;
+    int lay_a[kSweepMaxLayouts];
+    const int nlay = sweep_layouts(dt, lay_a);
+    const uint32_t budget = sweep_tab_budget(dt);
+    struct Step {
+        int stage;
+        bool diag;
+        std::vector<int> gates;
+    };
+    struct PassPlan {
+        uint64_t Q;
+        std::vector<Step> steps;
+    };
+    std::vector<PassPlan> plans;
+    size_t si = 0;
+    std::vector<int> rem = run.empty() ? std::vector<int>() : run[0].one;
+    bool diag_done = run.empty() || run[0].diag.empty();
+    while (si < run.size()) {
+        PassPlan pp{(1ull << lowb) - 1, {}};
+        int highs = L - lowb, nops = 0, ngrad = 0, ndiag = 0, ncross = 0, ngens = 0;
+        uint32_t tabs = 0;
+        for (;;) {
+            Step st{(int)si, false, {}};
+            if (!diag_done) {
+                const DiagCost dc = fused_diag_cost(c, run[si].diag, n);
+                if (ndiag + 1 > kSweepMaxDiags || tabs + dc.tab > budget || ncross + dc.cross > kSweepMaxCross ||
+                    ngens + dc.gens > kSweepMaxGens || ngrad + dc.gens > kSweepMaxGrads ||
+                    nops + 1 + nlay > kSweepMaxOps)
+                    break;
+                ndiag++;
+                tabs += dc.tab;
+                ncross += dc.cross;
+                ngens += dc.gens;
+                ngrad += dc.gens;
+                nops += 1;
+                st.diag = true;
+                diag_done = true;
+            }
+            std::vector<int> keep;
+            for (int gi : rem) {
+                const int q = c.gates[gi].qubits[0];
+                const bool in = (pp.Q >> q) & 1;
+                const int gr = c.gates[gi].param >= 0;
+                if ((in || highs > 0) && nops + 1 + nlay <= kSweepMaxOps && ngrad + gr <= kSweepMaxGrads) {
+                    if (!in) {
+                        pp.Q |= 1ull << q;
+                        --highs;
+                    }
+                    st.gates.push_back(gi);
+                    nops++;
+                    ngrad += gr;
+                } else {
+                    keep.push_back(gi);
+                }
+            }
+            rem.swap(keep);
+            nops += nlay - 1;  // layout changes of this step
+            if (st.diag || !st.gates.empty()) pp.steps.push_back(std::move(st));
+            if (!rem.empty()) break;
+            if (++si == run.size()) break;
+            rem = run[si].one;
+            diag_done = run[si].diag.empty();
+        }
+        if (pp.steps.empty()) return fail(QS_ERR_UNSUPPORTED, "fused sweep pass: a stage does not fit one pass");
+        plans.push_back(std::move(pp));
+    }
+    for (PassPlan& pp : plans) {
+        SweepPassDesc p;
+        p.L = L;
+        p.nlay = nlay;
+        for (int l = 0; l < nlay; ++l) p.lay_a[l] = lay_a[l];
+        for (int q = 0; q < n && __builtin_popcountll(pp.Q) < L; ++q) pp.Q |= 1ull << q;
+        int local_of[kMaxQubits];
+        int npos = 0;
+        for (int q = 0; q < n; ++q)
+            if ((pp.Q >> q) & 1) {
+                local_of[q] = npos;
+                p.pos[npos++] = q;
+            }
+        auto layout_of = [&](int bit) {
+            for (int l = 0; l < nlay; ++l)
+                if (bit >= lay_a[l] && bit < lay_a[l] + RB) return l;
+            return 0;
+        };
+        int cur = 0;
+        for (const Step& st : pp.steps) {
+            if (st.diag) {
+                int rq[8];
+                for (int k = 0; k < RB; ++k) rq[k] = p.pos[lay_a[cur] + k];
+                compile_fused_diag(c, run[st.stage].diag, n, rq, RB, p);
+            }
+            // this step's gates grouped by layout: the current one first, layout 0 last
+            std::vector<int> order{cur};
+            for (int l = nlay - 1; l >= 0; --l)
+                if (l != cur) order.push_back(l);
+            for (int l : order) {
+                bool any = false;
+                for (int gi : st.gates) {
+                    const GateRec& g = c.gates[gi];
+                    const int bit = local_of[g.qubits[0]];
+                    if (layout_of(bit) != l) continue;
+                    if (!any && l != cur) {
+                        p.ops.push_back({SWEEP_LAYOUT, (uint8_t)l, 0, 0, 0});
+                        cur = l;
+                    }
+                    any = true;
+                    GateRec u;
+                    conj_transpose(g, u);
+                    SweepOpRec op{SWEEP_G1, (uint8_t)(bit - lay_a[l]), 1, 0, (uint32_t)(p.mats.size() / 8)};
+                    for (int i = 0; i < 4; ++i) op.form = op.form && u.m[2 * i + 1] == 0.0;
+                    p.mats.insert(p.mats.end(), u.m.begin(), u.m.begin() + 8);
+                    if (g.param >= 0) {
+                        const char P = g.paulis[0];
+                        op.gen = P == 'X' ? 1 : P == 'Y' ? 2 : P == 'Z' ? 3 : 0;
+                        if (op.gen) p.slots.push_back(g.param);
+                    }
+                    p.ops.push_back(op);
+                }
+            }
+        }
+        p.mat0 = sw.allm.size() / 2;
+        sw.allm.insert(sw.allm.end(), p.mats.begin(), p.mats.end());
+        p.tab0 = sw.tables.size() / 2;
+        sw.tables.insert(sw.tables.end(), p.tabs.begin(), p.tabs.end());
+        sw.ops.push_back({4, (int)sw.fused.size()});
+        sw.fused.push_back(std::move(p));
+    }
+    return QS_OK;
+}
+
 // Host phase: stages, segments and every launch's arguments.  Stages are
 // formed by the scan of Section 4.5 over the reversed gate list: from the
 // first unplaced gate, a later gate joins when it commutes with every member
@@ -1054,6 +1308,14 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
         segment.clear();
         return st;
     };
+    std::vector<FusedStage> run;  // pending stages for the fused sweep passes
+    auto flush_run = [&]() -> qs_status {
+        if (run.empty()) return QS_OK;
+        qs_status st = add_fused_run(c, run, n, dt, sw);
+        run.clear();
+        return st;
+    };
+    const int fused_L = dt == QS_C64 ? kSweepTileC64 : kSweepTileC128;
     for (size_t s0 = 0; s0 < units.size(); ++s0) {
         if (placed[s0]) continue;
         std::vector<size_t> stage{s0};
@@ -1106,6 +1368,29 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
             }
             if ((bl_any & all) == all) break;  // every qubit obstructed: nothing more can join
         }
+        // fused sweep passes take a stage whose non-diagonal members act on one qubit
+        FusedStage fs;
+        bool fused_ok = n >= fused_L;
+        for (size_t j : stage) {
+            const GateRec& g = c.gates[units[j].fwd];
+            if (units[j].diag) fs.diag.push_back(units[j].fwd);
+            else if (g.k == 1) fs.one.push_back(units[j].fwd);
+            else fused_ok = false;
+        }
+        if (fused_ok) {
+            const DiagCost dc = fused_diag_cost(c, fs.diag, n);
+            fused_ok = dc.tab <= sweep_tab_budget(dt) && dc.cross <= kSweepDiagCross && dc.gens <= kSweepDiagGens;
+        }
+        if (fused_ok) {
+            qs_status fst = flush_segment();
+            if (fst != QS_OK) return fst;
+            run.push_back(std::move(fs));
+            continue;
+        }
+        {
+            qs_status fst = flush_run();
+            if (fst != QS_OK) return fst;
+        }
         // the gradient tile pass needs 2^8 amplitudes (one per thread)
         if ((int)stage.size() < kStageMin || (!all_diag && n < 8)) {
             for (size_t j : stage) segment.push_back(units[j].fwd);
@@ -1133,6 +1418,7 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
         }
     }
     qs_status st = flush_segment();
+    if (st == QS_OK) st = flush_run();
     if (st != QS_OK) return st;
     // the stages' inverse plans are independent: fused on host threads
     sw.plans.assign(invs.size(), nullptr);
@@ -1194,6 +1480,10 @@ static qs_status run_reverse_sweep(AdjointSweep& sw, qs_state* psi, qs_state* la
             e = launch_diag_stage(psi->data, lam->data, psi->n, psi->dt, dl.nchunks, dl.cross,
                                   (const char*)sw.dtables + dl.tab0 * esz, dl.tab_elems, dl.zm, dl.slots, dl.apply,
                                   sw.partials, nb, sm);
+        } else if (op.type == 4) {
+            const SweepPassDesc& fp = sw.fused[op.index];
+            e = launch_sweep_pass(psi->data, lam->data, psi->n, psi->dt, fp, (const char*)sw.dmats + fp.mat0 * esz,
+                                  (const char*)sw.dtables + fp.tab0 * esz, sw.partials, nb, sm);
         } else {
             qs_status st = qs_plan_execute(psi, sw.plans[op.index]);
             if (st == QS_OK) st = qs_plan_execute(lam, sw.plans[op.index]);

@@ -268,6 +268,67 @@ cudaError_t launch_diag_stage(void* psi, void* lam, int n, qs_dtype dt, int nchu
                               const std::vector<int>& slots, bool apply, double* partials, int nblocks,
                               cudaStream_t st);
 
+// Fused reverse-sweep pass: consecutive stages whose non-diagonal gates act on
+// one qubit, in one read/write pass over psi and lambda.  A tile of 2^L
+// amplitudes (qubits pos[0..L-1], ascending; pos[i] = i for the low rows)
+// stays in registers: a thread holds 2^(L-8) amplitudes of each state, the
+// register index j covering the tile bits a..a+L-9 of the current layout
+// (lay_a[layout]); layout 0 (a = L - 8) is the one loaded and stored.
+constexpr int kSweepTileC64 = 12;     // L for complex64
+constexpr int kSweepTileC128 = 11;    // L for complex128
+constexpr int kSweepMaxOps = 256;
+constexpr int kSweepMaxGrads = 128;
+constexpr int kSweepMaxDiags = 4;
+constexpr int kSweepMaxCross = 64;
+constexpr int kSweepMaxGens = 96;
+constexpr int kSweepMaxLayouts = 4;
+constexpr int kSweepDiagGens = 40;    // Z generators of one diagonal op
+constexpr int kSweepDiagCross = 32;
+inline uint32_t sweep_tab_budget(qs_dtype dt) { return dt == QS_C64 ? 3072u : 1536u; }
+enum SweepOpType { SWEEP_LAYOUT = 0, SWEEP_G1 = 1, SWEEP_DIAG = 2 };
+struct SweepOpRec {
+    uint8_t type;          // SweepOpType
+    uint8_t arg;           // LAYOUT: the new layout; G1: register bit
+    uint8_t form;          // G1: 1 when U^dagger is real
+    uint8_t gen;           // G1: generator 0 none, 1 X, 2 Y, 3 Z
+    uint32_t idx;          // G1: matrix (4 elements each); DIAG: diagonal record
+};
+struct SweepDiagRec {
+    uint8_t nchunks;       // chunk c = qubits 8c .. 8c+7
+    uint8_t touched;       // bit c: a register qubit lies in chunk c (looked up per amplitude)
+    uint8_t ncross, nct;   // cross gates; the first nct hold a register qubit
+    uint16_t cross0, gen0; // first cross gate / Z generator in the pass's lists
+    uint8_t ngen, pad;
+    uint32_t tab;          // element offset of the chunk tables in the pass's table block
+};
+// Z-generator gradient of a diagonal op: sum_x (-1)^popc(x & zmask) Im(conj(l_x) p_x),
+// split as the sign from the thread's fixed bits (mthr) times a register sum:
+// kind 0 all of them, 1..RB: j bit kind-1 negated, RB+1: jmask bit j negated
+struct SweepZGen {
+    uint64_t mthr;
+    uint16_t jmask;
+    uint8_t kind;
+    uint8_t pad[5];
+};
+struct SweepPassDesc {
+    int L = 0;
+    int pos[16] = {0};
+    int nlay = 0;
+    int lay_a[kSweepMaxLayouts] = {0};
+    std::vector<SweepOpRec> ops;
+    std::vector<SweepDiagRec> diags;
+    std::vector<DiagCross> cross;      // tab: element offset in the pass's table block
+    std::vector<SweepZGen> gens;
+    std::vector<int> slots;            // gradient order -> parameter
+    std::vector<double> mats, tabs;    // FP64 interleaved complex
+    size_t mat0 = 0, tab0 = 0;         // element offsets in the sweep's device buffers
+};
+// Register-layout starts for a dtype: tile bit i is held in registers by the
+// first layout l with lay_a[l] <= i < lay_a[l] + L - 8.
+int sweep_layouts(qs_dtype dt, int* lay_a);
+cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const SweepPassDesc& p, const void* dmats,
+                              const void* dtabs, double* partials, int nblocks, cudaStream_t st);
+
 int num_sms();
 
 // Host threads a planning step may use (fusion products, stage plans): the
