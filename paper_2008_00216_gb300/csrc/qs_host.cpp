@@ -1050,11 +1050,13 @@ static DiagCost fused_diag_cost(const qs_circuit& c, const std::vector<int>& dia
     return dc;
 }
 
-// The DIAG op of `diag` for a pass whose registers hold the global qubits
-// `rq[0..RB)` (register bit k = rq[k]): chunk tables and cross gates of the
-// members' inverses appended to p.tabs / p.cross, Z generators to p.gens.
+// The DIAG op of `diag` for a pass (tile p.pos) whose registers hold the
+// global qubits `rq[0..RB)` (register bit k = rq[k], thread bit b = tile bit
+// RB + b): chunk tables and cross gates of the members' inverses appended to
+// p.tabs / p.cross, Z generators to p.gens.  Block-summed generators get
+// gradient slots numbered in `block_slots` (placed after the staged ones).
 static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag, int n, const int* rq, int RB,
-                               SweepPassDesc& p) {
+                               SweepPassDesc& p, std::vector<int>& block_slots) {
     const int nchunks = (n + 7) / 8;
     uint64_t rmask = 0;
     for (int k = 0; k < RB; ++k) rmask |= 1ull << rq[k];
@@ -1104,7 +1106,16 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
         p.tabs.push_back(z.real());
         p.tabs.push_back(z.imag());
     }
+    // generators with at most one tile bit are summed per block (S - 2X);
+    // the others per thread, staged like the one-qubit gradients
     d.gen0 = (uint16_t)p.gens.size();
+    uint64_t tmask = 0;
+    int tile_bit[kMaxQubits];
+    for (int i = 0; i < p.L; ++i) {
+        tmask |= 1ull << p.pos[i];
+        tile_bit[p.pos[i]] = i;
+    }
+    std::vector<SweepZGen> staged, block;
     for (int gi : diag) {
         const GateRec& g = c.gates[gi];
         if (g.param < 0) continue;
@@ -1112,6 +1123,20 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
         for (int i = 0; i < g.k; ++i)
             if (g.paulis[i] == 'Z') zm |= 1ull << g.qubits[i];
         SweepZGen z{};
+        const uint64_t zin = zm & tmask;
+        if (__builtin_popcountll(zin) <= 1) {
+            z.mthr = zm & ~tmask;
+            z.src = 0;
+            if (zin) {
+                const int bit = tile_bit[__builtin_ctzll(zin)];
+                z.src = (uint8_t)(bit < RB ? 1 + bit : RB + 1 + (bit - RB));  // register bit, or thread bit
+            }
+            z.local = (uint16_t)block_slots.size();
+            block_slots.push_back(g.param);
+            block.push_back(z);
+            continue;
+        }
+        z.src = kZStaged;
         z.mthr = zm & ~rmask;
         uint32_t zr = 0;  // register bits of the mask
         for (int k = 0; k < RB; ++k)
@@ -1125,12 +1150,70 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
             for (int j = 0; j < (1 << RB); ++j)
                 if (__builtin_popcount(j & zr) & 1) z.jmask |= (uint16_t)(1u << j);
         }
-        p.gens.push_back(z);
+        staged.push_back(z);
         p.slots.push_back(g.param);
-        d.ngen++;
     }
+    d.nstaged = (uint8_t)staged.size();
+    d.ngen = (uint8_t)(staged.size() + block.size());
+    p.gens.insert(p.gens.end(), staged.begin(), staged.end());
+    p.gens.insert(p.gens.end(), block.begin(), block.end());
     p.ops.push_back({SWEEP_DIAG, 0, 0, 0, (uint32_t)p.diags.size()});
     p.diags.push_back(d);
+}
+
+// Form and coefficients (4 complex) of a one-qubit op of the fused pass for
+// U^dagger = `u` and generator `gen` (0 none, 1 X, 2 Y, 3 Z).  A phase
+// common to psi and lambda cancels in every Im <lambda|P|psi>, and the states
+// are work states, so U^dagger / sqrt(det) = M = [[a, -conj(b)], [b, conj(a)]]
+// (sign chosen so that Re a >= 0) can stand for it.  M is then three shears,
+// p0 += z p1, p1 += y p0, p0 += x p1 with y = b, x = (a - 1) / b,
+// z = (conj(a) - 1) / b, each done in place; real M (rotations, and
+// reflections after negating p1) keeps real coefficients.  Shears are used
+// when |x|, |z| <= 2 (always for rotations with Re a >= 0, whose |x| =
+// tan(angle / 4) <= 1); otherwise the four entries are applied directly.
+static int g1_coefficients(const GateRec& u, int gen, double* c8) {
+    using C = std::complex<double>;
+    const C m00(u.m[0], u.m[1]), m01(u.m[2], u.m[3]), m10(u.m[4], u.m[5]), m11(u.m[6], u.m[7]);
+    for (int i = 0; i < 8; ++i) c8[i] = u.m[i];
+    bool real = true;
+    for (int i = 0; i < 4; ++i) real = real && u.m[2 * i + 1] == 0.0;
+    auto put = [&](C z, C y, C x) {
+        const C v[4] = {z, y, x, C(0.0)};
+        for (int i = 0; i < 4; ++i) {
+            c8[2 * i] = v[i].real();
+            c8[2 * i + 1] = v[i].imag();
+        }
+    };
+    if (real) {
+        const double det = (m00 * m11 - m01 * m10).real();
+        const bool refl = det < 0;
+        // rotation part: U^dagger = R diag(1, -1) for a reflection
+        double a = m00.real(), b = m10.real();
+        const double r01 = refl ? -m01.real() : m01.real(), r11 = refl ? -m11.real() : m11.real();
+        if (std::abs(std::abs(det) - 1.0) > 1e-12 || std::abs(r01 + b) > 1e-12 || std::abs(r11 - a) > 1e-12)
+            return G1_DIRECT;  // not orthogonal (cannot happen for a unitary)
+        if (a < 0) {  // -R: the common sign
+            a = -a;
+            b = -b;
+        }
+        const double x = b == 0.0 ? 0.0 : (a - 1.0) / b;  // b = 0: R = I
+        if (std::abs(x) > 2.0) return G1_DIRECT;
+        if (gen != 0 && (refl || gen != 2)) return G1_DIRECT;
+        put(C(x), C(b), C(x));
+        return refl ? G1_RSHEAR_NEG : gen == 2 ? G1_RSHEAR_Y : G1_RSHEAR;
+    }
+    if (gen != 0 && gen != 1) return G1_DIRECT;
+    C ph = std::sqrt(m00 * m11 - m01 * m10);
+    C a = m00 / ph, b = m10 / ph;
+    if (a.real() < 0) {
+        a = -a;
+        b = -b;
+    }
+    if (std::abs(b) < 1e-9) return G1_DIRECT;
+    const C x = (a - 1.0) / b, z = (std::conj(a) - 1.0) / b;
+    if (std::abs(x) > 2.0 || std::abs(z) > 2.0) return G1_DIRECT;
+    put(z, b, x);
+    return gen == 1 ? G1_CSHEAR_X : G1_CSHEAR;
 }
 
 // A run of stages whose non-diagonal gates act on one qubit, as fused sweep
@@ -1198,7 +1281,7 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
                 }
             }
             rem.swap(keep);
-            nops += nlay - 1;  // layout changes of this step
+            nops += nlay;  // layout changes of this step
             if (st.diag || !st.gates.empty()) pp.steps.push_back(std::move(st));
             if (!rem.empty()) break;
             if (++si == run.size()) break;
@@ -1226,17 +1309,28 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
                 if (bit >= lay_a[l] && bit < lay_a[l] + RB) return l;
             return 0;
         };
+        // diagonal ops run in the last ("low") layout, whose registers hold
+        // qubits 0 .. RB-1; each step's gates are grouped by layout, the
+        // current one first and the one the next step starts in last
+        const int low = nlay - 1;
         int cur = 0;
-        for (const Step& st : pp.steps) {
+        std::vector<int> block_slots;
+        for (size_t k = 0; k < pp.steps.size(); ++k) {
+            const Step& st = pp.steps[k];
             if (st.diag) {
+                if (cur != low) {
+                    p.ops.push_back({SWEEP_LAYOUT, (uint8_t)low, 0, 0, 0});
+                    cur = low;
+                }
                 int rq[8];
-                for (int k = 0; k < RB; ++k) rq[k] = p.pos[lay_a[cur] + k];
-                compile_fused_diag(c, run[st.stage].diag, n, rq, RB, p);
+                for (int b = 0; b < RB; ++b) rq[b] = p.pos[lay_a[low] + b];
+                compile_fused_diag(c, run[st.stage].diag, n, rq, RB, p, block_slots);
             }
-            // this step's gates grouped by layout: the current one first, layout 0 last
+            const int last = k + 1 < pp.steps.size() && pp.steps[k + 1].diag ? low : 0;
             std::vector<int> order{cur};
-            for (int l = nlay - 1; l >= 0; --l)
-                if (l != cur) order.push_back(l);
+            for (int l = 0; l < nlay; ++l)
+                if (l != cur && l != last) order.push_back(l);
+            if (last != cur) order.push_back(last);
             for (int l : order) {
                 bool any = false;
                 for (int gi : st.gates) {
@@ -1250,18 +1344,22 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
                     any = true;
                     GateRec u;
                     conj_transpose(g, u);
-                    SweepOpRec op{SWEEP_G1, (uint8_t)(bit - lay_a[l]), 1, 0, (uint32_t)(p.mats.size() / 8)};
-                    for (int i = 0; i < 4; ++i) op.form = op.form && u.m[2 * i + 1] == 0.0;
-                    p.mats.insert(p.mats.end(), u.m.begin(), u.m.begin() + 8);
+                    SweepOpRec op{SWEEP_G1, (uint8_t)(bit - lay_a[l]), 0, 0, (uint32_t)(p.mats.size() / 8)};
                     if (g.param >= 0) {
                         const char P = g.paulis[0];
                         op.gen = P == 'X' ? 1 : P == 'Y' ? 2 : P == 'Z' ? 3 : 0;
                         if (op.gen) p.slots.push_back(g.param);
                     }
+                    double c8[8];
+                    op.form = (uint8_t)g1_coefficients(u, op.gen, c8);
+                    p.mats.insert(p.mats.end(), c8, c8 + 8);
                     p.ops.push_back(op);
                 }
             }
         }
+        for (const SweepDiagRec& d : p.diags)  // block generators' slots follow the staged ones
+            for (int g = d.nstaged; g < d.ngen; ++g) p.gens[d.gen0 + g].local += (uint16_t)p.slots.size();
+        p.slots.insert(p.slots.end(), block_slots.begin(), block_slots.end());
         p.mat0 = sw.allm.size() / 2;
         sw.allm.insert(sw.allm.end(), p.mats.begin(), p.mats.end());
         p.tab0 = sw.tables.size() / 2;

@@ -286,29 +286,51 @@ constexpr int kSweepDiagGens = 40;    // Z generators of one diagonal op
 constexpr int kSweepDiagCross = 32;
 inline uint32_t sweep_tab_budget(qs_dtype dt) { return dt == QS_C64 ? 3072u : 1536u; }
 enum SweepOpType { SWEEP_LAYOUT = 0, SWEEP_G1 = 1, SWEEP_DIAG = 2 };
+// One-qubit op forms.  U^dagger, times a phase common to psi and lambda (it
+// cancels in Im <lambda|P|psi>), is M = [[a, -conj(b)], [b, conj(a)]] with
+// Re a >= 0, applied as three in-place shears p0 += z p1, p1 += y p0,
+// p0 += x p1 (y = b, x = (a - 1) / b, z = (conj(a) - 1) / b), or directly.
+enum SweepG1Form {
+    G1_DIRECT = 0,         // the four entries, any generator
+    G1_RSHEAR = 1,         // real shears, no gradient
+    G1_RSHEAR_Y = 2,       // real shears, generator Y
+    G1_RSHEAR_NEG = 3,     // p1 negated, then real shears (a reflection), no gradient
+    G1_CSHEAR = 4,         // complex shears, no gradient
+    G1_CSHEAR_X = 5,       // complex shears, generator X
+    G1_FORMS = 6
+};
 struct SweepOpRec {
     uint8_t type;          // SweepOpType
     uint8_t arg;           // LAYOUT: the new layout; G1: register bit
-    uint8_t form;          // G1: 1 when U^dagger is real
+    uint8_t form;          // G1: SweepG1Form
     uint8_t gen;           // G1: generator 0 none, 1 X, 2 Y, 3 Z
-    uint32_t idx;          // G1: matrix (4 elements each); DIAG: diagonal record
+    uint32_t idx;          // G1: coefficients (4 elements: the entries, or z, y, x); DIAG: diagonal record
 };
 struct SweepDiagRec {
     uint8_t nchunks;       // chunk c = qubits 8c .. 8c+7
     uint8_t touched;       // bit c: a register qubit lies in chunk c (looked up per amplitude)
     uint8_t ncross, nct;   // cross gates; the first nct hold a register qubit
     uint16_t cross0, gen0; // first cross gate / Z generator in the pass's lists
-    uint8_t ngen, pad;
+    uint8_t ngen, nstaged; // Z generators; the first nstaged are summed per thread
     uint32_t tab;          // element offset of the chunk tables in the pass's table block
 };
-// Z-generator gradient of a diagonal op: sum_x (-1)^popc(x & zmask) Im(conj(l_x) p_x),
-// split as the sign from the thread's fixed bits (mthr) times a register sum:
-// kind 0 all of them, 1..RB: j bit kind-1 negated, RB+1: jmask bit j negated
+// Z-generator gradient of a diagonal op (run in the low layout: register bit
+// k = qubit k), sum_x (-1)^popc(x & zmask) Im(conj(l_x) p_x), with t_x the
+// summand and S its sum over a tile.
+//   block (src != kZStaged): at most one tile bit in the mask; the gradient
+//     is (-1)^popc(tile base & mthr) (S - 2 X), X = 0 (src 0), the sum over
+//     register bit src-1 set (src 1..RB), or over thread bit src-RB-1 set
+//   staged: the sign from the thread's fixed bits (mthr) times a register
+//     sum: kind 0 all, 1..RB register bit kind-1 negated, RB+1 jmask bit j
+//     negated; one value per thread, summed with the G1 gradients
+constexpr uint8_t kZStaged = 255;
 struct SweepZGen {
     uint64_t mthr;
     uint16_t jmask;
+    uint16_t local;        // block: its gradient slot in the pass
     uint8_t kind;
-    uint8_t pad[5];
+    uint8_t src;
+    uint8_t pad[2];
 };
 struct SweepPassDesc {
     int L = 0;

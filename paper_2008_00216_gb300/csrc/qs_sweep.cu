@@ -34,21 +34,24 @@ namespace {
 constexpr int kThreads = 256;
 
 // L: tile qubits; 2^SW elements per 128-byte row; ROWS: staged gradients
-// (one row of kThreads values each, in the state's precision)
+// (one row of kThreads values each, in the state's precision); LAY: the
+// register layouts (start of the register range), 0 natural, the last one
+// "low" (registers hold qubits 0 .. L-9, where diagonal ops run).
 template <typename R> struct SweepShape;
 template <> struct SweepShape<float> {
-    static constexpr int L = kSweepTileC64, SW = 4, ROWS = 16;
+    static constexpr int L = kSweepTileC64, SW = 4, ROWS = 16, NLAY = 3;
+    __host__ __device__ static constexpr int lay(int l) { return l == 0 ? 8 : l == 1 ? 4 : 0; }
 };
 template <> struct SweepShape<double> {
-    static constexpr int L = kSweepTileC128, SW = 3, ROWS = 8;
+    static constexpr int L = kSweepTileC128, SW = 3, ROWS = 8, NLAY = 4;
+    __host__ __device__ static constexpr int lay(int l) { return l == 0 ? 8 : l == 1 ? 5 : l == 2 ? 2 : 0; }
 };
 
 struct SweepArgs {
-    int n, nops, ngrad, nlay, nb;
+    int n, nops, ngrad, nb;
     uint32_t tab_elems;
     uint64_t ntiles;
     int pos[16];
-    int lay_a[kSweepMaxLayouts];
     SweepOpRec ops[kSweepMaxOps];
     SweepDiagRec diag[kSweepMaxDiags];
     DiagCross cross[kSweepMaxCross];
@@ -65,91 +68,165 @@ __device__ __forceinline__ uint32_t layout_base(uint32_t t, int a) {
 }
 
 // Shared-memory slot of tile element e: the low SW bits are XORed with the
-// next SW bits, so every layout's warp access is free of bank conflicts.
+// next SW bits, so every layout's warp access is free of bank conflicts.  The
+// map is linear over XOR, and a thread's elements are e0 | (j << a) with
+// disjoint bits, so slot = swz(e0) ^ swz(j << a): one XOR with a constant.
 template <int SW>
-__device__ __forceinline__ uint32_t swz(uint32_t e) {
+__host__ __device__ constexpr uint32_t swz(uint32_t e) {
     return e ^ ((e >> SW) & ((1u << SW) - 1u));
 }
 
-template <typename T, int L, int SW>
-__device__ __forceinline__ void transpose(T* buf, T (&ps)[1 << (L - 8)], T (&ls)[1 << (L - 8)], int a_from, int a_to) {
+template <typename T, int L, int SW, int AF, int AT>
+__device__ __forceinline__ void transpose_ct(T* buf, T (&ps)[1 << (L - 8)], T (&ls)[1 << (L - 8)]) {
     constexpr int RB = L - 8, PER = 1 << RB;
-    const uint32_t e0 = layout_base<RB>(threadIdx.x, a_from), e1 = layout_base<RB>(threadIdx.x, a_to);
+    const uint32_t s0 = swz<SW>(layout_base<RB>(threadIdx.x, AF)), s1 = swz<SW>(layout_base<RB>(threadIdx.x, AT));
     __syncthreads();  // earlier readers of buf are done
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        const uint32_t s = swz<SW>(e0 + ((uint32_t)j << a_from));
+        const uint32_t s = s0 ^ swz<SW>((uint32_t)j << AF);
         buf[s] = ps[j];
         buf[(1u << L) + s] = ls[j];
     }
     __syncthreads();
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
-        const uint32_t s = swz<SW>(e1 + ((uint32_t)j << a_to));
+        const uint32_t s = s1 ^ swz<SW>((uint32_t)j << AT);
         ps[j] = buf[s];
         ls[j] = buf[(1u << L) + s];
     }
 }
 
-// One-qubit gate on register bit r: gradient Im <l|P|p> of the thread's
-// pairs (GEN 1 X, 2 Y, 3 Z), then U^dagger (m, row-major) on both states;
-// FORM 1: m is real.
-template <typename T, int RB, int r, int FORM, int GEN>
-__device__ __forceinline__ auto g1(T (&ps)[1 << RB], T (&ls)[1 << RB], const T* __restrict__ m) {
+template <typename R, int F>
+__device__ __forceinline__ void transpose_from(typename C2<R>::T* buf, typename C2<R>::T (&ps)[1 << (SweepShape<R>::L - 8)],
+                                               typename C2<R>::T (&ls)[1 << (SweepShape<R>::L - 8)], int to) {
+    using S = SweepShape<R>;
+    using T = typename C2<R>::T;
+    switch (to) {
+        case 0: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(0)>(buf, ps, ls); break;
+        case 1: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(1)>(buf, ps, ls); break;
+        case 2: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(2)>(buf, ps, ls); break;
+        default: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(S::NLAY - 1)>(buf, ps, ls); break;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void transpose_any(typename C2<R>::T* buf, typename C2<R>::T (&ps)[1 << (SweepShape<R>::L - 8)],
+                                              typename C2<R>::T (&ls)[1 << (SweepShape<R>::L - 8)], int from, int to) {
+    switch (from) {
+        case 0: transpose_from<R, 0>(buf, ps, ls, to); break;
+        case 1: transpose_from<R, 1>(buf, ps, ls, to); break;
+        case 2: transpose_from<R, 2>(buf, ps, ls, to); break;
+        default: transpose_from<R, SweepShape<R>::NLAY - 1>(buf, ps, ls, to); break;
+    }
+}
+
+// Packed FP32 pairs (Blackwell f32x2): two lanes of a float2 per instruction.
+__device__ __forceinline__ uint64_t f2u(float2 v) {
+    return (uint64_t)__float_as_uint(v.x) | ((uint64_t)__float_as_uint(v.y) << 32);
+}
+__device__ __forceinline__ float2 u2f(uint64_t u) {
+    return make_float2(__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32)));
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
+    return u2f(d);
+}
+
+// sum over the pair of componentwise products: acc += x * y (both lanes)
+__device__ __forceinline__ float2 dot2(float2 acc, float2 x, float2 y) { return fma2(x, y, acc); }
+__device__ __forceinline__ double2 dot2(double2 acc, double2 x, double2 y) {
+    return make_double2(fma(x.x, y.x, acc.x), fma(x.y, y.y, acc.y));
+}
+
+// complex p += t q, in place
+template <typename T, typename C>
+__device__ __forceinline__ void shear(T& p, C t, T q) {
+    p.x = fma(t.x, q.x, p.x);
+    p.x = fma(-t.y, q.y, p.x);
+    p.y = fma(t.x, q.y, p.y);
+    p.y = fma(t.y, q.x, p.y);
+}
+// real t (both lanes (t, t)): p += t q, in place
+__device__ __forceinline__ void rshear(float2& p, float2 t, float2 q) { p = fma2(t, q, p); }
+__device__ __forceinline__ void rshear(double2& p, double2 t, double2 q) {
+    p.x = fma(t.x, q.x, p.x);
+    p.y = fma(t.x, q.y, p.y);
+}
+
+// One-qubit op on register bit r (form V, SweepG1Form): the gradient
+// Im <l|P|p> over the thread's pairs, then U^dagger on both states.
+template <typename T, int RB, int r, int V>
+__device__ __forceinline__ auto g1(T (&ps)[1 << RB], T (&ls)[1 << RB], const T* __restrict__ m, int gen) {
     using R = decltype(T{}.x);
-    const T u00 = m[0], u01 = m[1], u10 = m[2], u11 = m[3];
+    const T m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+    T t0, t1, t2;  // real shears: (z, z), (y, y), (x, x)
+    t0.x = t0.y = m0.x;
+    t1.x = t1.y = m1.x;
+    t2.x = t2.y = m2.x;
     R acc = 0;
+    T ya, yb;  // generator Y: sum l1 * p0 and sum l0 * p1, componentwise
+    ya.x = ya.y = yb.x = yb.y = 0;
 #pragma unroll
     for (int p = 0; p < (1 << (RB - 1)); ++p) {
         const int j0 = ((p >> r) << (r + 1)) | (p & ((1 << r) - 1));
         const int j1 = j0 | (1 << r);
-        const T p0 = ps[j0], p1 = ps[j1], l0 = ls[j0], l1 = ls[j1];
-        if (GEN == 1) acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
-        if (GEN == 2) acc += (l1.x * p0.x + l1.y * p0.y) - (l0.x * p1.x + l0.y * p1.y);
-        if (GEN == 3) acc += (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
-        T q0, q1, k0, k1;
-        if (FORM == 1) {
-            q0.x = u00.x * p0.x + u01.x * p1.x;
-            q0.y = u00.x * p0.y + u01.x * p1.y;
-            q1.x = u10.x * p0.x + u11.x * p1.x;
-            q1.y = u10.x * p0.y + u11.x * p1.y;
-            k0.x = u00.x * l0.x + u01.x * l1.x;
-            k0.y = u00.x * l0.y + u01.x * l1.y;
-            k1.x = u10.x * l0.x + u11.x * l1.x;
-            k1.y = u10.x * l0.y + u11.x * l1.y;
-        } else {
-            q0 = cmul(u00, p0);
-            cmac(q0, u01, p1);
-            q1 = cmul(u10, p0);
-            cmac(q1, u11, p1);
-            k0 = cmul(u00, l0);
-            cmac(k0, u01, l1);
-            k1 = cmul(u10, l0);
-            cmac(k1, u11, l1);
+        T& p0 = ps[j0];
+        T& p1 = ps[j1];
+        T& l0 = ls[j0];
+        T& l1 = ls[j1];
+        if (V == G1_RSHEAR_Y || (V == G1_DIRECT && gen == 2)) {  // Re(conj(l1) p0) - Re(conj(l0) p1)
+            ya = dot2(ya, l1, p0);
+            yb = dot2(yb, l0, p1);
         }
-        ps[j0] = q0;
-        ps[j1] = q1;
-        ls[j0] = k0;
-        ls[j1] = k1;
+        if (V == G1_CSHEAR_X || (V == G1_DIRECT && gen == 1))
+            acc += (l0.x * p1.y - l0.y * p1.x) + (l1.x * p0.y - l1.y * p0.x);
+        if (V == G1_DIRECT && gen == 3) acc += (l0.x * p0.y - l0.y * p0.x) - (l1.x * p1.y - l1.y * p1.x);
+        if (V == G1_RSHEAR || V == G1_RSHEAR_Y || V == G1_RSHEAR_NEG) {
+            if (V == G1_RSHEAR_NEG) {
+                p1.x = -p1.x;
+                p1.y = -p1.y;
+                l1.x = -l1.x;
+                l1.y = -l1.y;
+            }
+            rshear(p0, t0, p1);
+            rshear(p1, t1, p0);
+            rshear(p0, t2, p1);
+            rshear(l0, t0, l1);
+            rshear(l1, t1, l0);
+            rshear(l0, t2, l1);
+        } else if (V == G1_CSHEAR || V == G1_CSHEAR_X) {
+            shear(p0, m0, p1);
+            shear(p1, m1, p0);
+            shear(p0, m2, p1);
+            shear(l0, m0, l1);
+            shear(l1, m1, l0);
+            shear(l0, m2, l1);
+        } else {
+            T q0 = cmul(m0, p0), q1 = cmul(m2, p0), k0 = cmul(m0, l0), k1 = cmul(m2, l0);
+            cmac(q0, m1, p1);
+            cmac(q1, m3, p1);
+            cmac(k0, m1, l1);
+            cmac(k1, m3, l1);
+            p0 = q0;
+            p1 = q1;
+            l0 = k0;
+            l1 = k1;
+        }
     }
+    if (V == G1_RSHEAR_Y || (V == G1_DIRECT && gen == 2)) acc = (ya.x + ya.y) - (yb.x + yb.y);
     return acc;
 }
 
 template <typename T, int RB, int r>
 __device__ __forceinline__ auto g1_form(T (&ps)[1 << RB], T (&ls)[1 << RB], const T* m, int form, int gen) {
-    if (form) {
-        switch (gen) {
-            case 1: return g1<T, RB, r, 1, 1>(ps, ls, m);
-            case 2: return g1<T, RB, r, 1, 2>(ps, ls, m);
-            case 3: return g1<T, RB, r, 1, 3>(ps, ls, m);
-            default: return g1<T, RB, r, 1, 0>(ps, ls, m);
-        }
-    }
-    switch (gen) {
-        case 1: return g1<T, RB, r, 0, 1>(ps, ls, m);
-        case 2: return g1<T, RB, r, 0, 2>(ps, ls, m);
-        case 3: return g1<T, RB, r, 0, 3>(ps, ls, m);
-        default: return g1<T, RB, r, 0, 0>(ps, ls, m);
+    switch (form) {
+        case G1_RSHEAR: return g1<T, RB, r, G1_RSHEAR>(ps, ls, m, gen);
+        case G1_RSHEAR_Y: return g1<T, RB, r, G1_RSHEAR_Y>(ps, ls, m, gen);
+        case G1_RSHEAR_NEG: return g1<T, RB, r, G1_RSHEAR_NEG>(ps, ls, m, gen);
+        case G1_CSHEAR: return g1<T, RB, r, G1_CSHEAR>(ps, ls, m, gen);
+        case G1_CSHEAR_X: return g1<T, RB, r, G1_CSHEAR_X>(ps, ls, m, gen);
+        default: return g1<T, RB, r, G1_DIRECT>(ps, ls, m, gen);
     }
 }
 
@@ -172,30 +249,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                                                             const __grid_constant__ SweepArgs a,
                                                             double* __restrict__ partials) {
     using T = typename C2<R>::T;
-    constexpr int L = SweepShape<R>::L, SW = SweepShape<R>::SW, RB = L - 8, PER = 1 << RB;
-    constexpr int kRows = SweepShape<R>::ROWS, TPR = kThreads / kRows;  // threads per staged row
+    using S = SweepShape<R>;
+    constexpr int L = S::L, RB = L - 8, PER = 1 << RB, LOW = S::NLAY - 1;
+    constexpr int kRows = S::ROWS, TPR = kThreads / kRows;  // threads per staged row
+    static_assert(S::lay(0) == L - RB && S::lay(LOW) == 0, "layouts");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* buf = reinterpret_cast<T*>(smem_raw);                                    // 2 x 2^L (psi, lambda)
     T* tab = buf + 2 * (1u << L);                                               // a.tab_elems
     R* gs = reinterpret_cast<R*>(tab + a.tab_elems);                            // kRows x kThreads
     double* red = reinterpret_cast<double*>(gs + kRows * kThreads);             // a.ngrad
-    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // a.nlay x PER
+    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // PER: byte offset of j
+    R* dred = reinterpret_cast<R*>(xo + PER);                                   // 8 warps x (6 + RB)
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = tabs[i];
     for (int i = tid; i < a.ngrad; i += kThreads) red[i] = 0.0;
-    for (int i = tid; i < a.nlay * PER; i += kThreads) {  // global offset of register index j per layout
-        const int l = i / PER, j = i % PER;
+    if (tid < PER) {  // natural layout: register bit k is tile bit L - RB + k
         uint64_t o = 0;
         for (int k = 0; k < RB; ++k)
-            if ((j >> k) & 1) o |= 1ull << a.pos[a.lay_a[l] + k];
-        xo[i] = o;
+            if ((tid >> k) & 1) o |= 1ull << a.pos[L - RB + k];
+        xo[tid] = o * sizeof(T);
     }
     auto global_of = [&](uint32_t e) {  // tile index -> global offset within the tile
         uint64_t x = 0;
         for (int i = 0; i < L; ++i) x |= (uint64_t)((e >> i) & 1u) << a.pos[i];
         return x;
     };
-    const uint64_t xg0 = global_of(layout_base<RB>(tid, a.lay_a[0]));
+    const uint64_t xg0 = global_of(layout_base<RB>(tid, S::lay(0)));  // the thread's bits, natural layout
     __syncthreads();
 
     int gcount = 0;  // gradients produced so far in this tile
@@ -221,12 +300,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
         T ps[PER], ls[PER];
         {
-            const uint64_t x0 = base | xg0;
+            const char* pp = reinterpret_cast<const char*>(psi) + (base | xg0) * sizeof(T);
+            const char* pl = reinterpret_cast<const char*>(lam) + (base | xg0) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                const uint64_t x = x0 | xo[j];
-                ps[j] = psi[x];
-                ls[j] = lam[x];
+                const uint64_t o = xo[j];
+                ps[j] = *reinterpret_cast<const T*>(pp + o);
+                ls[j] = *reinterpret_cast<const T*>(pl + o);
             }
         }
         int lay = 0;
@@ -234,22 +314,19 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         for (int o = 0; o < a.nops; ++o) {
             const SweepOpRec op = a.ops[o];
             if (op.type == SWEEP_LAYOUT) {
-                transpose<T, L, SW>(buf, ps, ls, a.lay_a[lay], a.lay_a[op.arg]);
+                transpose_any<R>(buf, ps, ls, lay, op.arg);
                 lay = op.arg;
             } else if (op.type == SWEEP_G1) {
                 const R v = g1_any<T, RB>(ps, ls, mats + 4 * op.idx, op.arg, op.form, op.gen);
                 if (op.gen) stage(v);
-            } else {
+            } else {  // DIAG, in the low layout: register index j = bits 0 .. RB-1 of the index
                 const SweepDiagRec d = a.diag[op.idx];
                 const T* dtab = tab + d.tab;
-                const uint64_t xt = base | global_of(layout_base<RB>(tid, a.lay_a[lay]));
-                const uint64_t* xl = xo + lay * PER;
-                // factors that do not depend on the register index
-                T pc;
+                const uint64_t xt = base | global_of(layout_base<RB>(tid, 0));
+                T pc;  // chunks 1.. and the cross gates without a register qubit
                 pc.x = 1;
                 pc.y = 0;
-                for (int c = 0; c < d.nchunks; ++c)
-                    if (!((d.touched >> c) & 1)) pc = cmul(pc, dtab[256 * c + ((xt >> (8 * c)) & 255)]);
+                for (int c = 1; c < d.nchunks; ++c) pc = cmul(pc, dtab[256 * c + ((xt >> (8 * c)) & 255)]);
                 pc = cross_phase(a.cross + d.cross0 + d.nct, d.ncross - d.nct, tab, xt, pc);
                 R tsum = 0, u[RB];
 #pragma unroll
@@ -262,7 +339,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                     for (int i = 0; i < RB; ++i)
                         if ((j >> i) & 1) u[i] += t;
                 }
-                for (int g = 0; g < d.ngen; ++g) {
+                for (int g = 0; g < d.nstaged; ++g) {
                     const SweepZGen z = a.gens[d.gen0 + g];
                     R v;
                     if (z.kind == 0) {
@@ -283,26 +360,50 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                     }
                     stage((__popcll(xt & z.mthr) & 1) ? -v : v);
                 }
+                if (d.ngen > d.nstaged) {  // block generators: warp sums of S, W_b (lane bits), U_k
+                    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+                    for (int i = 0; i < 6 + RB; ++i) {
+                        R w = i == 0 ? tsum : i < 6 ? (((lane >> (i - 1)) & 1) ? tsum : (R)0) : u[i < 6 ? 0 : i - 6];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+                        if (lane == 0) dred[warp * (6 + RB) + i] = w;
+                    }
+                    __syncthreads();
+                    for (int g = d.nstaged + tid; g < d.ngen; g += kThreads) {
+                        const SweepZGen z = a.gens[d.gen0 + g];
+                        R S = 0, X = 0;
+                        for (int q = 0; q < kThreads / 32; ++q) {  // fixed order
+                            const R* wq = dred + q * (6 + RB);
+                            S += wq[0];
+                            if (z.src >= 1 && z.src <= RB) X += wq[5 + z.src];
+                            else if (z.src > RB && z.src <= RB + 5) X += wq[z.src - RB];
+                            else if (z.src > RB + 5 && ((q >> (z.src - RB - 6)) & 1)) X += wq[0];
+                        }
+                        const R v = S - 2 * X;
+                        red[z.local] += (double)((__popcll(base & z.mthr) & 1) ? -v : v);
+                    }
+                    __syncthreads();  // dred is reused by the next diagonal op
+                }
+                const T* t0 = dtab + (xt & 255);  // chunk 0: the thread's bits, plus j
 #pragma unroll
                 for (int j = 0; j < PER; ++j) {
-                    const uint64_t x = xt | xl[j];
-                    T ph = pc;
-                    for (int c = 0; c < d.nchunks; ++c)
-                        if ((d.touched >> c) & 1) ph = cmul(ph, dtab[256 * c + ((x >> (8 * c)) & 255)]);
-                    ph = cross_phase(a.cross + d.cross0, d.nct, tab, x, ph);
+                    T ph = cmul(pc, t0[j]);
+                    if (d.nct) ph = cross_phase(a.cross + d.cross0, d.nct, tab, xt | (uint64_t)j, ph);
                     ps[j] = cmul(ph, ps[j]);
                     ls[j] = cmul(ph, ls[j]);
                 }
             }
         }
-        if (lay != 0) transpose<T, L, SW>(buf, ps, ls, a.lay_a[lay], a.lay_a[0]);
+        if (lay != 0) transpose_any<R>(buf, ps, ls, lay, 0);
         {
-            const uint64_t x0 = base | xg0;
+            char* pp = reinterpret_cast<char*>(psi) + (base | xg0) * sizeof(T);
+            char* pl = reinterpret_cast<char*>(lam) + (base | xg0) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                const uint64_t x = x0 | xo[j];
-                psi[x] = ps[j];
-                lam[x] = ls[j];
+                const uint64_t o = xo[j];
+                *reinterpret_cast<T*>(pp + o) = ps[j];
+                *reinterpret_cast<T*>(pl + o) = ls[j];
             }
         }
         if (gcount % kRows) flush(gcount % kRows);
@@ -320,7 +421,8 @@ size_t sweep_smem(const SweepArgs& a) {
     constexpr int L = SweepShape<R>::L;
     const size_t esz = sizeof(typename C2<R>::T);
     return esz * (2 * ((size_t)1 << L) + a.tab_elems) + sizeof(R) * SweepShape<R>::ROWS * kThreads +
-           sizeof(double) * a.ngrad + sizeof(uint64_t) * a.nlay * ((size_t)1 << (L - 8));
+           sizeof(double) * a.ngrad + sizeof(uint64_t) * ((size_t)1 << (L - 8)) +
+           sizeof(R) * (kThreads / 32) * (6 + (L - 8));
 }
 
 }  // namespace
@@ -355,12 +457,10 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
     a.tab_elems = (uint32_t)(p.tabs.size() / 2);
     a.ntiles = 1ull << (n - L);
     int lay[kSweepMaxLayouts];
-    a.nlay = sweep_layouts(dt, lay);
-    if (p.nlay != a.nlay) return cudaErrorInvalidValue;
-    for (int l = 0; l < a.nlay; ++l) {
+    const int nlay = sweep_layouts(dt, lay);
+    if (p.nlay != nlay) return cudaErrorInvalidValue;
+    for (int l = 0; l < nlay; ++l)
         if (p.lay_a[l] != lay[l]) return cudaErrorInvalidValue;
-        a.lay_a[l] = lay[l];
-    }
     // every index the kernel follows is checked here
     for (int i = 0; i < L; ++i) {
         if (p.pos[i] < 0 || p.pos[i] >= n || (i > 0 && p.pos[i] <= p.pos[i - 1])) return cudaErrorInvalidValue;
@@ -369,23 +469,28 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
     for (int i = 0; i < 5 && i < L; ++i)  // rows of contiguous amplitudes for the coalesced load
         if (p.pos[i] != i) return cudaErrorInvalidValue;
     const uint32_t nmat = (uint32_t)(p.mats.size() / 8);
-    int grads = 0;
+    int grads = 0, cur = 0;  // cur: the layout the kernel is in at this op
     for (int o = 0; o < a.nops; ++o) {
         const SweepOpRec& op = p.ops[o];
         if (op.type == SWEEP_LAYOUT) {
-            if (op.arg >= a.nlay) return cudaErrorInvalidValue;
+            if (op.arg >= nlay) return cudaErrorInvalidValue;
+            cur = op.arg;
         } else if (op.type == SWEEP_G1) {
-            if (op.arg >= RB || op.idx >= nmat || op.gen > 3 || op.form > 1) return cudaErrorInvalidValue;
+            if (op.arg >= RB || op.idx >= nmat || op.gen > 3 || op.form >= G1_FORMS) return cudaErrorInvalidValue;
             grads += op.gen != 0;
         } else if (op.type == SWEEP_DIAG) {
-            if (op.idx >= p.diags.size()) return cudaErrorInvalidValue;
+            if (op.idx >= p.diags.size() || cur != nlay - 1) return cudaErrorInvalidValue;  // the low layout
             const SweepDiagRec& d = p.diags[op.idx];
             if (d.nchunks < 1 || d.nchunks > 8 || 8 * (d.nchunks - 1) >= n || d.nct > d.ncross ||
                 (size_t)d.cross0 + d.ncross > p.cross.size() || (size_t)d.gen0 + d.ngen > p.gens.size() ||
                 (size_t)d.tab + 256 * (size_t)d.nchunks > a.tab_elems)
                 return cudaErrorInvalidValue;
-            for (int g = 0; g < d.ngen; ++g)
-                if (p.gens[d.gen0 + g].kind > RB + 1) return cudaErrorInvalidValue;
+            if (d.nstaged > d.ngen) return cudaErrorInvalidValue;
+            for (int g = 0; g < d.ngen; ++g) {
+                const SweepZGen& z = p.gens[d.gen0 + g];
+                if (g < d.nstaged ? z.kind > RB + 1 : (z.src > RB + 8 || z.local >= p.slots.size()))
+                    return cudaErrorInvalidValue;
+            }
             grads += d.ngen;
         } else {
             return cudaErrorInvalidValue;
