@@ -48,7 +48,7 @@ template <> struct SweepShape<double> {
 };
 
 struct SweepArgs {
-    int n, nops, ngrad, nb;
+    int n, nops, ngrad, nb, nmat;
     uint32_t tab_elems;
     uint64_t ntiles;
     int pos[16];
@@ -257,11 +257,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     T* buf = reinterpret_cast<T*>(smem_raw);                                    // 2 x 2^L (psi, lambda)
     T* tab = buf + 2 * (1u << L);                                               // a.tab_elems
     R* gs = reinterpret_cast<R*>(tab + a.tab_elems);                            // kRows x kThreads
-    double* red = reinterpret_cast<double*>(gs + kRows * kThreads);             // a.ngrad
-    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // PER: byte offset of j
+    double* red = reinterpret_cast<double*>(gs + kRows * kThreads);             // a.ngrad (even count: 16-byte alignment below)
+    uint64_t* xo = reinterpret_cast<uint64_t*>(red + ((a.ngrad + 1) & ~1));    // PER: byte offset of j
     R* dred = reinterpret_cast<R*>(xo + PER);                                   // 8 warps x (6 + RB)
+    T* cm = reinterpret_cast<T*>(dred + (kThreads / 32) * (6 + RB));            // 4 x a.nmat coefficients
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = tabs[i];
+    for (int i = tid; i < 4 * a.nmat; i += kThreads) cm[i] = mats[i];
     for (int i = tid; i < a.ngrad; i += kThreads) red[i] = 0.0;
     if (tid < PER) {  // natural layout: register bit k is tile bit L - RB + k
         uint64_t o = 0;
@@ -277,8 +279,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     const uint64_t xg0 = global_of(layout_base<RB>(tid, S::lay(0)));  // the thread's bits, natural layout
     __syncthreads();
 
-    int gcount = 0;  // gradients produced so far in this tile
-    auto flush = [&](int rows) {  // block-uniform: add the staged rows to red
+    int gdone = 0, srow = 0;  // gradients of this tile already added to red; rows staged since
+    auto flush = [&]() {  // block-uniform: add the staged rows to red
         __syncthreads();
         const int row = tid / TPR, part = tid % TPR;
         R v = 0;
@@ -286,13 +288,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         for (int k = 0; k < kThreads / TPR; ++k) v += gs[row * kThreads + part + TPR * k];
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
-        if (part == 0 && row < rows) red[gcount - rows + row] += (double)v;
+        if (part == 0 && row < srow) red[gdone + row] += (double)v;
+        gdone += srow;
+        srow = 0;
         __syncthreads();
     };
     auto stage = [&](R v) {
-        gs[(gcount % kRows) * kThreads + tid] = v;
-        ++gcount;
-        if (gcount % kRows == 0) flush(kRows);
+        gs[srow * kThreads + tid] = v;
+        if (++srow == kRows) flush();
     };
 
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -310,14 +313,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
             }
         }
         int lay = 0;
-        gcount = 0;
+        gdone = 0;
         for (int o = 0; o < a.nops; ++o) {
             const SweepOpRec op = a.ops[o];
             if (op.type == SWEEP_LAYOUT) {
                 transpose_any<R>(buf, ps, ls, lay, op.arg);
                 lay = op.arg;
             } else if (op.type == SWEEP_G1) {
-                const R v = g1_any<T, RB>(ps, ls, mats + 4 * op.idx, op.arg, op.form, op.gen);
+                const R v = g1_any<T, RB>(ps, ls, cm + 4 * op.idx, op.arg, op.form, op.gen);
                 if (op.gen) stage(v);
             } else {  // DIAG, in the low layout: register index j = bits 0 .. RB-1 of the index
                 const SweepDiagRec d = a.diag[op.idx];
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 *reinterpret_cast<T*>(pl + o) = ls[j];
             }
         }
-        if (gcount % kRows) flush(gcount % kRows);
+        if (srow) flush();
     }
     __syncthreads();
     for (int s = tid; s < a.ngrad; s += kThreads) {
@@ -421,8 +424,8 @@ size_t sweep_smem(const SweepArgs& a) {
     constexpr int L = SweepShape<R>::L;
     const size_t esz = sizeof(typename C2<R>::T);
     return esz * (2 * ((size_t)1 << L) + a.tab_elems) + sizeof(R) * SweepShape<R>::ROWS * kThreads +
-           sizeof(double) * a.ngrad + sizeof(uint64_t) * ((size_t)1 << (L - 8)) +
-           sizeof(R) * (kThreads / 32) * (6 + (L - 8));
+           sizeof(double) * ((a.ngrad + 1) & ~1) + sizeof(uint64_t) * ((size_t)1 << (L - 8)) +
+           sizeof(R) * (kThreads / 32) * (6 + (L - 8)) + sizeof(typename C2<R>::T) * 4 * a.nmat;
 }
 
 }  // namespace
@@ -469,6 +472,8 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
     for (int i = 0; i < 5 && i < L; ++i)  // rows of contiguous amplitudes for the coalesced load
         if (p.pos[i] != i) return cudaErrorInvalidValue;
     const uint32_t nmat = (uint32_t)(p.mats.size() / 8);
+    if (nmat > kSweepMaxOps) return cudaErrorInvalidValue;
+    a.nmat = (int)nmat;
     int grads = 0, cur = 0;  // cur: the layout the kernel is in at this op
     for (int o = 0; o < a.nops; ++o) {
         const SweepOpRec& op = p.ops[o];
