@@ -694,19 +694,8 @@ qs_status qs_expectation(const qs_state* s, const qs_pauli_sum* h, double* out) 
     if (st != QS_OK) return st;
     if (!h || !out) return fail(QS_ERR_ARG, "null argument");
     if (h->n != s->n) return fail(QS_ERR_ARG, "Hamiltonian and state qubit counts differ");
-    // group terms by flip mask: one pass over the state per group
-    std::map<uint64_t, std::vector<qs_pauli_sum::Term>> groups;
-    for (const auto& t : h->terms) groups[t.xmask].push_back(t);
     double* res = result_area(s);
-    QS_CUDA(cudaMemsetAsync(res, 0, sizeof(double), s->stream));
-    for (auto& kv : groups) {
-        const auto& v = kv.second;
-        for (size_t at = 0; at < v.size(); at += 32) {
-            const int cnt = (int)std::min<size_t>(32, v.size() - at);
-            QS_CUDA(launch_pauli_group(s->data, s->n, s->dt, kv.first, v.data() + at, cnt, s->scratch,
-                                       res, s->stream));
-        }
-    }
+    QS_CUDA(launch_expectation(s->data, s->n, s->dt, *h, s->scratch, res, s->stream));
     QS_CUDA(cudaMemcpyAsync(s->host_pinned, res, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
     QS_CUDA(cudaStreamSynchronize(s->stream));
     *out = s->host_pinned[0];
@@ -1217,15 +1206,17 @@ static int g1_coefficients(const GateRec& u, int gen, double* c8) {
 }
 
 // A run of stages whose non-diagonal gates act on one qubit, as fused sweep
-// passes.  Each pass's tile holds the 5 lowest qubits (rows of 32 contiguous
-// amplitudes) and up to L - 5 others, taken as the pending stage's one-qubit
-// gates need them.  A pass finishes the current stage's one-qubit gates
+// passes.  Each pass's tile holds the lowest qubits (rows of 128 contiguous
+// bytes) and up to L - 4 (complex64) or L - 3 (complex128) others, taken as
+// the pending stage's one-qubit gates need them.  A pass finishes the current stage's one-qubit gates
 // whose qubits fit, and while a stage completes it carries on into the next
 // one (its diagonal op, then its one-qubit gates), so a layered circuit
-// needs about (qubits - 5) / (L - 5) passes per layer.
+// needs about (qubits - 4) / 8 passes per layer.
 static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage>& run, int n, qs_dtype dt,
                                AdjointSweep& sw) {
-    const int L = dt == QS_C64 ? kSweepTileC64 : kSweepTileC128, RB = L - 8, lowb = 5;
+    // low rows of 128 bytes (16 complex64 / 8 complex128 amplitudes): full
+    // sectors, and the diagonal ops' register qubits 0 .. RB-1 among them
+    const int L = dt == QS_C64 ? kSweepTileC64 : kSweepTileC128, RB = L - 8, lowb = dt == QS_C64 ? 4 : 3;
     int lay_a[kSweepMaxLayouts];
     const int nlay = sweep_layouts(dt, lay_a);
     const uint32_t budget = sweep_tab_budget(dt);

@@ -217,12 +217,15 @@ cudaError_t launch_init_uniform(void* psi, int n, qs_dtype dt, cudaStream_t st);
 int reduce_blocks();
 cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* scratch, double* result,
                         cudaStream_t st);
-// Expectation of the terms sharing one flip mask; adds into result[0].
-cudaError_t launch_pauli_group(const void* psi, int n, qs_dtype dt, uint64_t xmask,
-                               const qs_pauli_sum::Term* terms, int nterms, double* scratch,
-                               double* result, cudaStream_t st);
+// out = H psi (distinct memory) and result[0] = <psi|H|psi>, in tile passes
+// that each read psi once (qs_pauli.cu); scratch holds reduce_blocks()
+// partial sums.
 cudaError_t launch_apply_pauli_sum(const void* psi, void* out, int n, qs_dtype dt,
                                    const qs_pauli_sum& h, cudaStream_t st);
+cudaError_t launch_expectation(const void* psi, int n, qs_dtype dt, const qs_pauli_sum& h, double* scratch,
+                               double* result, cudaStream_t st);
+// result[0] = (set) or += the fixed-order sum of `cols` partials.
+cudaError_t launch_accumulate(const double* partials, int cols, double* result, bool set, cudaStream_t st);
 // <a|b> partial sums (complex, FP64) into result[0..1].
 cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, double* scratch,
                          double* result, cudaStream_t st);

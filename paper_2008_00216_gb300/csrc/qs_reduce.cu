@@ -83,173 +83,20 @@ cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* scratch, do
     return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------ <psi|P|psi>
+// ------------------------------------------------------------------ partial sums
 
-struct PauliGroupP {
-    uint64_t xmask;
-    int f0;        // lowest flipped bit (pairs are visited once)
-    int nterms;
-    double coeff[32];
-    uint64_t zmask[32];
-    int ny[32];
-    uint64_t units;
-};
-
-// For the pair (y, y^F) with bit f0 of y clear and z = conj(psi_y) psi_{y^F},
-// the two contributions of a term with sign s(x) = (-1)^popc(x & Z) sum to
-// i^ny [s(y^F) z + s(y) conj(z)], whose real part is taken.
-template <typename R>
-__global__ void __launch_bounds__(256) k_pauli_group(const typename C2<R>::T* __restrict__ psi,
-                                                     const __grid_constant__ PauliGroupP p,
-                                                     double* __restrict__ partial) {
-    using T = typename C2<R>::T;
-    __shared__ double sh[32];
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    double acc = 0.0;
-    if (p.xmask == 0) {
-        for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < p.units; y += stride) {
-            const T a = psi[y];
-            const double pr = (double)(a.x * a.x + a.y * a.y);
-            double w = 0.0;
-            for (int t = 0; t < p.nterms; ++t) w += (__popcll(y & p.zmask[t]) & 1) ? -p.coeff[t] : p.coeff[t];
-            acc = fma(w, pr, acc);
-        }
-    } else {
-        for (uint64_t u = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; u < p.units; u += stride) {
-            const uint64_t y = insert_zero(u, p.f0), y2 = y ^ p.xmask;
-            const T a = psi[y], b = psi[y2];
-            const double zr = (double)(a.x * b.x + a.y * b.y);   // conj(a) b
-            const double zi = (double)(a.x * b.y - a.y * b.x);
-            for (int t = 0; t < p.nterms; ++t) {
-                const double s1 = (__popcll(y & p.zmask[t]) & 1) ? -1.0 : 1.0;
-                const double s2 = (__popcll(y2 & p.zmask[t]) & 1) ? -1.0 : 1.0;
-                double re;
-                switch (p.ny[t] & 3) {
-                    case 0: re = (s1 + s2) * zr; break;
-                    case 1: re = -(s2 - s1) * zi; break;
-                    case 2: re = -(s1 + s2) * zr; break;
-                    default: re = (s2 - s1) * zi; break;
-                }
-                acc = fma(p.coeff[t], re, acc);
-            }
-        }
-    }
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
-}
-
-__global__ void k_accumulate(const double* __restrict__ partials, int cols, double* __restrict__ result) {
+// result[0] (+)= the sum of cols partials, in a fixed order
+__global__ void k_accumulate(const double* __restrict__ partials, int cols, double* __restrict__ result, int set) {
     __shared__ double sh[32];
     double s = 0.0;
     for (int c = threadIdx.x; c < cols; c += blockDim.x) s += partials[c];
     s = block_sum(s, sh);
-    if (threadIdx.x == 0) result[0] += s;
+    if (threadIdx.x == 0) result[0] = set ? s : result[0] + s;
 }
 
-cudaError_t launch_pauli_group(const void* psi, int n, qs_dtype dt, uint64_t xmask, const qs_pauli_sum::Term* terms,
-                               int nterms, double* scratch, double* result, cudaStream_t st) {
-    if (nterms < 1 || nterms > 32) return cudaErrorInvalidValue;
-    PauliGroupP p{};
-    p.xmask = xmask;
-    p.f0 = xmask ? __builtin_ctzll(xmask) : -1;
-    p.nterms = nterms;
-    for (int t = 0; t < nterms; ++t) {
-        p.coeff[t] = terms[t].coeff;
-        p.zmask[t] = terms[t].zmask;
-        p.ny[t] = terms[t].ny;
-    }
-    p.units = xmask ? (1ull << (n - 1)) : (1ull << n);
-    const int nb = reduce_blocks();
-    if (dt == QS_C64) k_pauli_group<float><<<nb, 256, 0, st>>>((const float2*)psi, p, scratch);
-    else k_pauli_group<double><<<nb, 256, 0, st>>>((const double2*)psi, p, scratch);
-    k_accumulate<<<1, 256, 0, st>>>(scratch, nb, result);
+cudaError_t launch_accumulate(const double* partials, int cols, double* result, bool set, cudaStream_t st) {
+    k_accumulate<<<1, 256, 0, st>>>(partials, cols, result, set ? 1 : 0);
     return cudaGetLastError();
-}
-
-// ------------------------------------------------------------------ out = H psi
-
-struct HP {
-    int ngroups;
-    int accumulate;
-    uint64_t xmask[48];
-    int first[49];        // terms of group g: [first[g], first[g+1])
-    double coeff[96];
-    uint64_t zmask[96];
-    int ny[96];
-    uint64_t size;
-};
-
-template <typename R>
-__global__ void __launch_bounds__(256) k_apply_pauli(const typename C2<R>::T* __restrict__ psi,
-                                                     typename C2<R>::T* __restrict__ out,
-                                                     const __grid_constant__ HP p) {
-    using T = typename C2<R>::T;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t y = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; y < p.size; y += stride) {
-        // in the state's precision: the result is stored in it, and FP64 is
-        // a slow pipe on this GPU for complex64 states
-        R accr = 0, acci = 0;
-        if (p.accumulate) {
-            const T o = out[y];
-            accr = o.x;
-            acci = o.y;
-        }
-        for (int g = 0; g < p.ngroups; ++g) {
-            const uint64_t x = y ^ p.xmask[g];
-            // w = sum_t c_t i^ny (-1)^popc(x & Z_t)
-            R wr = 0, wi = 0;
-            for (int t = p.first[g]; t < p.first[g + 1]; ++t) {
-                const R c = (__popcll(x & p.zmask[t]) & 1) ? -(R)p.coeff[t] : (R)p.coeff[t];
-                const int q = p.ny[t] & 3;
-                wr += (q == 0) ? c : (q == 2) ? -c : (R)0;
-                wi += (q == 1) ? c : (q == 3) ? -c : (R)0;
-            }
-            const T a = psi[x];
-            accr += wr * a.x - wi * a.y;
-            acci += wr * a.y + wi * a.x;
-        }
-        T o;
-        o.x = accr;
-        o.y = acci;
-        out[y] = o;
-    }
-}
-
-cudaError_t launch_apply_pauli_sum(const void* psi, void* out, int n, qs_dtype dt, const qs_pauli_sum& h,
-                                   cudaStream_t st) {
-    std::map<uint64_t, std::vector<qs_pauli_sum::Term>> groups;
-    for (const auto& t : h.terms) groups[t.xmask].push_back(t);
-    std::vector<std::pair<uint64_t, std::vector<qs_pauli_sum::Term>>> gl(groups.begin(), groups.end());
-    const uint64_t size = 1ull << n;
-    int gi = 0;
-    bool first_launch = true;
-    while (gi < (int)gl.size() || first_launch) {
-        HP p{};
-        p.size = size;
-        p.accumulate = first_launch ? 0 : 1;
-        int nt = 0;
-        while (gi < (int)gl.size() && p.ngroups < 48 && nt + (int)gl[gi].second.size() <= 96) {
-            p.xmask[p.ngroups] = gl[gi].first;
-            p.first[p.ngroups] = nt;
-            for (const auto& t : gl[gi].second) {
-                p.coeff[nt] = t.coeff;
-                p.zmask[nt] = t.zmask;
-                p.ny[nt] = t.ny;
-                ++nt;
-            }
-            ++p.ngroups;
-            ++gi;
-        }
-        p.first[p.ngroups] = nt;
-        if (p.ngroups == 0 && gi < (int)gl.size()) return cudaErrorInvalidValue;  // one group > 96 terms
-        const int nb = reduce_blocks() * 2;
-        if (dt == QS_C64) k_apply_pauli<float><<<nb, 256, 0, st>>>((const float2*)psi, (float2*)out, p);
-        else k_apply_pauli<double><<<nb, 256, 0, st>>>((const double2*)psi, (double2*)out, p);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        first_launch = false;
-    }
-    return cudaSuccess;
 }
 
 // ------------------------------------------------------------------ <a|b>

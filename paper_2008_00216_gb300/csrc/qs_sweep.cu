@@ -469,7 +469,7 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
         if (p.pos[i] < 0 || p.pos[i] >= n || (i > 0 && p.pos[i] <= p.pos[i - 1])) return cudaErrorInvalidValue;
         a.pos[i] = p.pos[i];
     }
-    for (int i = 0; i < 5 && i < L; ++i)  // rows of contiguous amplitudes for the coalesced load
+    for (int i = 0; i < RB; ++i)  // diagonal ops: the low layout's registers hold qubits 0 .. RB-1
         if (p.pos[i] != i) return cudaErrorInvalidValue;
     const uint32_t nmat = (uint32_t)(p.mats.size() / 8);
     if (nmat > kSweepMaxOps) return cudaErrorInvalidValue;
