@@ -121,6 +121,20 @@ __device__ __forceinline__ T cross_phase(const X* cg, int count, const T* tab, u
     return ph;
 }
 
+// Componentwise a * b + c; for FP32 pairs one packed f32x2 instruction
+// (Blackwell), which halves the issue slots of real-by-complex products.
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+    const uint64_t ua = (uint64_t)__float_as_uint(a.x) | ((uint64_t)__float_as_uint(a.y) << 32);
+    const uint64_t ub = (uint64_t)__float_as_uint(b.x) | ((uint64_t)__float_as_uint(b.y) << 32);
+    const uint64_t uc = (uint64_t)__float_as_uint(c.x) | ((uint64_t)__float_as_uint(c.y) << 32);
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
+    return make_float2(__uint_as_float((uint32_t)d), __uint_as_float((uint32_t)(d >> 32)));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
 // acc += m * x (complex), as four fused multiply-adds
 template <typename T>
 __device__ __forceinline__ void cmac(T& acc, T m, T x) {

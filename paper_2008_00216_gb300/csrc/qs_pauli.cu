@@ -41,9 +41,11 @@ struct PauliTileArgs {
     int first[kPTGroups + 1];  // terms of group g
     int loop0[kPTGroups];      // first term summed per element (the diagonal group's tabled terms come first)
     double wc[kPTGroups][2];   // groups whose terms have no Z: the constant weight
+    float wcf[kPTGroups][2];   // the same in FP32 (complex64 states)
     uint8_t wconst[kPTGroups];
     uint8_t gread[kPTGroups];  // flip mask wider than a tile: the partner is read from global memory
     double coeff[kPTTerms];
+    float coeff_f[kPTTerms];
     uint64_t zmask[kPTTerms];
     uint8_t ny[kPTTerms];
     int8_t chunk[kPTTerms];    // diagonal group: chunk of a term in one chunk (its sum is tabled), else -1
@@ -88,7 +90,10 @@ __global__ void __launch_bounds__(256) k_pauli_tile(const typename C2<R>::T* __r
             const uint64_t x = (uint64_t)(i & 255) << (8 * c);
             R w = 0;
             for (int t = a.first[a.dg]; t < a.first[a.dg + 1]; ++t)
-                if (a.chunk[t] == c) w += (__popcll(x & a.zmask[t]) & 1) ? -(R)a.coeff[t] : (R)a.coeff[t];
+                if (a.chunk[t] == c) {
+                    const R ct = sizeof(R) == 4 ? (R)a.coeff_f[t] : (R)a.coeff[t];
+                    w += (__popcll(x & a.zmask[t]) & 1) ? -ct : ct;
+                }
             wtab[i] = w;
         }
     }
@@ -103,23 +108,35 @@ __global__ void __launch_bounds__(256) k_pauli_tile(const typename C2<R>::T* __r
         __syncthreads();
         auto elem = [&](int k) { return threadIdx.x + 256u * (uint32_t)k; };
         auto gidx = [&](uint32_t e) { return base + rowoff[e >> b] + (e & mask); };
+        auto live = [&](int k) { return PER > 1 || elem(k) < ne; };  // a tile below 256 elements
+        auto coef = [&](int t) { return sizeof(R) == 4 ? (R)a.coeff_f[t] : (R)a.coeff[t]; };
         T acc[PER];
 #pragma unroll
         for (int k = 0; k < PER; ++k) {
             acc[k].x = acc[k].y = 0;
-            if (a.mode == 1 && elem(k) < ne) acc[k] = out[gidx(elem(k))];
+            if (a.mode == 1 && live(k)) acc[k] = out[gidx(elem(k))];
         }
         for (int g = 0; g < a.ngroups; ++g) {
             const uint32_t fl = a.flip[g];
             const uint64_t gf = a.gflip[g];
             if (a.wconst[g] && !a.gread[g]) {  // weight c i^ny: the common case (X, Y strings without Z)
-                const R wr = (R)a.wc[g][0], wi = (R)a.wc[g][1];
+                const R wr = sizeof(R) == 4 ? (R)a.wcf[g][0] : (R)a.wc[g][0];
+                const R wi = sizeof(R) == 4 ? (R)a.wcf[g][1] : (R)a.wc[g][1];
+                const uint32_t tf = threadIdx.x ^ (fl & 255u), fh = fl >> 8;
+                if (wi == 0) {
+                    T w2;
+                    w2.x = w2.y = wr;
 #pragma unroll
-                for (int k = 0; k < PER; ++k) {
-                    if (elem(k) >= ne) continue;
-                    const T v = tile[elem(k) ^ fl];
-                    acc[k].x += wr * v.x - wi * v.y;
-                    acc[k].y += wr * v.y + wi * v.x;
+                    for (int k = 0; k < PER; ++k)
+                        if (live(k)) acc[k] = cfma(w2, tile[tf + (((uint32_t)k ^ fh) << 8)], acc[k]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PER; ++k) {
+                        if (!live(k)) continue;
+                        const T v = tile[tf + (((uint32_t)k ^ fh) << 8)];
+                        acc[k].x += wr * v.x - wi * v.y;
+                        acc[k].y += wr * v.y + wi * v.x;
+                    }
                 }
                 continue;
             }
@@ -127,13 +144,13 @@ __global__ void __launch_bounds__(256) k_pauli_tile(const typename C2<R>::T* __r
             const bool diag = g == a.dg, rd = a.gread[g];
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                if (elem(k) >= ne) continue;
+                if (!live(k)) continue;
                 const uint32_t e = elem(k);
                 const uint64_t x = gidx(e) ^ gf;
                 R wr = 0, wi = 0;
                 if (diag)
                     for (int c = 0; c < a.nchunks; ++c) wr += wtab[256 * c + ((x >> (8 * c)) & 255)];
-                for (int t = t0; t < t1; ++t) term_weight(wr, wi, (R)a.coeff[t], a.ny[t], x, a.zmask[t]);
+                for (int t = t0; t < t1; ++t) term_weight(wr, wi, coef(t), a.ny[t], x, a.zmask[t]);
                 const T v = rd ? psi[x] : tile[e ^ fl];
                 acc[k].x += wr * v.x - wi * v.y;
                 acc[k].y += wr * v.y + wi * v.x;
@@ -143,7 +160,7 @@ __global__ void __launch_bounds__(256) k_pauli_tile(const typename C2<R>::T* __r
             R es = 0;
 #pragma unroll
             for (int k = 0; k < PER; ++k) {
-                if (elem(k) >= ne) continue;
+                if (!live(k)) continue;
                 const T p = tile[elem(k)];
                 es += p.x * acc[k].x + p.y * acc[k].y;  // Re(conj(psi_y) (H psi)_y)
             }
@@ -152,7 +169,7 @@ __global__ void __launch_bounds__(256) k_pauli_tile(const typename C2<R>::T* __r
         } else {
 #pragma unroll
             for (int k = 0; k < PER; ++k)
-                if (elem(k) < ne) out[gidx(elem(k))] = acc[k];
+                if (live(k)) out[gidx(elem(k))] = acc[k];
         }
         __syncthreads();  // the tile is overwritten next
     }
@@ -241,6 +258,7 @@ std::vector<PauliTileArgs> plan_pauli(const qs_pauli_sum& h, int n, qs_dtype dt,
             a.loop0[k] = nt;
             for (const auto& t : ts) {
                 a.coeff[nt] = t.coeff;
+                a.coeff_f[nt] = (float)t.coeff;
                 a.zmask[nt] = t.zmask;
                 a.ny[nt] = (uint8_t)(t.ny & 3);
                 a.chunk[nt] = -1;
@@ -261,6 +279,8 @@ std::vector<PauliTileArgs> plan_pauli(const qs_pauli_sum& h, int n, qs_dtype dt,
             a.wconst[k] = noz ? 1 : 0;
             a.wc[k][0] = wr;
             a.wc[k][1] = wi;
+            a.wcf[k][0] = (float)wr;
+            a.wcf[k][1] = (float)wi;
         }
         a.first[mine.size()] = nt;
         passes.push_back(a);
@@ -280,7 +300,10 @@ cudaError_t launch_pass(const void* psi, void* out, const PauliTileArgs& a, doub
     using T = typename C2<R>::T;
     const size_t smem = pauli_smem<R>(a);
     switch (a.L) {
-        case 12: k_pauli_tile<R, 16><<<grid, 256, smem, st>>>((const T*)psi, (T*)out, a, partial); break;
+        case 12:  // complex64 only (complex128 tiles hold 2^11 amplitudes)
+            if constexpr (sizeof(R) == 4) k_pauli_tile<R, 16><<<grid, 256, smem, st>>>((const T*)psi, (T*)out, a, partial);
+            else return cudaErrorInvalidValue;
+            break;
         case 11: k_pauli_tile<R, 8><<<grid, 256, smem, st>>>((const T*)psi, (T*)out, a, partial); break;
         case 10: k_pauli_tile<R, 4><<<grid, 256, smem, st>>>((const T*)psi, (T*)out, a, partial); break;
         case 9: k_pauli_tile<R, 2><<<grid, 256, smem, st>>>((const T*)psi, (T*)out, a, partial); break;

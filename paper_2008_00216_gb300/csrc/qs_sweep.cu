@@ -120,24 +120,9 @@ __device__ __forceinline__ void transpose_any(typename C2<R>::T* buf, typename C
     }
 }
 
-// Packed FP32 pairs (Blackwell f32x2): two lanes of a float2 per instruction.
-__device__ __forceinline__ uint64_t f2u(float2 v) {
-    return (uint64_t)__float_as_uint(v.x) | ((uint64_t)__float_as_uint(v.y) << 32);
-}
-__device__ __forceinline__ float2 u2f(uint64_t u) {
-    return make_float2(__uint_as_float((uint32_t)u), __uint_as_float((uint32_t)(u >> 32)));
-}
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2u(a)), "l"(f2u(b)), "l"(f2u(c)));
-    return u2f(d);
-}
-
 // sum over the pair of componentwise products: acc += x * y (both lanes)
-__device__ __forceinline__ float2 dot2(float2 acc, float2 x, float2 y) { return fma2(x, y, acc); }
-__device__ __forceinline__ double2 dot2(double2 acc, double2 x, double2 y) {
-    return make_double2(fma(x.x, y.x, acc.x), fma(x.y, y.y, acc.y));
-}
+template <typename T>
+__device__ __forceinline__ T dot2(T acc, T x, T y) { return cfma(x, y, acc); }
 
 // complex p += t q, in place
 template <typename T, typename C>
@@ -148,11 +133,8 @@ __device__ __forceinline__ void shear(T& p, C t, T q) {
     p.y = fma(t.y, q.x, p.y);
 }
 // real t (both lanes (t, t)): p += t q, in place
-__device__ __forceinline__ void rshear(float2& p, float2 t, float2 q) { p = fma2(t, q, p); }
-__device__ __forceinline__ void rshear(double2& p, double2 t, double2 q) {
-    p.x = fma(t.x, q.x, p.x);
-    p.y = fma(t.x, q.y, p.y);
-}
+template <typename T>
+__device__ __forceinline__ void rshear(T& p, T t, T q) { p = cfma(t, q, p); }
 
 // One-qubit op on register bit r (form V, SweepG1Form): the gradient
 // Im <l|P|p> over the thread's pairs, then U^dagger on both states.
