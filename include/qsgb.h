@@ -91,7 +91,12 @@ typedef struct qs_pauli_sum qs_pauli_sum;
  *                 diagonal gates with diagonal gates, in clusters of any
  *                 width (one wide diagonal pass each, pass kind 6), the
  *                 other gates with each other up to k_max.  0 (default) =
- *                 fuse any gates while their qubits fit k_max.  */
+ *                 fuse any gates while their qubits fit k_max.
+ *   fusion_effort : search behind each fused block (Section 4.5's scan,
+ *                 best-first).  1 (default): each candidate qubit set is
+ *                 scored by its completion with a one-level lookahead at
+ *                 the first step (fewer blocks; tens of ms for ~1000 gates);
+ *                 0: greedy completion only (a few ms).  */
 typedef struct qs_options {
     int k_max;
     int tile_qubits;
@@ -100,7 +105,8 @@ typedef struct qs_options {
     int fuse;
     int inject_wait_timeout;
     int diag_clusters;
-    int reserved[6];
+    int fusion_effort;
+    int reserved[5];
 } qs_options;
 
 const char* qs_version(void);

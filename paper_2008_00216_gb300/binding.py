@@ -34,7 +34,7 @@ class QsError(RuntimeError):
 class Options(ct.Structure):
     _fields_ = [("k_max", ct.c_int), ("tile_qubits", ct.c_int), ("use_tile", ct.c_int),
                 ("precision", ct.c_int), ("fuse", ct.c_int), ("inject_wait_timeout", ct.c_int),
-                ("diag_clusters", ct.c_int), ("reserved", ct.c_int * 6)]
+                ("diag_clusters", ct.c_int), ("fusion_effort", ct.c_int), ("reserved", ct.c_int * 5)]
 
 
 _P = ct.c_void_p
@@ -148,11 +148,13 @@ def _stream_ptr(stream=None) -> int:
 
 
 def options(k_max: int = 4, tile_qubits: int = 0, use_tile: bool = True, precision="fp32",
-            fuse: bool = True, inject_wait_timeout: bool = False, diag_clusters: bool = False) -> Options:
+            fuse: bool = True, inject_wait_timeout: bool = False, diag_clusters: bool = False,
+            fusion_effort: int = 1) -> Options:
     o = Options()
     _call("qs_options_default", ct.byref(o))
     o.inject_wait_timeout = 1 if inject_wait_timeout else 0
     o.diag_clusters = 1 if diag_clusters else 0
+    o.fusion_effort = int(fusion_effort)
     o.k_max = int(k_max)
     o.tile_qubits = int(tile_qubits)
     o.use_tile = 1 if use_tile else 0

@@ -173,6 +173,7 @@ qs_status qs_options_default(qs_options* opt) {
     opt->use_tile = 1;
     opt->precision = QS_PREC_FP32;
     opt->fuse = 1;
+    opt->fusion_effort = 1;
     return QS_OK;
 }
 
@@ -450,6 +451,7 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     if (opt_in) opt = *opt_in;
     else qs_options_default(&opt);
     if (opt.k_max < 1 || opt.k_max > kMaxK) return fail(QS_ERR_ARG, "k_max outside 1..6");
+    if (opt.fusion_effort < 0 || opt.fusion_effort > 1) return fail(QS_ERR_ARG, "fusion_effort must be 0 or 1");
     const int maxL = dt == QS_C64 ? 13 : 12;
     if (opt.tile_qubits != 0 && (opt.tile_qubits < 6 || opt.tile_qubits > maxL))
         return fail(QS_ERR_ARG, "tile_qubits outside 6..%d", maxL);
@@ -464,8 +466,8 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     std::vector<GateRec> blocks;
     qs_status st;
     if (opt.fuse) {
-        st = opt.diag_clusters ? fuse_by_kind(c->n, c->gates, opt.k_max, blocks)
-                               : fuse_gates(c->n, c->gates, opt.k_max, blocks);
+        st = opt.diag_clusters ? fuse_by_kind(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort)
+                               : fuse_gates(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort);
         if (st != QS_OK) return st;
     } else {
         blocks = c->gates;
@@ -1617,6 +1619,8 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
         fast.k_max = 6;
         fast.precision = QS_PREC_3XTF32;
     }
+    // the forward cannot start before its plan: the quicker block search
+    fast.fusion_effort = 0;
     // forward and lambda are enqueued first; the reverse sweep is planned on
     // the host while the GPU runs them (plan memory is stream-ordered, so
     // nothing here synchronises)

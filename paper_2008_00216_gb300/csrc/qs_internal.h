@@ -168,12 +168,13 @@ namespace qsgb {
 // qs_plan_create with the matrices uploaded and (at destruction) freed in the
 // order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
 qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
-qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
+// effort 1: each candidate block scored with a one-level lookahead; 0: greedy
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1);
 // Clustering by kind (Sections 4.2, 4.5): diagonal gates join diagonal
 // clusters of any width (one wide pass each), the others fuse among
 // themselves up to k_max qubits.  Clusters on <= 6 qubits come back as
 // ordinary diagonal blocks.
-qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out);
+qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1);
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 int auto_tile_qubits(int n, qs_dtype dt);
