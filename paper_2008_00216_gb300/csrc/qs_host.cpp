@@ -466,8 +466,9 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     std::vector<GateRec> blocks;
     qs_status st;
     if (opt.fuse) {
-        st = opt.diag_clusters ? fuse_by_kind(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort)
-                               : fuse_gates(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort);
+        FuseCache* fc = c->fuse_cache.get();
+        st = opt.diag_clusters ? fuse_by_kind(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort, fc)
+                               : fuse_gates(c->n, c->gates, opt.k_max, blocks, opt.fusion_effort, fc);
         if (st != QS_OK) return st;
     } else {
         blocks = c->gates;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -49,10 +51,23 @@ void pauli_matrix(int k, const char* paulis, double* m);
 
 }  // namespace qsgb
 
+namespace qsgb {
+// The grouping found by the block search for one circuit, reused while the
+// gates' qubits and structural kinds are unchanged (new angles only change
+// the FP64 block products).
+struct FuseCache {
+    std::mutex mu;
+    uint64_t key = 0;
+    bool valid = false;
+    std::vector<std::vector<int>> groups;
+};
+}  // namespace qsgb
+
 struct qs_circuit {
     int n = 0;
     int num_params = 0;
     std::vector<qsgb::GateRec> gates;
+    std::shared_ptr<qsgb::FuseCache> fuse_cache = std::make_shared<qsgb::FuseCache>();
 };
 
 struct qs_pauli_sum {
@@ -169,12 +184,14 @@ namespace qsgb {
 // order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
 qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
 // effort 1: each candidate block scored with a one-level lookahead; 0: greedy
-qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1);
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1,
+                     FuseCache* cache = nullptr);
 // Clustering by kind (Sections 4.2, 4.5): diagonal gates join diagonal
 // clusters of any width (one wide pass each), the others fuse among
 // themselves up to k_max qubits.  Clusters on <= 6 qubits come back as
 // ordinary diagonal blocks.
-qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1);
+qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1,
+                       FuseCache* cache = nullptr);
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 int auto_tile_qubits(int n, qs_dtype dt);

@@ -360,13 +360,31 @@ static std::vector<int> best_first_group(const GateView& v, std::vector<char>& p
 // by_kind = false: any gates fuse while their qubits fit k_max.  by_kind =
 // true: diagonal gates only with diagonal gates, in clusters of any width
 // (bounded by what one wide pass holds), the others only with each other.
-static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, std::vector<GateRec>& out,
-                           int effort) {
-    if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
-    out.clear();
-    // 1. the scans (sequential: each one sees what the previous placed)
-    std::vector<char> placed(in.size(), 0);
+// What the grouping depends on: the gates' qubits and kinds, and the search.
+static uint64_t grouping_key(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, int effort) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) {
+        h ^= v;
+        h *= 1099511628211ull;
+    };
+    mix((uint64_t)n);
+    mix((uint64_t)k_max);
+    mix((uint64_t)by_kind);
+    mix((uint64_t)effort);
+    for (const GateRec& g : in) {
+        mix((uint64_t)g.k | ((uint64_t)g.kind << 8) | (g.wide_mask << 16));
+        for (int i = 0; i < g.k; ++i) mix((uint64_t)g.qubits[i]);
+    }
+    return h;
+}
+
+// The block search (phase 1 of the fusion): groups of gate indices in
+// sequence; a group {-1 - i} is gate i kept as it is (wider than the bound).
+// Sequential: each search sees what the previous groups placed.
+static std::vector<std::vector<int>> search_groups(int n, const std::vector<GateRec>& in, int k_max, bool by_kind,
+                                                   int effort) {
     std::vector<std::vector<int>> groups;
+    std::vector<char> placed(in.size(), 0);
     const int nchunks = (n + 7) / 8;
     GateView view;  // by kind, the dense blocks take non-diagonal gates only
     for (const GateRec& g : in) {
@@ -407,6 +425,33 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
             groups.push_back(scan_group(in, placed, start, 0, 64, 1 << 14, kMaxK, &accept));
         } else {
             groups.push_back(best_first_group(view, placed, start, k_max, effort));
+        }
+    }
+    return groups;
+}
+
+static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, std::vector<GateRec>& out,
+                           int effort, FuseCache* cache) {
+    if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
+    out.clear();
+    // 1. the grouping: searched, or reused while qubits and kinds are unchanged
+    std::vector<std::vector<int>> groups;
+    bool hit = false;
+    const uint64_t key = cache ? grouping_key(n, in, k_max, by_kind, effort) : 0;
+    if (cache) {
+        std::lock_guard<std::mutex> lk(cache->mu);
+        if (cache->valid && cache->key == key) {
+            groups = cache->groups;
+            hit = true;
+        }
+    }
+    if (!hit) {
+        groups = search_groups(n, in, k_max, by_kind, effort);
+        if (cache) {
+            std::lock_guard<std::mutex> lk(cache->mu);
+            cache->key = key;
+            cache->groups = groups;
+            cache->valid = true;
         }
     }
     // 2. the FP64 block products, independent per group: spread over host threads
@@ -467,12 +512,14 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
     return QS_OK;
 }
 
-qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort) {
-    return fuse_impl(n, in, k_max, false, out, effort);
+qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort,
+                     FuseCache* cache) {
+    return fuse_impl(n, in, k_max, false, out, effort, cache);
 }
 
-qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort) {
-    return fuse_impl(n, in, k_max, true, out, effort);
+qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort,
+                       FuseCache* cache) {
+    return fuse_impl(n, in, k_max, true, out, effort, cache);
 }
 
 // The phase tables of a wide diagonal cluster (FP64 on the host).

@@ -111,3 +111,24 @@ def test_fused_sweep_full_size_shift_rule(qs):
     assert np.max(np.abs(grads["c128"][sample] - ps)) < 1e-9 * max(1.0, np.max(np.abs(ps)))
     ref = grads["c128"]
     assert np.linalg.norm(grads["c64"] - ref) / np.linalg.norm(ref) < 1e-4
+
+
+def test_gradient_reuses_grouping_across_angles(qs):
+    """One circuit object, several angle sets: the block grouping found for
+    the first call is reused while the gates' kinds stay the same; gradients
+    equal those of freshly built circuits, also when angles of 0 turn RY
+    gates into the identity (a different kind, so a new grouping)."""
+    n, layers = 14, 3
+    h = B.PauliSum(n, C.ising_hamiltonian(n))
+    t1 = C.ansatz_theta(n, layers, seed=21)
+    t2 = C.ansatz_theta(n, layers, seed=22)
+    t3 = t2.copy()
+    t3[::7] = 0.0
+    c = B.circuit_from(C.ansatz_circuit(n, layers, t1))
+    for theta in (t1, t2, t3, t1):
+        e, g = B.adjoint_gradient(c, theta, h, B.State(n, "c64"), B.State(n, "c64", init=None))
+        fresh = B.circuit_from(C.ansatz_circuit(n, layers, theta))
+        e0, g0 = B.adjoint_gradient(fresh, theta, h, B.State(n, "c64"), B.State(n, "c64", init=None))
+        fresh.close()
+        assert e == e0 and np.array_equal(g, g0)
+    c.close()
