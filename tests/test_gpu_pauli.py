@@ -71,3 +71,24 @@ def test_pauli_sum_empty_and_identity(qs):
     B.apply_pauli_sum(s, h, out)
     assert rel_l2(out.amplitudes(), 1.5 * psi0) < 1e-15
     assert abs(B.expectation(s, h) - 1.5 * np.vdot(psi0, psi0).real) < 1e-12
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 9, 11])
+def test_pauli_sum_small_states(qs, dtype, n):
+    """Tiles smaller than a full pass tile (down to one qubit): every term
+    kind, against the oracle."""
+    rng = Xoshiro256ss(300 + n)
+    terms = [C.PauliTerm(0.7, ())]
+    for _ in range(12):
+        qs_ = sorted({rng.randint(n) for _ in range(1 + rng.randint(3))})
+        terms.append(C.PauliTerm(rng.uniform_range(-1, 1), tuple((q, "XYZ"[rng.randint(3)]) for q in qs_)))
+    psi0 = random_state(n, 40 + n)
+    h = B.PauliSum(n, terms)
+    s = to_state(psi0, n, dtype)
+    ref = oracle.expectation(psi0, n, terms)
+    tol = 2e-5 if dtype == "c64" else 1e-12
+    assert abs(B.expectation(s, h) - ref) < tol * max(1.0, abs(ref))
+    out = to_state(np.zeros(1 << n), n, dtype)
+    B.apply_pauli_sum(s, h, out)
+    assert rel_l2(out.amplitudes(), oracle.apply_pauli_sum(psi0, n, terms)) < (2e-6 if dtype == "c64" else 1e-13)

@@ -42,7 +42,7 @@ def layered_circuit(n, layers, theta, seed=11):
             circ.append((q, q + 1), G.CZ, "cz")
         for q in range(0, n - 5, 5):
             rot((q, q + 5), "ZZ")
-        circ.append((2, 9, n - 1), ccz, "ccz")
+        circ.append((2, min(9, n - 2), n - 1), ccz, "ccz")
         circ.append((n - 2,), G.T, "t")
         for q in range(n):  # fixed one-qubit gates, some complex
             u = (G.SQRT_X, G.SQRT_Y, G.H)[rng.randint(3)]
@@ -132,3 +132,22 @@ def test_gradient_reuses_grouping_across_angles(qs):
         fresh.close()
         assert e == e0 and np.array_equal(g, g0)
     c.close()
+
+
+@pytest.mark.parametrize("dtype,n", [("c64", 11), ("c64", 12), ("c64", 13), ("c128", 10), ("c128", 11)])
+def test_sweep_smallest_sizes(qs, dtype, n):
+    """At and just below the fused pass's tile size (12 qubits for complex64,
+    11 for complex128; smaller states take the per-gate paths): gradients
+    against oracle parameter shift."""
+    layers = 2
+    P = count_params(n, layers)
+    rng = Xoshiro256ss(500 + n)
+    theta = np.array([rng.uniform_range(-np.pi, np.pi) for _ in range(P)])
+    terms = C.ising_hamiltonian(n)
+    build = lambda t: layered_circuit(n, layers, t).gates
+    sample = sorted({rng.randint(P) for _ in range(40)})[:20]
+    ps = oracle.parameter_shift_gradient(n, build, theta, terms, params=sample)
+    c = B.circuit_from(layered_circuit(n, layers, theta))
+    e, g = B.adjoint_gradient(c, theta, B.PauliSum(n, terms), B.State(n, dtype), B.State(n, dtype, init=None))
+    tol = 1e-4 if dtype == "c64" else 1e-10
+    assert np.linalg.norm(g[sample] - ps) / np.linalg.norm(ps) < tol
