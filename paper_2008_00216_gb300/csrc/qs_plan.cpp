@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <atomic>
 #include <complex>
+#include <deque>
 #include <functional>
 #include <thread>
 #include <unordered_map>
@@ -205,31 +206,29 @@ static std::vector<int> scan_group(const std::vector<GateRec>& g, std::vector<ch
 struct GateView {
     std::vector<uint64_t> m;
     std::vector<uint8_t> diag, ok;
-    uint64_t allq = 0;  // the qubits of the circuit
+    std::vector<int> idx;  // the gate's index in the circuit
+    uint64_t allq = 0;     // the qubits of the circuit
 };
 
-// The scan of Section 4.5 with the block's qubit set S fixed: from `start`,
-// take every unplaced gate whose qubits lie in S and that commutes with the
-// gates skipped so far (disjoint qubits, or both diagonal); a skipped gate
-// obstructs its qubits.  With `ext`, also collect the qubits that each
+// The scan of Section 4.5 with the block's qubit set S fixed, over `v` (the
+// unplaced gates after `start`, in order): take every gate whose qubits lie
+// in S and that commutes with the gates skipped so far (disjoint qubits, or
+// both diagonal); a skipped gate obstructs its qubits.  With `ext`, also collect the qubits that each
 // reachable gate outside S would add (keeping |S| <= kmax).
-static int absorb_scan(const GateView& v, const std::vector<char>& placed, int start, uint64_t S, int window,
-                       std::vector<int>* taken, std::vector<uint64_t>* ext, int kmax) {
+static int absorb_scan(const GateView& v, int start, uint64_t S, std::vector<int>* taken, std::vector<uint64_t>* ext,
+                       int kmax) {
     int count = 1;
     if (taken) taken->push_back(start);
     uint64_t blocked_any = 0, blocked_diag = 0;
-    int scanned = 0;
     const int G = (int)v.m.size();
-    for (int j = start + 1; j < G && scanned < window; ++j) {
-        if (placed[j]) continue;
-        ++scanned;
+    for (int j = 0; j < G; ++j) {
         const uint64_t gm = v.m[j];
         const bool gdiag = v.diag[j];
         const bool commutes = (gm & blocked_any) == 0 && (gdiag || (gm & blocked_diag) == 0);
         const bool ok = v.ok[j];
         if (commutes && ok && (gm & ~S) == 0) {
             ++count;
-            if (taken) taken->push_back(j);
+            if (taken) taken->push_back(v.idx[j]);
             continue;
         }
         if (ext && commutes && ok && __builtin_popcountll(S | gm) <= kmax) ext->push_back(gm & ~S);
@@ -242,29 +241,58 @@ static int absorb_scan(const GateView& v, const std::vector<char>& placed, int s
     return count;
 }
 
+// Open-addressing map from a nonzero qubit set to an int (linear probing).
+struct SetMap {
+    std::vector<uint64_t> keys;
+    std::vector<int> vals;
+    size_t used = 0;
+    explicit SetMap(size_t cap = 1024) : keys(cap, 0), vals(cap, 0) {}
+    static size_t hash(uint64_t k) { return (size_t)((k * 0x9E3779B97F4A7C15ull) >> 20); }
+    int* find(uint64_t k) {
+        const size_t mask = keys.size() - 1;
+        for (size_t i = hash(k) & mask;; i = (i + 1) & mask) {
+            if (keys[i] == k) return &vals[i];
+            if (keys[i] == 0) return nullptr;
+        }
+    }
+    void put(uint64_t k, int v) {
+        if (2 * (used + 1) > keys.size()) {  // grow at half full
+            SetMap bigger(keys.size() * 2);
+            for (size_t i = 0; i < keys.size(); ++i)
+                if (keys[i]) bigger.put(keys[i], vals[i]);
+            *this = std::move(bigger);
+        }
+        const size_t mask = keys.size() - 1;
+        size_t i = hash(k) & mask;
+        while (keys[i] != 0 && keys[i] != k) i = (i + 1) & mask;
+        if (keys[i] == 0) ++used;
+        keys[i] = k;
+        vals[i] = v;
+    }
+};
+
 // Scans of one block's search (same placed gates and start), memoised by
 // qubit set: the completions of different candidates revisit the same sets.
 struct AbsorbCache {
-    const GateView& v;
-    const std::vector<char>& placed;
-    int start, window, kmax;
-    std::unordered_map<uint64_t, int> counts;
-    std::unordered_map<uint64_t, std::vector<uint64_t>> exts;
+    const GateView& v;  // the unplaced gates after the block's first gate
+    int start, kmax;
+    SetMap counts, ext_at;                   // set -> absorbed gates / index into exts
+    std::deque<std::vector<uint64_t>> exts;  // stable references while it grows
     int count(uint64_t S) {
-        auto it = counts.find(S);
-        if (it != counts.end()) return it->second;
-        const int c = absorb_scan(v, placed, start, S, window, nullptr, nullptr, kmax);
-        counts.emplace(S, c);
+        if (const int* c = counts.find(S)) return *c;
+        const int c = absorb_scan(v, start, S, nullptr, nullptr, kmax);
+        counts.put(S, c);
         return c;
     }
     const std::vector<uint64_t>& ext(uint64_t S) {
-        auto it = exts.find(S);
-        if (it != exts.end()) return it->second;
+        if (const int* i = ext_at.find(S)) return exts[*i];
         std::vector<uint64_t> e;
-        absorb_scan(v, placed, start, S, window, nullptr, &e, kmax);
+        absorb_scan(v, start, S, nullptr, &e, kmax);
         std::sort(e.begin(), e.end());
         e.erase(std::unique(e.begin(), e.end()), e.end());
-        return exts.emplace(S, std::move(e)).first->second;
+        ext_at.put(S, (int)exts.size());
+        exts.push_back(std::move(e));
+        return exts.back();
     }
     // the extension of S with the most absorbed gates (ties: fewer added qubits), 0 if none
     uint64_t greedy_step(uint64_t S) {
@@ -325,8 +353,17 @@ struct AbsorbCache {
 // first come, first served.
 static std::vector<int> best_first_group(const GateView& v, std::vector<char>& placed, int start, int kmax,
                                          int effort) {
-    const int window = 1 << 14;
-    AbsorbCache cache{v, placed, start, window, kmax, {}, {}};
+    // the unplaced gates after start (at most 2^14 of them), in flat arrays
+    GateView live;
+    live.allq = v.allq;
+    for (int j = start + 1; j < (int)v.m.size() && (int)live.m.size() < (1 << 14); ++j) {
+        if (placed[j]) continue;
+        live.m.push_back(v.m[j]);
+        live.diag.push_back(v.diag[j]);
+        live.ok.push_back(v.ok[j]);
+        live.idx.push_back(j);
+    }
+    AbsorbCache cache{live, start, kmax, SetMap(4096), SetMap(1024), {}};
     uint64_t S = v.m[start];
     while (__builtin_popcountll(S) < kmax) {
         const std::vector<uint64_t> ext = cache.ext(S);
@@ -352,7 +389,7 @@ static std::vector<int> best_first_group(const GateView& v, std::vector<char>& p
         S |= best;
     }
     std::vector<int> taken;
-    absorb_scan(v, placed, start, S, window, &taken, nullptr, kmax);
+    absorb_scan(live, start, S, &taken, nullptr, kmax);
     for (int t : taken) placed[t] = 1;
     return taken;
 }
