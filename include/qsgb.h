@@ -214,10 +214,14 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
  * amplitude pass (k, or the tile's L), and gates applied in it. */
 qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_gates);
 
-/* Convenience: plan with the default options and the given precision (k_max
- * 6 when `prec` is a tensor-core mode on a complex64 state, else k_max 4),
- * execute, free the plan.  Asynchronous like qs_plan_execute: the plan's
- * device memory is allocated and freed in the state's stream order. */
+/* Fuse and run a circuit with the default options and the given precision.
+ * A tensor-core mode on a complex64 state (n >= 12): 6-qubit blocks, fused
+ * and run together -- a host thread runs the block search while this call
+ * launches each block's pass (its own pass: no tile grouping) as soon as the
+ * block is found, so the search overlaps the device passes; the call returns
+ * after the last launch.  Otherwise: plan (k_max 4), execute, free the plan.
+ * Asynchronous like qs_plan_execute: matrices are allocated and freed in the
+ * state's stream order. */
 qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec);
 
 /* ------------------------------------------------------------ read back */

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <atomic>
 #include <complex>
+#include <condition_variable>
+#include <deque>
 #include <string>
 #include <thread>
 #include <map>
@@ -551,6 +553,90 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
     return QS_OK;
 }
 
+}  // extern "C"
+
+// One pass on the state's stream; `dm` holds its matrices in the state's
+// precision (the passes that take their matrix as a kernel argument ignore it).
+static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int precision) {
+    switch (ps.kind) {
+        case PASS_TILE: return launch_tile(s->data, s->n, s->dt, ps, dm, s->stream);
+        case PASS_DENSE: return launch_dense(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+        case PASS_DIAG: return launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+        case PASS_MONO: return launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
+        case PASS_GEMM: return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream);
+        case PASS_DIAG_WIDE: return launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream);
+        case PASS_DENSE_SMEM: return launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// Fuse and run together (qs_apply_circuit on the tensor cores): a host thread
+// runs the block search and hands over each group as soon as it is found;
+// this thread forms the group's block and pass (each block its own pass),
+// uploads the pass's matrix and launches it in stream order, so the GPU runs
+// pass i while the search looks for block i + 1.
+static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<std::vector<int>> queue;
+    bool done = false;
+    qs_status fst = QS_OK;
+    std::string fmsg;
+    std::thread search([&]() {
+        const qs_status st = fuse_each(c->n, c->gates, opt.k_max, opt.fusion_effort, c->fuse_cache.get(),
+                                       [&](std::vector<int>&& g) {
+                                           std::lock_guard<std::mutex> lk(mu);
+                                           queue.push_back(std::move(g));
+                                           cv.notify_one();
+                                       });
+        std::lock_guard<std::mutex> lk(mu);
+        fst = st;
+        if (st != QS_OK) fmsg = qs_last_error();
+        done = true;
+        cv.notify_one();
+    });
+    qs_status st = QS_OK;
+    const size_t esz = s->amp_bytes();
+    std::vector<char> host;
+    for (;;) {
+        std::vector<int> g;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&]() { return !queue.empty() || done; });
+            if (queue.empty()) break;
+            g = std::move(queue.front());
+            queue.pop_front();
+        }
+        if (st != QS_OK) continue;  // drain the search after a failure
+        GateRec b;
+        block_product(c->n, c->gates, g, b);
+        Pass p;
+        single_block_pass(c->n, s->dt, opt, b, p);
+        factor_tile_scalars(p);
+        void* dm = nullptr;
+        const size_t elems = p.mats.size() / 2;
+        cudaError_t e = cudaSuccess;
+        if (elems && p.kind != PASS_DENSE && p.kind != PASS_DIAG && p.kind != PASS_MONO) {
+            host.resize(elems * esz);
+            for (size_t i = 0; i < p.mats.size(); ++i) {
+                if (s->dt == QS_C64) ((float*)host.data())[i] = (float)p.mats[i];
+                else ((double*)host.data())[i] = p.mats[i];
+            }
+            // stream-ordered; a pageable source is staged before the call returns
+            e = cudaMallocAsync(&dm, elems * esz, s->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dm, host.data(), elems * esz, cudaMemcpyHostToDevice, s->stream);
+        }
+        if (e == cudaSuccess) e = launch_pass(s, p, dm, opt.precision);
+        if (dm) cudaFreeAsync(dm, s->stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "streamed pass");
+    }
+    search.join();
+    if (fst != QS_OK) return fail(fst, "%s", fmsg.c_str());
+    return st;
+}
+
+extern "C" {
+
 qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int count) {
     qs_status st = check_state(s);
     if (st != QS_OK) return st;
@@ -564,26 +650,7 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
     for (int pi = first; pi < last; ++pi) {
         const Pass& ps = p->passes[pi];
         const char* dm = (const char*)p->dev_mats + ps.dev_offset * esz;
-        cudaError_t e = cudaSuccess;
-        switch (ps.kind) {
-            case PASS_TILE: e = launch_tile(s->data, s->n, s->dt, ps, dm, s->stream); break;
-            case PASS_DENSE:
-                e = launch_dense(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
-                break;
-            case PASS_DIAG:
-                e = launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
-                break;
-            case PASS_MONO:
-                e = launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
-                break;
-            case PASS_GEMM:
-                e = launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, p->opt.precision, s->errflag, s->stream);
-                break;
-            case PASS_DIAG_WIDE: e = launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream); break;
-            case PASS_DENSE_SMEM:
-                e = launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
-                break;
-        }
+        cudaError_t e = launch_pass(s, ps, dm, p->opt.precision);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     }
     return QS_OK;
@@ -596,6 +663,12 @@ qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec) 
     qs_options_default(&opt);
     opt.precision = prec;
     if (prec != QS_PREC_FP32 && s->dt == QS_C64) opt.k_max = 6;  // 6-qubit blocks on the tensor cores
+    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XBF16) return fail(QS_ERR_ARG, "bad precision");
+    if (s->dt == QS_C64 && prec != QS_PREC_FP32 && gemm_supported(s->n, 6)) {
+        qs_status st = check_state(s);
+        if (st != QS_OK) return st;
+        return apply_streamed(s, c, opt);
+    }
     qs_plan* p = nullptr;
     // matrices allocated and freed in the state's stream order: no synchronisation
     qs_status st = plan_create_on(c, s->dt, &opt, s->stream, &p);

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -194,6 +195,14 @@ qs_status fuse_by_kind(int n, const std::vector<GateRec>& in, int k_max, std::ve
                        FuseCache* cache = nullptr);
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
+// The pass of one fused block on its own (no tile grouping).
+void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec& g, Pass& p);
+// One group's fused block (see fuse_gates): the FP64 product of in[taken].
+void block_product(int n, const std::vector<GateRec>& in, const std::vector<int>& taken, GateRec& b);
+// fuse_gates in stream form: each group of gate indices goes to `emit` as soon
+// as the block search finds it (group {-1 - i}: gate i kept as it is).
+qs_status fuse_each(int n, const std::vector<GateRec>& in, int k_max, int effort, FuseCache* cache,
+                    const std::function<void(std::vector<int>&&)>& emit);
 int auto_tile_qubits(int n, qs_dtype dt);
 // Section 4.1: one-qubit tile gates that are a scalar times a matrix with
 // entries in {0, +-1, +-i} (H, sqrt X, sqrt Y, X, Y, ...) become kTileMulfree

@@ -418,9 +418,8 @@ static uint64_t grouping_key(int n, const std::vector<GateRec>& in, int k_max, b
 // The block search (phase 1 of the fusion): groups of gate indices in
 // sequence; a group {-1 - i} is gate i kept as it is (wider than the bound).
 // Sequential: each search sees what the previous groups placed.
-static std::vector<std::vector<int>> search_groups(int n, const std::vector<GateRec>& in, int k_max, bool by_kind,
-                                                   int effort) {
-    std::vector<std::vector<int>> groups;
+static void search_groups_each(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, int effort,
+                               const std::function<void(std::vector<int>&&)>& emit) {
     std::vector<char> placed(in.size(), 0);
     const int nchunks = (n + 7) / 8;
     GateView view;  // by kind, the dense blocks take non-diagonal gates only
@@ -435,11 +434,11 @@ static std::vector<std::vector<int>> search_groups(int n, const std::vector<Gate
         const bool diag = in[start].kind == QS_GATE_DIAGONAL;
         if (in[start].k > k_max && !(by_kind && diag)) {  // wider than the bound: kept as it is
             placed[start] = 1;
-            groups.push_back({-1 - start});
+            emit({-1 - start});
             continue;
         }
         if (!by_kind) {
-            groups.push_back(best_first_group(view, placed, start, k_max, effort));
+            emit(best_first_group(view, placed, start, k_max, effort));
         } else if (diag) {
             // capacity of one wide pass: cross-chunk gates and table entries
             size_t entries = 256 * (size_t)nchunks;
@@ -459,12 +458,60 @@ static std::vector<std::vector<int>> search_groups(int n, const std::vector<Gate
             std::function<bool(const GateRec&)> accept = [&](const GateRec& g) {
                 return g.kind == QS_GATE_DIAGONAL && fits(g);
             };
-            groups.push_back(scan_group(in, placed, start, 0, 64, 1 << 14, kMaxK, &accept));
+            emit(scan_group(in, placed, start, 0, 64, 1 << 14, kMaxK, &accept));
         } else {
-            groups.push_back(best_first_group(view, placed, start, k_max, effort));
+            emit(best_first_group(view, placed, start, k_max, effort));
         }
     }
+}
+
+static std::vector<std::vector<int>> search_groups(int n, const std::vector<GateRec>& in, int k_max, bool by_kind,
+                                                   int effort) {
+    std::vector<std::vector<int>> groups;
+    search_groups_each(n, in, k_max, by_kind, effort, [&](std::vector<int>&& g) { groups.push_back(std::move(g)); });
     return groups;
+}
+
+// The fused block of one group: the gate kept as it is (group {-1 - i}), a
+// wide diagonal cluster (more than kMaxK qubits: its gates kept as parts), or
+// the FP64 product of the group's gates on their qubits (descending order,
+// qubits[0] the most significant local bit), classified.
+void block_product(int n, const std::vector<GateRec>& in, const std::vector<int>& taken, GateRec& b) {
+    if (taken[0] < 0) {
+        b = in[-1 - taken[0]];
+        b.param = -1;
+        b.paulis[0] = 0;
+        return;
+    }
+    uint64_t support = 0;
+    for (int t : taken) support |= qmask(in[t]);
+    if (__builtin_popcountll(support) > kMaxK) {  // a wide diagonal cluster: keep its gates
+        b.k = 0;
+        b.kind = QS_GATE_DIAGONAL;
+        b.wide_mask = support;
+        for (int t : taken) {
+            b.parts.push_back(in[t]);
+            b.parts.back().param = -1;
+            b.parts.back().paulis[0] = 0;
+        }
+        return;
+    }
+    b.k = __builtin_popcountll(support);
+    int bq[kMaxK];
+    int j = 0;
+    for (int q = n - 1; q >= 0; --q)
+        if ((support >> q) & 1) bq[j++] = q;  // descending: qubits[0] most significant
+    for (int i = 0; i < b.k; ++i) b.qubits[i] = bq[i];
+    const int D = 1 << b.k;
+    std::vector<cd> acc(D * D, 0.0);
+    for (int i = 0; i < D; ++i) acc[i * D + i] = 1.0;
+    for (int t : taken) apply_into_block(in[t], b.k, bq, acc);
+    b.m.resize(2 * D * D);
+    for (int i = 0; i < D * D; ++i) {
+        b.m[2 * i] = acc[i].real();
+        b.m[2 * i + 1] = acc[i].imag();
+    }
+    b.kind = classify_matrix(b.k, b.m.data());
 }
 
 static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, std::vector<GateRec>& out,
@@ -493,45 +540,7 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
     }
     // 2. the FP64 block products, independent per group: spread over host threads
     out.resize(groups.size());
-    auto build = [&](size_t gi) {
-        const std::vector<int>& taken = groups[gi];
-        GateRec& b = out[gi];
-        if (taken[0] < 0) {
-            b = in[-1 - taken[0]];
-            b.param = -1;
-            b.paulis[0] = 0;
-            return;
-        }
-        uint64_t support = 0;
-        for (int t : taken) support |= qmask(in[t]);
-        if (__builtin_popcountll(support) > kMaxK) {  // a wide diagonal cluster: keep its gates
-            b.k = 0;
-            b.kind = QS_GATE_DIAGONAL;
-            b.wide_mask = support;
-            for (int t : taken) {
-                b.parts.push_back(in[t]);
-                b.parts.back().param = -1;
-                b.parts.back().paulis[0] = 0;
-            }
-            return;
-        }
-        b.k = __builtin_popcountll(support);
-        int bq[kMaxK];
-        int j = 0;
-        for (int q = n - 1; q >= 0; --q)
-            if ((support >> q) & 1) bq[j++] = q;  // descending: qubits[0] most significant
-        for (int i = 0; i < b.k; ++i) b.qubits[i] = bq[i];
-        const int D = 1 << b.k;
-        std::vector<cd> acc(D * D, 0.0);
-        for (int i = 0; i < D; ++i) acc[i * D + i] = 1.0;
-        for (int t : taken) apply_into_block(in[t], b.k, bq, acc);
-        b.m.resize(2 * D * D);
-        for (int i = 0; i < D * D; ++i) {
-            b.m[2 * i] = acc[i].real();
-            b.m[2 * i + 1] = acc[i].imag();
-        }
-        b.kind = classify_matrix(b.k, b.m.data());
-    };
+    auto build = [&](size_t gi) { block_product(n, in, groups[gi], out[gi]); };
     size_t work = 0;
     for (const auto& g : groups) work += g.size();
     const unsigned nthreads = (unsigned)std::min<size_t>({(size_t)host_threads(16), groups.size(), work / 64 + 1});
@@ -545,6 +554,38 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
                 for (size_t gi = next++; gi < groups.size(); gi = next++) build(gi);
             });
         for (auto& th : pool) th.join();
+    }
+    return QS_OK;
+}
+
+// fuse_gates in stream form: each group is handed to `emit` as soon as the
+// block search finds it (or, on a grouping-cache hit, all at once).
+qs_status fuse_each(int n, const std::vector<GateRec>& in, int k_max, int effort, FuseCache* cache,
+                    const std::function<void(std::vector<int>&&)>& emit) {
+    if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
+    const uint64_t key = cache ? grouping_key(n, in, k_max, false, effort) : 0;
+    std::vector<std::vector<int>> groups;
+    bool hit = false;
+    if (cache) {
+        std::lock_guard<std::mutex> lk(cache->mu);
+        if (cache->valid && cache->key == key) {
+            groups = cache->groups;
+            hit = true;
+        }
+    }
+    if (hit) {
+        for (auto& g : groups) emit(std::move(g));
+        return QS_OK;
+    }
+    search_groups_each(n, in, k_max, false, effort, [&](std::vector<int>&& g) {
+        groups.push_back(g);
+        emit(std::move(g));
+    });
+    if (cache) {
+        std::lock_guard<std::mutex> lk(cache->mu);
+        cache->key = key;
+        cache->groups = std::move(groups);
+        cache->valid = true;
     }
     return QS_OK;
 }
@@ -753,6 +794,29 @@ static int low_bits(qs_dtype dt) { return dt == QS_C64 ? 5 : 4; }
 constexpr int kTileDenseK = 4;
 constexpr size_t kTileMatElems = 3072;
 
+void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec& g, Pass& p) {
+    const bool tensor = dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6);
+    if (g.k == 0) {
+        p.kind = PASS_DIAG_WIDE;
+        build_wide_diag(n, g, p);
+        return;
+    }
+    p.k = g.k;
+    for (int i = 0; i < g.k; ++i) p.qubits[i] = g.qubits[i];
+    p.gate_kind = g.kind;
+    p.mats = g.m;
+    if (g.kind == QS_GATE_DIAGONAL) p.kind = PASS_DIAG;
+    else if (g.kind == QS_GATE_MONOMIAL) p.kind = PASS_MONO;
+    else if (g.k <= 3 || (g.k == 4 && !tensor)) p.kind = PASS_DENSE;
+    else if (tensor) {
+        // the tensor-core pass is 6-qubit only; a 4-qubit block is also
+        // cheaper there than on the FP32 CUDA cores (64 FMA per amplitude)
+        p.kind = PASS_GEMM;
+        while (p.k < 6) pad_to_six(n, p);
+        sort_qubits_descending(p);
+    } else p.kind = PASS_DENSE_SMEM;
+}
+
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes) {
     passes.clear();
@@ -760,7 +824,6 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
     const int b = std::min(low_bits(dt), L);
     const uint64_t lowmask = (b >= 64) ? ~0ull : ((1ull << b) - 1);
     std::vector<char> placed(blocks.size(), 0);
-    const bool tensor = dt == QS_C64 && opt.precision != QS_PREC_FP32 && gemm_supported(n, 6);
     for (int start = 0; start < (int)blocks.size(); ++start) {
         if (placed[start]) continue;
         std::vector<int> taken;
@@ -785,25 +848,8 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
             placed[start] = 1;
         }
         Pass p;
-        if (taken.size() == 1 && blocks[taken[0]].k == 0) {
-            p.kind = PASS_DIAG_WIDE;
-            build_wide_diag(n, blocks[taken[0]], p);
-        } else if (taken.size() == 1) {
-            const GateRec& g = blocks[taken[0]];
-            p.k = g.k;
-            for (int i = 0; i < g.k; ++i) p.qubits[i] = g.qubits[i];
-            p.gate_kind = g.kind;
-            p.mats = g.m;
-            if (g.kind == QS_GATE_DIAGONAL) p.kind = PASS_DIAG;
-            else if (g.kind == QS_GATE_MONOMIAL) p.kind = PASS_MONO;
-            else if (g.k <= 3 || (g.k == 4 && !tensor)) p.kind = PASS_DENSE;
-            else if (tensor) {
-                // the tensor-core pass is 6-qubit only; a 4-qubit block is
-                // also cheaper there than on the FP32 CUDA cores (64 FMA per amplitude)
-                p.kind = PASS_GEMM;
-                while (p.k < 6) pad_to_six(n, p);
-                sort_qubits_descending(p);
-            } else p.kind = PASS_DENSE_SMEM;
+        if (taken.size() == 1) {
+            single_block_pass(n, dt, opt, blocks[taken[0]], p);
         } else {
             p.kind = PASS_TILE;
             uint64_t S = lowmask;

@@ -116,3 +116,27 @@ def test_below_one_tile_uses_cuda_cores(qs):
                          use_tile=False)
     assert "tensor" not in info["per_kind"], info
     assert rel_l2(got, oracle.apply_gate(psi0, n, qubits, m)) < 2e-6
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "tf32", "3xbf16"])
+def test_apply_circuit_streamed(qs, prec):
+    """qs_apply_circuit on the tensor cores fuses and runs together (each block
+    launched as the search finds it): the oracle's state, and the same state
+    as a plan built from the same circuit; also on a repeat call (grouping
+    cached on the circuit) and on a circuit with small remainder blocks."""
+    tol = {"3xtf32": 2e-5, "tf32": 5e-3, "3xbf16": 2e-4}[prec]
+    for n, cycles, seed in ((14, 6, 3), (17, 5, 4), (12, 3, 5)):
+        circ = C.scale_grid_circuit(n, cycles, seed=seed)
+        ref = oracle.simulate(n, circ.gates)
+        c = B.circuit_from(circ)
+        for _ in range(2):
+            s = B.State(n, "c64")
+            B.apply_circuit(s, c, prec)
+            got = s.amplitudes()
+            s.close()
+            assert rel_l2(got, ref) < tol, (n, prec)
+        p = B.Plan(c, "c64", k_max=6, precision=prec)
+        s = B.State(n, "c64")
+        p.execute(s)
+        assert rel_l2(s.amplitudes(), ref) < tol
+        s.close(); p.close(); c.close()
