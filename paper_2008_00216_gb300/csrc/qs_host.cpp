@@ -1127,7 +1127,6 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
     for (int k = 0; k < RB; ++k) rmask |= 1ull << rq[k];
     SweepDiagRec d{};
     d.nchunks = (uint8_t)nchunks;
-    for (int k = 0; k < RB; ++k) d.touched |= (uint8_t)(1u << (rq[k] >> 3));
     d.tab = (uint32_t)(p.tabs.size() / 2);
     std::vector<std::complex<double>> tab(256 * (size_t)nchunks, 1.0);
     struct Cross { DiagCross x; std::vector<std::complex<double>> e; bool touched; };

@@ -337,8 +337,8 @@ struct SweepOpRec {
     uint32_t idx;          // G1: coefficients (4 elements: the entries, or z, y, x); DIAG: diagonal record
 };
 struct SweepDiagRec {
-    uint8_t nchunks;       // chunk c = qubits 8c .. 8c+7
-    uint8_t touched;       // bit c: a register qubit lies in chunk c (looked up per amplitude)
+    uint8_t nchunks;       // chunk c = qubits 8c .. 8c+7; chunk 0 (with the register qubits) is looked up per amplitude
+    uint8_t pad0;
     uint8_t ncross, nct;   // cross gates; the first nct hold a register qubit
     uint16_t cross0, gen0; // first cross gate / Z generator in the pass's lists
     uint8_t ngen, nstaged; // Z generators; the first nstaged are summed per thread
