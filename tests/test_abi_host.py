@@ -121,3 +121,35 @@ def test_fused_block_kinds_are_exact():
     gates = [((0, 1), G.CZ), ((1,), G.T), ((0,), G.S), ((1, 2), G.cphase(0.3))]
     f = B.fuse(B.Circuit(3, gates), 3)
     assert [k for _, _, k in f.gates()] == ["diagonal"]
+
+
+@pytest.mark.parametrize("k_max", [2, 4, 6])
+def test_block_search_preserves_circuits_with_commuting_runs(k_max):
+    """The block search moves gates past commuting ones (disjoint qubits, or
+    diagonal past diagonal): circuits rich in such runs -- the paper's gate
+    set (CZ and T layers), the ansatz (RZ and CZ layers), a diagonal-heavy
+    random mix -- fuse to the same operator (FP64 oracle, 1e-13)."""
+    n = 10
+    circs = [C.paper_circuit(n, 8, seed=2), C.ansatz_circuit(n, 3, C.ansatz_theta(n, 3, seed=4)),
+             C.grid_circuit(n, 8, seed=5)]
+    rng = np.random.default_rng(7)
+    gates = []
+    for _ in range(120):
+        a, b = rng.choice(n, 2, replace=False)
+        r = rng.random()
+        if r < 0.4:
+            gates.append(((int(a), int(b)), G.CZ))
+        elif r < 0.6:
+            gates.append(((int(a),), G.T))
+        elif r < 0.8:
+            gates.append(((int(a), int(b)), G.cphase(float(rng.random()))))
+        else:
+            gates.append(((int(a),), G.SQRT_X if r < 0.9 else G.H))
+    for circ in circs + [gates]:
+        glist = circ if isinstance(circ, list) else circ.gates
+        c = B.Circuit(n, glist) if isinstance(circ, list) else B.circuit_from(circ)
+        f = B.fuse(c, k_max)
+        assert all(len(q) <= max(k_max, 2) for q, _, _ in f.gates())
+        psi0 = random_state(n, 11)
+        ref = oracle.simulate(n, glist if isinstance(circ, list) else circ.gates, psi0)
+        assert oracle.metrics.rel_l2(oracle.simulate(n, _oracle_of(f), psi0), ref) < 1e-13
