@@ -58,7 +58,7 @@ namespace qsgb {
 // the FP64 block products).
 struct FuseCache {
     std::mutex mu;
-    uint64_t key = 0;
+    std::vector<uint64_t> key;   // the search's settings and every gate's qubits and kind
     bool valid = false;
     std::vector<std::vector<int>> groups;
 };

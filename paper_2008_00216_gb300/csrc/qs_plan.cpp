@@ -397,27 +397,22 @@ static std::vector<int> best_first_group(const GateView& v, std::vector<char>& p
 // by_kind = false: any gates fuse while their qubits fit k_max.  by_kind =
 // true: diagonal gates only with diagonal gates, in clusters of any width
 // (bounded by what one wide pass holds), the others only with each other.
-// What the grouping depends on: the gates' qubits and kinds, and the search.
-static uint64_t grouping_key(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, int effort) {
-    uint64_t h = 1469598103934665603ull;
-    auto mix = [&](uint64_t v) {
-        h ^= v;
-        h *= 1099511628211ull;
-    };
-    mix((uint64_t)n);
-    mix((uint64_t)k_max);
-    mix((uint64_t)by_kind);
-    mix((uint64_t)effort);
+// What the grouping depends on: the gates' qubits and kinds, and the search
+// (compared in full on a cache hit).
+static std::vector<uint64_t> grouping_key(int n, const std::vector<GateRec>& in, int k_max, bool by_kind,
+                                          int effort) {
+    std::vector<uint64_t> key;
+    key.reserve(in.size() * 2 + 1);
+    key.push_back((uint64_t)n | ((uint64_t)k_max << 8) | ((uint64_t)by_kind << 16) | ((uint64_t)effort << 24));
     for (const GateRec& g : in) {
-        mix((uint64_t)g.k | ((uint64_t)g.kind << 8) | (g.wide_mask << 16));
-        for (int i = 0; i < g.k; ++i) mix((uint64_t)g.qubits[i]);
+        uint64_t q = 0;
+        for (int i = 0; i < g.k; ++i) q |= (uint64_t)(g.qubits[i] & 63) << (6 * i);  // ordered qubits
+        key.push_back(q | ((uint64_t)g.k << 36) | ((uint64_t)g.kind << 40));
+        key.push_back(g.wide_mask);
     }
-    return h;
+    return key;
 }
 
-// The block search (phase 1 of the fusion): groups of gate indices in
-// sequence; a group {-1 - i} is gate i kept as it is (wider than the bound).
-// Sequential: each search sees what the previous groups placed.
 static void search_groups_each(int n, const std::vector<GateRec>& in, int k_max, bool by_kind, int effort,
                                const std::function<void(std::vector<int>&&)>& emit) {
     std::vector<char> placed(in.size(), 0);
@@ -521,7 +516,8 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
     // 1. the grouping: searched, or reused while qubits and kinds are unchanged
     std::vector<std::vector<int>> groups;
     bool hit = false;
-    const uint64_t key = cache ? grouping_key(n, in, k_max, by_kind, effort) : 0;
+    std::vector<uint64_t> key;
+    if (cache) key = grouping_key(n, in, k_max, by_kind, effort);
     if (cache) {
         std::lock_guard<std::mutex> lk(cache->mu);
         if (cache->valid && cache->key == key) {
@@ -563,7 +559,8 @@ static qs_status fuse_impl(int n, const std::vector<GateRec>& in, int k_max, boo
 qs_status fuse_each(int n, const std::vector<GateRec>& in, int k_max, int effort, FuseCache* cache,
                     const std::function<void(std::vector<int>&&)>& emit) {
     if (k_max < 1 || k_max > kMaxK) return fail(QS_ERR_ARG, "k_max must be in 1..6");
-    const uint64_t key = cache ? grouping_key(n, in, k_max, false, effort) : 0;
+    std::vector<uint64_t> key;
+    if (cache) key = grouping_key(n, in, k_max, false, effort);
     std::vector<std::vector<int>> groups;
     bool hit = false;
     if (cache) {
@@ -583,7 +580,7 @@ qs_status fuse_each(int n, const std::vector<GateRec>& in, int k_max, int effort
     });
     if (cache) {
         std::lock_guard<std::mutex> lk(cache->mu);
-        cache->key = key;
+        cache->key = std::move(key);
         cache->groups = std::move(groups);
         cache->valid = true;
     }
