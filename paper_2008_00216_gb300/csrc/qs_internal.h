@@ -383,6 +383,13 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
 
 int num_sms();
 
+// State helpers shared by the C ABI files: argument check of a state, its
+// result slots (device doubles after the partials), and the report of a
+// timed-out bounded device wait (QS_ERR_TIMEOUT; the flag is cleared).
+qs_status check_state(const qs_state* s);
+double* result_area(const qs_state* s);
+qs_status check_device_flag(const qs_state* s);
+
 // Host threads a planning step may use (fusion products, stage plans): the
 // hardware's, at most `cap`; workers that already run in parallel (batched
 // gradients) set the calling thread's cap to 1.
