@@ -153,3 +153,16 @@ def test_block_search_preserves_circuits_with_commuting_runs(k_max):
         psi0 = random_state(n, 11)
         ref = oracle.simulate(n, glist if isinstance(circ, list) else circ.gates, psi0)
         assert oracle.metrics.rel_l2(oracle.simulate(n, _oracle_of(f), psi0), ref) < 1e-13
+
+
+def test_options_fusion_effort():
+    """qs_options_default selects the block search with the lookahead step;
+    an effort outside {0, 1} is rejected before any device work."""
+    o = B.options()
+    assert o.fusion_effort == 1 and o.k_max == 4 and o.fuse == 1
+    assert B.options(fusion_effort=0).fusion_effort == 0
+    c = B.circuit_from(C.small_grid_circuit())
+    for bad in (-1, 2):
+        with pytest.raises(B.QsError) as ei:
+            B.Plan(c, "c64", opts=B.options(fusion_effort=bad))
+        assert ei.value.status == 1  # QS_ERR_ARG
