@@ -248,9 +248,13 @@ qs_status qs_norm(const qs_state* s, double* out);
  * Scratch: a fixed device array of 4096 partial sums (plus a result slot,
  * about 32 KB) inside the library, held by every GPU that loads it until the
  * process exits.  A GPU that needs more partial sums than that (more than
- * 1024 SMs) gets QS_ERR_UNSUPPORTED.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the one
+ * 1024 SMs) gets QS_ERR_UNSUPPORTED.  Each call outside stream capture looks
+ * up the array's device address (cudaGetSymbolAddress) with the current
+ * device, so the address stays valid across a device reset; a call during a
+ * capture reuses the address of the last uncaptured call on that device, so
+ * make one call before any stream capture (a first call made during a
+ * capture returns QS_ERR_STATE).  The amplitudes must be on the current
+ * device.  All calls share the one
  * array and it keeps the last call's contents (each call overwrites every
  * entry it reads, so nothing needs clearing): calls whose work overlaps on
  * the GPU -- on different streams, or from several host threads -- race and

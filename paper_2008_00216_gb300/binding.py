@@ -239,10 +239,26 @@ class State:
 
 def norm_noalloc(tensor, n: int, dtype="c64", stream=None) -> float:
     """sum |alpha|^2 of a raw CUDA tensor through qs_norm_noalloc, which
-    allocates no device memory (for callers that cannot allocate)."""
+    allocates no device memory (for callers that cannot allocate).  The C
+    entry point only sees a pointer, so the tensor is checked here: the
+    state dtype, exactly 2^n contiguous amplitudes, on a CUDA device (the
+    call runs with that device current)."""
+    import torch
+    if dtype not in ("c64", "c128"):
+        raise ValueError("dtype must be 'c64' or 'c128'")
+    tdt = torch.complex64 if dtype == "c64" else torch.complex128
+    if tensor.dtype != tdt:
+        raise ValueError(f"tensor dtype {tensor.dtype} does not match the state dtype {dtype}")
+    if not 1 <= int(n) <= 40 or tensor.numel() != (1 << int(n)):
+        raise ValueError(f"tensor holds {tensor.numel()} amplitudes, not 2^{n}")
+    if not tensor.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if not tensor.is_cuda:
+        raise ValueError("tensor must be a CUDA tensor")
     v = ct.c_double()
-    _call("qs_norm_noalloc", ct.c_void_p(tensor.data_ptr()), int(n), QS_C64 if dtype == "c64" else QS_C128,
-          ct.c_void_p(_stream_ptr(stream)), ct.byref(v))
+    with torch.cuda.device(tensor.device):
+        _call("qs_norm_noalloc", ct.c_void_p(tensor.data_ptr()), int(n), QS_C64 if dtype == "c64" else QS_C128,
+              ct.c_void_p(_stream_ptr(stream)), ct.byref(v))
     return v.value
 
 

@@ -257,10 +257,22 @@ __global__ void __launch_bounds__(256) k_diag_stage(typename C2<R>::T* __restric
         flush_multi();
     } else {
         const uint64_t N = 1ull << a.n;
-        for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < N; x += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t x0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, xs = (uint64_t)gridDim.x * blockDim.x;
+        // one-qubit generators first (reads only): each thread sums its
+        // amplitudes, the warp reduces, lane 0 adds -- a fixed order
+        for (int g = 0; g < a.nsingle; ++g) {
+            R acc = 0;
+            for (uint64_t x = x0; x < N; x += xs) {
+                const T p = psi[x], l = lam[x];
+                const R v = l.x * p.y - l.y * p.x;
+                acc += ((x >> a.zbit[g]) & 1) ? -v : v;
+            }
+            acc = wsum(acc);
+            if (lane == 0) red[warp][g] += (double)acc;
+        }
+        for (uint64_t x = x0; x < N; x += xs) {
             const T p = psi[x], l = lam[x];
             const R v = l.x * p.y - l.y * p.x;
-            for (int g = 0; g < a.nsingle; ++g) atomicAdd(&red[warp][g], (double)(((x >> a.zbit[g]) & 1) ? -v : v));
             multi(x, v);
             if (a.apply) {
                 T ph = tab[x & 255];

@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cmath>
 #include <complex>
 #include <condition_variable>
 #include <deque>
@@ -103,8 +104,7 @@ static qs_status check_gate_args(int n, const int* qubits, int k, const double* 
     }
     const int d = 1 << k;
     for (int i = 0; i < 2 * d * d; ++i)
-        if (!(m[i] == m[i]) || m[i] > 1e300 || m[i] < -1e300)
-            return fail(QS_ERR_ARG, "matrix entry %d is not finite", i);
+        if (!std::isfinite(m[i])) return fail(QS_ERR_ARG, "matrix entry %d is not finite", i);
     return QS_OK;
 }
 

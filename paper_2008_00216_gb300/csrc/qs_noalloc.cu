@@ -21,18 +21,25 @@ static __device__ __align__(256) double g_norm_scratch[kNoAllocMaxPartials + 8];
 
 // Device address of g_norm_scratch per device.  In host code the array's
 // name is only a host-side stand-in, so the address is looked up with
-// cudaGetSymbolAddress once per device (with that device current).
+// cudaGetSymbolAddress (with that device current).  Outside stream capture
+// every call looks it up again, so the address stays right after a device
+// reset reloads the library's module; a call made during a capture uses
+// the address found by the last call on that device outside any capture.
 constexpr int kNoAllocMaxDevices = 64;
 static double* g_norm_scratch_dev[kNoAllocMaxDevices] = {nullptr};
 static std::mutex g_norm_scratch_mu;
 
-static qs_status norm_scratch_address(int dev, double** out) {
+static qs_status norm_scratch_address(int dev, cudaStream_t st, double** out) {
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    QS_CUDA(cudaStreamIsCapturing(st, &cap));
     std::lock_guard<std::mutex> lock(g_norm_scratch_mu);
-    if (!g_norm_scratch_dev[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_norm_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(norm scratch)");
         g_norm_scratch_dev[dev] = static_cast<double*>(p);
+    } else if (!g_norm_scratch_dev[dev]) {
+        return fail(QS_ERR_STATE, "first qs_norm_noalloc call on device %d made during stream capture", dev);
     }
     *out = g_norm_scratch_dev[dev];
     return QS_OK;
@@ -58,12 +65,12 @@ extern "C" qs_status qs_norm_noalloc(const void* device_amplitudes, int n, qs_dt
         return fail(QS_ERR_UNSUPPORTED,
                     "this GPU needs %d partial sums, more than the %d the fixed scratch array holds", nb,
                     kNoAllocMaxPartials);
+    cudaStream_t s = (cudaStream_t)stream;
     double* scratch = nullptr;
-    qs_status st = norm_scratch_address(dev, &scratch);
+    qs_status st = norm_scratch_address(dev, s, &scratch);
     if (st != QS_OK) return st;
     // every partial the sum reads is written by the same call, and the
     // result slot is overwritten, so nothing needs clearing first
-    cudaStream_t s = (cudaStream_t)stream;
     QS_CUDA(launch_norm(device_amplitudes, n, dt, scratch, scratch + kNoAllocMaxPartials, s));
     QS_CUDA(cudaMemcpyAsync(out, scratch + kNoAllocMaxPartials, sizeof(double), cudaMemcpyDeviceToHost, s));
     QS_CUDA(cudaStreamSynchronize(s));

@@ -708,7 +708,7 @@ void factor_tile_scalars(Pass& p) {
     p.scale_c[1] = total.imag();
 }
 
-// Widen a 5-qubit dense pass to 6 qubits: an identity on the lowest unused
+// Widen a 5-qubit dense pass to 6 qubits: an identity on the highest unused
 // qubit, placed first (most significant), so the matrix is kron(I2, M).
 static void pad_to_six(int n, Pass& p) {
     uint64_t used = 0;

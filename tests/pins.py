@@ -279,9 +279,87 @@ def check_gradients_closed_form():
         _close(fd, ref, 1e-7)
 
 
+
+# ----------------------------------------------------------------- Pauli sums
+def _pauli_sum_dense(n, terms):
+    """sum_t c_t P_t as a 2^n x 2^n matrix built with np.kron from the
+    textbook Pauli matrices of the gate library (qubit q is index bit q, so
+    it is the (n-1-q)-th factor of the Kronecker product)."""
+    mats = {"X": G.X, "Y": G.Y, "Z": G.Z}
+    h = np.zeros((1 << n, 1 << n), dtype=np.complex128)
+    for t in terms:
+        ops = dict(t.ops)
+        m = np.ones((1, 1), dtype=np.complex128)
+        for q in range(n - 1, -1, -1):
+            m = np.kron(m, mats[ops[q]] if q in ops else G.I2)
+        h += t.coeff * m
+    return h
+
+
+def _random_terms(n, count, rng):
+    terms = []
+    for _ in range(count):
+        length = 1 + rng.randint(min(n, 3))
+        qs = []
+        while len(qs) < length:
+            q = rng.randint(n)
+            if q not in qs:
+                qs.append(q)
+        ops = tuple((q, "XYZ"[rng.randint(3)]) for q in qs)
+        terms.append(PauliTerm(rng.uniform_range(-2.0, 2.0), ops))
+    return terms
+
+
+def check_pauli_sum_dense():
+    """H psi equals the np.kron-built matrix of the Pauli sum times psi, on
+    basis states (each column of H) and random states; <psi|H psi> is the
+    expectation."""
+    rng = Xoshiro256ss(61)
+    for n in (1, 3, 6, 8):
+        terms = _random_terms(n, 2 + 2 * n, rng)
+        terms.append(PauliTerm(0.75, ((n - 1, "Y"),)))    # a Y on the top qubit in every case
+        h = _pauli_sum_dense(n, terms)
+        for j in (0, 1, (1 << n) - 1, (5 * n) % (1 << n)):
+            _close(oracle.apply_pauli_sum(oracle.basis_state(n, j), n, terms), h[:, j], 1e-14)
+        psi = random_state(n, 70 + n)
+        hpsi = oracle.apply_pauli_sum(psi, n, terms)
+        _close(hpsi, h @ psi, 1e-13)
+        assert abs(np.vdot(psi, hpsi).real - oracle.expectation(psi, n, terms)) < 1e-13
+        assert abs(np.vdot(psi, h @ psi).imag) < 1e-13          # Hermitian: a real expectation
+
+
+# ----------------------------------------------------------------- error measures
+def check_error_metrics():
+    """Relative L2, max |dp| and total variation on vectors worked by hand:
+    psi = (1, 0) against ref = (0.6, 0.8): d = (0.4, -0.8), |d| = sqrt(0.8);
+    p = (1, 0), p_ref = (0.36, 0.64): max |dp| = 0.64, TV = (0.64 + 0.64)/2.
+    A relative phase changes the amplitudes (relative L2 = 1 below) but no
+    probability (max |dp| = TV = 0)."""
+    from oracle import metrics as M
+    psi, ref = np.array([1.0, 0.0]), np.array([0.6, 0.8])
+    assert abs(M.rel_l2(psi, ref) - math.sqrt(0.8)) < 1e-15
+    assert abs(M.max_prob_error(psi, ref) - 0.64) < 1e-15
+    assert abs(M.tv_distance(psi, ref) - 0.64) < 1e-15
+    s = 1 / math.sqrt(2)
+    psi, ref = np.array([1j * s, s]), np.array([s, s])
+    assert abs(M.rel_l2(psi, ref) - 1.0) < 1e-15
+    assert M.max_prob_error(psi, ref) < 1e-16 and M.tv_distance(psi, ref) < 1e-16
+    # three outcomes, two of them moved: TV is half the summed moves, max the largest
+    psi = np.array([math.sqrt(0.5), math.sqrt(0.3), math.sqrt(0.2)])
+    ref = np.array([math.sqrt(0.4), math.sqrt(0.3), math.sqrt(0.3)])
+    assert abs(M.max_prob_error(psi, ref) - 0.1) < 1e-15
+    assert abs(M.tv_distance(psi, ref) - 0.1) < 1e-15
+    psi = np.array([math.sqrt(0.7), math.sqrt(0.1), math.sqrt(0.2)])
+    assert abs(M.max_prob_error(psi, ref) - 0.3) < 1e-15
+    assert abs(M.tv_distance(psi, ref) - 0.3) < 1e-15         # (0.3 + 0.2 + 0.1) / 2
+    # the same pair swapped: the largest move is now a decrease (-0.3)
+    assert abs(M.max_prob_error(ref, psi) - 0.3) < 1e-15
+    assert abs(M.tv_distance(ref, psi) - 0.3) < 1e-15
+    assert abs(M.rel_l2_vec(np.array([3.0, 4.0]), np.array([0.0, 5.0])) - math.sqrt(10) / 5) < 1e-15
+
 ALL_CHECKS = [
     check_basis_convention, check_eq1_cz, check_unitary_builder_vs_kron, check_brute_force,
     check_kron_coalescing, check_h_layer_uniform, check_ghz, check_qft_basis,
     check_norm_preserved, check_norm_exact, check_reorder_invariance, check_gate_constants,
-    check_expectation_closed_forms, check_gradients_closed_form,
+    check_expectation_closed_forms, check_gradients_closed_form, check_pauli_sum_dense, check_error_metrics,
 ]

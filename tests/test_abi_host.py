@@ -166,3 +166,19 @@ def test_options_fusion_effort():
         with pytest.raises(B.QsError) as ei:
             B.Plan(c, "c64", opts=B.options(fusion_effort=bad))
         assert ei.value.status == 1  # QS_ERR_ARG
+
+
+def test_norm_noalloc_binding_checks_the_tensor():
+    """qs_norm_noalloc only receives a pointer, so the binding checks the
+    tensor before the call: too few amplitudes for n, or a dtype other than
+    the state's, raise before anything reaches the library."""
+    import torch
+    t = torch.zeros(8, dtype=torch.complex64)
+    with pytest.raises(ValueError, match="amplitudes"):
+        B.norm_noalloc(t, 4, "c64")                     # 8 amplitudes, n = 4 needs 16
+    with pytest.raises(ValueError, match="dtype"):
+        B.norm_noalloc(t, 3, "c128")                    # complex64 data read as complex128
+    with pytest.raises(ValueError, match="contiguous"):
+        B.norm_noalloc(torch.zeros(16, dtype=torch.complex64)[::2], 3, "c64")
+    with pytest.raises(ValueError, match="CUDA"):
+        B.norm_noalloc(t, 3, "c64")                     # right size and dtype, but host memory

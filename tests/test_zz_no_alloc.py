@@ -28,8 +28,14 @@ def test_norm_noalloc_matches_norm_twice(qs, dtype):
 
 
 def test_norm_noalloc_rejects_bad_arguments(qs):
+    """The C entry point's own checks (the binding's are bypassed here)."""
+    import ctypes as ct
+    lib = B.load()
     t = torch.zeros(16, dtype=torch.complex64, device="cuda")
-    with pytest.raises(B.QsError):
-        B.norm_noalloc(t, 0, "c64")
-    with pytest.raises(B.QsError):
-        B.norm_noalloc(t[1:], 3, "c64")   # 8-byte offset: not 16-byte aligned
+    v = ct.c_double()
+    stream = ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.qs_norm_noalloc(ct.c_void_p(t.data_ptr()), 0, B.QS_C64, stream, ct.byref(v)) == 1   # n = 0
+    # 8-byte offset: not 16-byte aligned
+    assert lib.qs_norm_noalloc(ct.c_void_p(t[1:].data_ptr()), 3, B.QS_C64, stream, ct.byref(v)) == 1
+    with pytest.raises(ValueError):                     # and through the binding: too few amplitudes
+        B.norm_noalloc(t[:8], 4, "c64")
