@@ -25,6 +25,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -57,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", default="auto",
                     help="fp32 | 3xtf32 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of fp32 and 3xtf32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the adjoint, 32-qubit and batched measurements of the default line")
     ap.add_argument("--unfused", action="store_true", help="one pass per gate (no fusion, no tiles)")
     ap.add_argument("--circuit", choices=["grid", "grid_fixed", "ansatz", "paper"], default="grid",
                     help="grid: random fSim angles; grid_fixed: fSim(pi/2, pi/6) everywhere (permutation-with-"
@@ -164,52 +168,114 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- CPU (oracle) sample
 
-def cpu_sample(n: int, cycles: int, seed: int, budget_s: float) -> dict:
-    """Run the FP64 oracle gate by gate on the circuit until `budget_s`
-    seconds have passed (at least one gate); return the seconds per gate."""
-    import oracle
+def _circuit_spec(a):
+    from workloads import circuits as C
+    if a.circuit == "ansatz":
+        return C.ansatz_circuit(a.n, a.layers, C.ansatz_theta(a.n, a.layers, a.seed))
+    if a.circuit == "grid_fixed":
+        return C.grid_circuit(a.n, a.cycles, a.seed, fixed_fsim=(math.pi / 2, math.pi / 6))
+    if a.circuit == "paper":
+        return C.paper_circuit(a.n, a.depth, a.seed)
+    return C.scale_grid_circuit(a.n, a.cycles, a.seed)
+
+
+def _host_memory_bytes():
+    try:
+        return os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
+    except (ValueError, OSError):
+        return 0
+
+
+def cpu_sample_cycle(n: int, cycles: int, seed: int) -> dict:
+    """One whole cycle of the grid circuit (its one-qubit layer and its fSim
+    layer) on the C form of the FP64 oracle, all host cores (OpenMP over set
+    ids).  Returns the seconds per one-qubit and per two-qubit gate and the
+    circuit's gate counts, so that circuit time = n1 t1 + n2 t2."""
+    from oracle import omp
     from workloads import circuits as C
     circ = C.scale_grid_circuit(n, cycles, seed)
-    psi = oracle.zero_state(n)
-    t0 = time.perf_counter()
-    done = 0
-    for g in circ.gates:
-        psi = oracle.apply_gate(psi, n, g.qubits, g.matrix)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"n": n, "gates_done": done, "seconds": dt, "sec_per_gate": dt / done,
-            "circuit_gates": len(circ.gates)}
+    gates = circ.gates
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    omp.apply_gate_inplace(psi, n, gates[0].qubits, gates[0].matrix)   # untimed: touches every page
+    # the first cycle after the H layer: n one-qubit gates, then its fSim layer
+    i = n
+    sample = []
+    while i < len(gates) and gates[i].k == 1:
+        sample.append(gates[i]); i += 1
+    while i < len(gates) and gates[i].k == 2:
+        sample.append(gates[i]); i += 1
+    t = {1: 0.0, 2: 0.0}
+    cnt = {1: 0, 2: 0}
+    for g in sample:
+        t0 = time.perf_counter()
+        omp.apply_gate_inplace(psi, n, g.qubits, g.matrix)
+        t[g.k] += time.perf_counter() - t0
+        cnt[g.k] += 1
+    total = {1: sum(1 for g in gates if g.k == 1), 2: sum(1 for g in gates if g.k == 2)}
+    return {"n": n, "threads": omp.threads(), "sec_per_1q": t[1] / max(1, cnt[1]), "sec_per_2q": t[2] / max(1, cnt[2]),
+            "sample_1q": cnt[1], "sample_2q": cnt[2], "seconds": t[1] + t[2], "circuit_1q": total[1],
+            "circuit_2q": total[2]}
 
 
-def cpu_baseline(a, budget_s=20.0) -> dict:
-    """The oracle as it stands, single-threaded (BLAS pinned to one thread),
-    in a fresh process.  At 30 qubits the oracle needs ~4x the state (16 GB
-    complex128) in host memory; with less memory the sample runs at 28
-    qubits and the per-gate time is scaled by the amplitude ratio."""
-    try:
-        mem = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_AVPHYS_PAGES")
-    except (ValueError, OSError):
-        mem = 0
-    need = 4 * (16 << a.n)
-    n_used = a.n if mem > 1.5 * need else min(a.n, 28)
-    env = dict(os.environ, OPENBLAS_NUM_THREADS="1", OMP_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,bench;print(json.dumps(bench.cpu_sample(%d,%d,%d,%f)))" % (n_used, a.cycles, a.seed, budget_s))
-    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
-                       timeout=600)
+def cpu_baseline(a) -> dict:
+    """The oracle as it stands, in its C form on every host core (a fresh
+    spawned process, away from the GPU process's threads): one whole cycle of
+    the circuit timed per gate kind, scaled to the circuit's gate counts.
+    At 30 qubits the oracle holds the state in complex128 (16 GB of host
+    memory); with less memory the sample runs at 28 qubits and the time is
+    scaled by the amplitude ratio."""
+    need = 16 << a.n
+    n_used = a.n if _host_memory_bytes() > 1.5 * need else min(a.n, 28)
+    code = ("import json,bench;print(json.dumps(bench.cpu_sample_cycle(%d,%d,%d)))" % (n_used, a.cycles, a.seed))
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         raise RuntimeError("cpu baseline failed: " + r.stderr[-2000:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
     scale = float(1 << (a.n - n_used))
-    sec_circuit = d["sec_per_gate"] * scale * d["circuit_gates"]
-    return {"value": 1.0 / sec_circuit, "unit": "circuits/s", "cores": 1, "kind": "oracle",
-            "sample": (f"FP64 numpy oracle, first {d['gates_done']} gates of the {d['n']}-qubit circuit "
-                       f"({d['seconds']:.1f} s), per-gate time x {d['circuit_gates']} gates"
-                       + (f" x {int(scale)} (amplitude ratio {a.n} vs {n_used} qubits)" if scale > 1 else ""))}
+    sec_circuit = scale * (d["sec_per_1q"] * d["circuit_1q"] + d["sec_per_2q"] * d["circuit_2q"])
+    return {"value": 1.0 / sec_circuit, "unit": "circuits/s", "cores": d["threads"], "kind": "oracle",
+            "sample": (f"C FP64 oracle (OpenMP over set ids, {d['threads']} threads): one whole cycle of the "
+                       f"{d['n']}-qubit circuit ({d['sample_1q']} one-qubit + {d['sample_2q']} fSim gates, "
+                       f"{d['seconds']:.1f} s), per-kind gate time x the circuit's {d['circuit_1q']} one-qubit "
+                       f"+ {d['circuit_2q']} fSim gates"
+                       + (f", x {int(scale)} (amplitude ratio {a.n} vs {n_used} qubits)" if scale > 1 else ""))}
 
 
 # ----------------------------------------------------------------- own implementation
+
+def time_passes(plan, state, steps, warmup):
+    """Run |0> + every pass of the plan `steps` times after `warmup` untimed
+    runs, with a CUDA event after each pass on the state's (current) stream.
+    Returns (ms per step, {pass kind: (total ms, launches)}); the first pass
+    of each step is left out of the per-kind sums (it includes the |0>
+    initialisation)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    passes = plan.passes()
+    npass = len(passes)
+    for _ in range(warmup):
+        state.init_basis(0)
+        plan.execute(state)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(npass + 1)] for _ in range(steps)]
+    for s in range(steps):
+        ev[s][0].record(stream)
+        state.init_basis(0)
+        for i in range(npass):
+            plan.execute_range(state, i, 1)
+            ev[s][i + 1].record(stream)
+    torch.cuda.synchronize()
+    total = 0.0
+    by_kind = {}
+    for s in range(steps):
+        total += ev[s][0].elapsed_time(ev[s][npass])
+        for i in range(1, npass):
+            dur = ev[s][i].elapsed_time(ev[s][i + 1])
+            t, c = by_kind.get(passes[i][0], (0.0, 0))
+            by_kind[passes[i][0]] = (t + dur, c + 1)
+    return total / steps, by_kind
+
 
 def run_own(a):
     import torch
@@ -224,19 +290,11 @@ def run_own(a):
 
     import paper_2008_00216_gb300 as pkg
     from paper_2008_00216_gb300 import binding as B
-    from workloads import circuits as C
 
     pkg.load()
     esz = 8 if a.dtype == "c64" else 16
     state_bytes = (1 << a.n) * esz
-    if a.circuit == "ansatz":
-        circ = C.ansatz_circuit(a.n, a.layers, C.ansatz_theta(a.n, a.layers, a.seed))
-    elif a.circuit == "grid_fixed":
-        circ = C.grid_circuit(a.n, a.cycles, a.seed, fixed_fsim=(math.pi / 2, math.pi / 6))
-    elif a.circuit == "paper":
-        circ = C.paper_circuit(a.n, a.depth, a.seed)
-    else:
-        circ = C.scale_grid_circuit(a.n, a.cycles, a.seed)
+    circ = _circuit_spec(a)
     c = B.circuit_from(circ)
     state = B.State(a.n, a.dtype)
     stream = torch.cuda.current_stream()
@@ -403,6 +461,25 @@ def run_own(a):
             "e2e": e2e,
             "clocks": clk,
         }
+        if not a.no_extras and a.workload == "grid" and a.circuit == "grid" and a.n == 30 and a.dtype == "c64":
+            # the rest of the metric, measured in the same run: adjoint
+            # gradient vs forward (24 qubits, both dtypes), the 32-qubit
+            # circuit, and the batched form (each timed with CUDA events)
+            del plan, c
+            state.close()
+            torch.cuda.empty_cache()
+            extras = (("adjoint_c64", lambda: measure_adjoint(24, 20, 1, "c64", 5, 2)),
+                      ("adjoint_c128", lambda: measure_adjoint(24, 20, 1, "c128", 3, 1)),
+                      ("n32", lambda: measure_grid_tensor(32, 20, 1, 3, 1)),
+                      ("batch", lambda: measure_batch(512, "c64", 5, 2)))
+            for key, fn in extras:
+                try:
+                    out[key] = fn()
+                except Exception as ex:  # reported, never silently dropped
+                    out[key] = {"error": str(ex)[:300]}
+            out["adjoint"] = {"n": 24, "layers": 20,
+                              "c64": {k: out["adjoint_c64"].get(k) for k in ("forward_ms", "gradient_ms", "ratio")},
+                              "c128": {k: out["adjoint_c128"].get(k) for k in ("forward_ms", "gradient_ms", "ratio")}}
         if not a.no_cpu_baseline:
             try:
                 out["cpu_baseline"] = cpu_baseline(a)
@@ -415,26 +492,57 @@ def run_own(a):
 
 # ----------------------------------------------------------------- reference arm (the oracle)
 
-def run_reference(a):
+def run_reference(a, step_target_s: float = 6.0):
+    """The oracle (the C form, every host core) on the same circuit.  Each
+    step runs the next chunk of the circuit's gates in order (wrapping
+    around), sized from one untimed gate to take about `step_target_s`; the
+    value is the circuits' worth of gates the timed steps ran over their
+    time.  Rank 0 only; other ranks return without work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each step: a bounded sample of the circuit on the FP64 oracle
-    per_step = []
-    info = None
+    from oracle import omp
+    need = 16 << a.n
+    n = a.n if _host_memory_bytes() > 1.5 * need else min(a.n, 28)
+    circ = _circuit_spec(argparse.Namespace(**{**vars(a), "n": n}))
+    gates = circ.gates
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    psi[0] = 1.0
+    omp.apply_gate_inplace(psi, n, gates[0].qubits, gates[0].matrix)   # untimed: touches every page
+    t0 = time.perf_counter()
+    omp.apply_gate_inplace(psi, n, gates[1].qubits, gates[1].matrix)   # untimed: calibration
+    per_gate = time.perf_counter() - t0
+    chunk = max(1, min(len(gates), int(round(step_target_s / per_gate))))
+    pos = 2
+    times, done, kinds = [], 0, {1: 0, 2: 0}
     for i in range(a.warmup + a.steps):
-        d = cpu_baseline(a, budget_s=8.0)
+        t0 = time.perf_counter()
+        ran = []
+        for _ in range(chunk):
+            g = gates[pos % len(gates)]
+            omp.apply_gate_inplace(psi, n, g.qubits, g.matrix)
+            ran.append(g.k)
+            pos += 1
+        dt = time.perf_counter() - t0
         if i >= a.warmup:
-            per_step.append(1.0 / d["value"])
-            info = d
-    sec = statistics.mean(per_step)
-    value = 1.0 / sec
+            times.append(dt)
+            done += len(ran)
+            for k in ran:
+                kinds[k] = kinds.get(k, 0) + 1
+    scale = float(1 << (a.n - n))
+    sec = sum(times) * scale
+    value = (done / len(gates)) / sec
+    sample = (f"C FP64 oracle (OpenMP over set ids, {omp.threads()} threads) on the {n}-qubit circuit: "
+              f"{a.steps} timed steps of {chunk} consecutive gates each ({kinds.get(1, 0)} one-qubit + "
+              f"{kinds.get(2, 0)} two-qubit gates in all, {sum(times):.1f} s) = {done / len(gates):.3f} circuits"
+              + (f", x {int(scale)} (amplitude ratio {a.n} vs {n} qubits)" if scale > 1 else ""))
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": a.gpus,
-           "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded grid circuit generator)",
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic (seeded grid circuit generator)",
            "config": {"workload": workload_name(a), "n": a.n, "cycles": a.cycles},
-           "cpu_baseline": {"value": value, "unit": "circuits/s", "kind": "oracle", "cores": 1,
-                            "sample": info["sample"]},
+           "cpu_baseline": {"value": value, "unit": "circuits/s", "kind": "oracle", "cores": omp.threads(),
+                            "sample": sample},
            "e2e": {"value": value, "unit": "circuits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -455,38 +563,44 @@ def _events_ms(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_adjoint(a):
+def measure_adjoint(n, layers, seed, dtype, steps, warmup) -> dict:
     """Hardware-efficient ansatz (RY, RZ per qubit per layer + CZ ladder),
     transverse-field Ising H: adjoint gradient time against one forward
-    evaluation of E(theta) (circuit + expectation)."""
-    import torch
+    evaluation of E(theta) (circuit + expectation), both with CUDA events."""
     import paper_2008_00216_gb300 as pkg
     from paper_2008_00216_gb300 import binding as B
     from workloads import circuits as C
     pkg.load()
-    n, layers = a.n, a.layers
-    theta = C.ansatz_theta(n, layers, seed=a.seed)
+    theta = C.ansatz_theta(n, layers, seed=seed)
     spec = C.ansatz_circuit(n, layers, theta)
     c = B.circuit_from(spec)
     h = B.PauliSum(n, C.ising_hamiltonian(n))
-    psi, lam = B.State(n, a.dtype), B.State(n, a.dtype, init=None)
+    psi, lam = B.State(n, dtype), B.State(n, dtype, init=None)
     best = None
     # the fastest forward evaluation the library offers (tensor-core
     # 6-qubit blocks included for complex64)
-    cands = [(k, "fp32") for k in (1, 2, 3, 4)] + ([(6, "3xtf32")] if a.dtype == "c64" else [])
+    cands = [(k, "fp32") for k in (1, 2, 3, 4)] + ([(6, "3xtf32")] if dtype == "c64" else [])
     for k, prec in cands:
-        p = B.Plan(c, a.dtype, k_max=k, precision=prec)
+        p = B.Plan(c, dtype, k_max=k, precision=prec)
         ms = _events_ms(lambda: (psi.init_basis(0), p.execute(psi), B.expectation(psi, h)), 2, 1)
         if best is None or ms < best[0]:
             best = (ms, k, prec)
         p.close()
-    plan = B.Plan(c, a.dtype, k_max=best[1], precision=best[2])
-    fwd_ms = _events_ms(lambda: (psi.init_basis(0), plan.execute(psi), B.expectation(psi, h)), a.steps, a.warmup)
-    adj_ms = _events_ms(lambda: B.adjoint_gradient(c, theta, h, psi, lam), a.steps, a.warmup)
-    out = {"metric": "adjoint-gradient time vs forward", "workload": "adjoint", "value": adj_ms / fwd_ms,
-           "unit": "adjoint/forward time ratio", "higher_is_better": False, "n": n, "layers": layers,
-           "params": int(theta.size), "dtype": a.dtype, "forward_ms": fwd_ms, "forward_k_max": best[1], "forward_precision": best[2],
-           "adjoint_ms": adj_ms, "gradients_per_s": 1e3 / adj_ms, "steps": a.steps, "warmup": a.warmup}
+    plan = B.Plan(c, dtype, k_max=best[1], precision=best[2])
+    fwd_ms = _events_ms(lambda: (psi.init_basis(0), plan.execute(psi), B.expectation(psi, h)), steps, warmup)
+    adj_ms = _events_ms(lambda: B.adjoint_gradient(c, theta, h, psi, lam), steps, warmup)
+    psi.sync()
+    for o in (plan, c, h, psi, lam):
+        o.close()
+    return {"n": n, "layers": layers, "params": int(theta.size), "dtype": dtype, "forward_ms": fwd_ms,
+            "forward_k_max": best[1], "forward_precision": best[2], "gradient_ms": adj_ms, "ratio": adj_ms / fwd_ms,
+            "gradients_per_s": 1e3 / adj_ms, "steps": steps, "warmup": warmup}
+
+
+def run_adjoint(a):
+    d = measure_adjoint(a.n, a.layers, a.seed, a.dtype, a.steps, a.warmup)
+    out = {"metric": "adjoint-gradient time vs forward", "workload": "adjoint", "value": d["ratio"],
+           "unit": "adjoint/forward time ratio", "higher_is_better": False, **d, "adjoint_ms": d["gradient_ms"]}
     print(json.dumps(out), flush=True)
 
 
@@ -538,40 +652,75 @@ def run_batch_adjoint(a):
     print(json.dumps(out), flush=True)
 
 
-def run_batch(a):
-    """512 seeded grid circuits, n ~ U{10..22}, depth ~ U{8..24}: one batched
-    graph launch against looping the single-circuit plans."""
-    import torch
+def measure_batch(count, dtype, steps, warmup) -> dict:
+    """Seeded grid circuits, n ~ U{10..22}, depth ~ U{8..24}: one batched
+    graph launch (autotuned) against looping the single-circuit plans."""
     import paper_2008_00216_gb300 as pkg
     from paper_2008_00216_gb300 import binding as B
     from workloads import circuits as C
     pkg.load()
-    a.count = a.count or 512
-    specs = C.batched_workload(a.count, seed0=0)
+    specs = C.batched_workload(count, seed0=0)
     circs = [B.circuit_from(s) for s in specs]
     t0 = time.perf_counter()
-    best = B.batch_autotune(circs, a.dtype)
+    best = B.batch_autotune(circs, dtype)
     tune_s = time.perf_counter() - t0
-    bt = B.Batch(circs, a.dtype, opts=best)
-    ms = _events_ms(lambda: bt.run(), a.steps, a.warmup)
+    bt = B.Batch(circs, dtype, opts=best)
+    ms = _events_ms(lambda: bt.run(), steps, warmup)
     bt.sync()
     # loop of the single-circuit path: one plan and state per circuit, built beforehand
-    plans = [B.Plan(c, a.dtype, k_max=best.k_max) for c in circs]
-    states = [B.State(s.n, a.dtype) for s in specs]
+    plans = [B.Plan(c, dtype, k_max=best.k_max) for c in circs]
+    states = [B.State(s.n, dtype) for s in specs]
 
     def loop():
         for p, st in zip(plans, states):
             st.init_basis(0)
             p.execute(st)
-    loop_ms = _events_ms(loop, max(1, a.steps // 2), 1)
+    loop_ms = _events_ms(loop, max(1, steps // 2), 1)
     amps_gates = sum((1 << s.n) * len(s.gates) for s in specs)
-    out = {"metric": "batched circuits/s vs looped single-circuit path", "workload": "batch", "value": a.count / (ms * 1e-3),
-           "unit": "circuits/s", "higher_is_better": True, "dtype": a.dtype, "circuits": a.count,
-           "batch_ms": ms, "loop_ms": loop_ms, "loop_circuits_per_s": a.count / (loop_ms * 1e-3),
-           "speedup_vs_loop": loop_ms / ms, "autotune": {"k_max": best.k_max, "tile_qubits": best.tile_qubits,
-                                                         "seconds": tune_s}, "batch_info": bt.info(),
-           "amplitude_gate_updates_per_s": amps_gates / (ms * 1e-3), "steps": a.steps, "warmup": a.warmup}
+    info = bt.info()
+    for o in plans + states + circs + [bt]:
+        o.close()
+    return {"circuits": count, "dtype": dtype, "circuits_per_s": count / (ms * 1e-3), "batch_ms": ms,
+            "loop_ms": loop_ms, "loop_circuits_per_s": count / (loop_ms * 1e-3), "speedup_vs_loop": loop_ms / ms,
+            "autotune": {"k_max": best.k_max, "tile_qubits": best.tile_qubits, "seconds": tune_s},
+            "batch_info": info, "amplitude_gate_updates_per_s": amps_gates / (ms * 1e-3), "steps": steps,
+            "warmup": warmup}
+
+
+def run_batch(a):
+    d = measure_batch(a.count or 512, a.dtype, a.steps, a.warmup)
+    out = {"metric": "batched circuits/s vs looped single-circuit path", "workload": "batch",
+           "value": d["circuits_per_s"], "unit": "circuits/s", "higher_is_better": True, **d}
     print(json.dumps(out), flush=True)
+
+
+def measure_grid_tensor(n, cycles, seed, steps, warmup) -> dict:
+    """The grid circuit at n qubits (complex64, 6-qubit 3xTF32 tensor-core
+    blocks): time per circuit with CUDA events around every pass, passes,
+    and the tensor pass's fraction of the HBM roofline."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    pkg.load()
+    spec = C.scale_grid_circuit(n, cycles, seed)
+    c = B.circuit_from(spec)
+    plan = B.Plan(c, "c64", k_max=6, precision="3xtf32")
+    state = B.State(n, "c64")
+    ms, by_kind = time_passes(plan, state, steps, warmup)
+    state.sync()
+    peak, src = measured_peaks()
+    nbytes = 2 * (1 << n) * 8
+    kinds = {k: {"launches_per_circuit": v[1] / steps, "avg_launch_ms": v[0] / v[1],
+                 "hbm_frac": nbytes / (v[0] / v[1] * 1e-3) / 1e9 / peak} for k, v in by_kind.items()}
+    out = {"n": n, "cycles": cycles, "gates": len(spec.gates), "ms_per_circuit": ms, "passes": plan.info()["passes"],
+           "pass_kinds": plan.info()["per_kind"], "per_kind": kinds,
+           "hbm_frac": kinds.get("tensor", {}).get("hbm_frac"), "peak_gbs": peak, "peak_source": src,
+           "steps": steps, "warmup": warmup}
+    for o in (plan, c, state):
+        o.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def run_precision(a):

@@ -96,7 +96,13 @@ typedef struct qs_pauli_sum qs_pauli_sum;
  *                 best-first).  1 (default): each candidate qubit set is
  *                 scored by its completion with a one-level lookahead at
  *                 the first step (fewer blocks; tens of ms for ~1000 gates);
- *                 0: greedy completion only (a few ms).  */
+ *                 0: greedy completion only (a few ms).
+ *   inject_mma_timeout : testing only, tensor-core passes of a plan: 1 = in
+ *                 the first thread block, one producer warp withholds its
+ *                 "operand ready" arrival for the first tile, so the MMA
+ *                 issuer's bounded wait runs out (~2 s); the block stops
+ *                 its other roles, frees its tensor memory and exits, and
+ *                 qs_state_sync reports QS_ERR_TIMEOUT.  0 in normal use.  */
 typedef struct qs_options {
     int k_max;
     int tile_qubits;
@@ -106,7 +112,8 @@ typedef struct qs_options {
     int inject_wait_timeout;
     int diag_clusters;
     int fusion_effort;
-    int reserved[5];
+    int inject_mma_timeout;
+    int reserved[4];
 } qs_options;
 
 const char* qs_version(void);

@@ -34,7 +34,8 @@ class QsError(RuntimeError):
 class Options(ct.Structure):
     _fields_ = [("k_max", ct.c_int), ("tile_qubits", ct.c_int), ("use_tile", ct.c_int),
                 ("precision", ct.c_int), ("fuse", ct.c_int), ("inject_wait_timeout", ct.c_int),
-                ("diag_clusters", ct.c_int), ("fusion_effort", ct.c_int), ("reserved", ct.c_int * 5)]
+                ("diag_clusters", ct.c_int), ("fusion_effort", ct.c_int), ("inject_mma_timeout", ct.c_int),
+                ("reserved", ct.c_int * 4)]
 
 
 _P = ct.c_void_p
@@ -149,10 +150,11 @@ def _stream_ptr(stream=None) -> int:
 
 def options(k_max: int = 4, tile_qubits: int = 0, use_tile: bool = True, precision="fp32",
             fuse: bool = True, inject_wait_timeout: bool = False, diag_clusters: bool = False,
-            fusion_effort: int = 1) -> Options:
+            fusion_effort: int = 1, inject_mma_timeout: bool = False) -> Options:
     o = Options()
     _call("qs_options_default", ct.byref(o))
     o.inject_wait_timeout = 1 if inject_wait_timeout else 0
+    o.inject_mma_timeout = 1 if inject_mma_timeout else 0
     o.diag_clusters = 1 if diag_clusters else 0
     o.fusion_effort = int(fusion_effort)
     o.k_max = int(k_max)

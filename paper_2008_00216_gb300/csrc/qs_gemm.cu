@@ -180,6 +180,7 @@ struct Args {
                         // descending order, so local bit b is the b-th lowest target
     int sorted[6];      // target bits ascending
     uint64_t ntiles;    // 2^(n-6) / 64
+    int inject;         // testing: block 0's first producer warp skips its first arrival
 };
 
 template <int SPLITS, int KIND>
@@ -362,7 +363,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_st_wait();
             tc_before();
             __syncwarp();  // all lanes' tensor-memory writes done; raw slot `it` free again
-            if (lane == 0) mbar_arrive(&afull[b]);
+            // (testing: a withheld arrival makes the MMA issuer's wait run out)
+            const bool withhold = a.inject && blockIdx.x == 0 && it == 0 && pw == 0;
+            if (lane == 0 && !withhold) mbar_arrive(&afull[b]);
         }
         cp_async_wait<0>();  // nothing of ours still in flight at exit
     } else if (warp == kMmaWarp) {
@@ -495,7 +498,7 @@ static cudaError_t run(float2* psi, const float2* U, const Args& a, int* err, cu
 bool gemm_supported(int n, int k) { return k == 6 && n >= 12; }
 
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat, int precision, int* err,
-                        cudaStream_t st) {
+                        cudaStream_t st, int inject) {
     if (!gemm_supported(n, k)) return cudaErrorInvalidValue;
     for (int i = 0; i + 1 < 6; ++i)  // the planner hands over descending qubit lists
         if (qubits[i] <= qubits[i + 1]) return cudaErrorInvalidValue;
@@ -509,6 +512,7 @@ cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* 
     for (int i = 0; i < 6; ++i) a.sorted[i] = qubits[i];
     std::sort(a.sorted, a.sorted + 6);
     a.ntiles = (1ull << (n - 6)) / tc::kSets;
+    a.inject = inject ? 1 : 0;
     float2* p = (float2*)psi;
     const float2* U = (const float2*)dmat;
     switch (precision) {

@@ -557,13 +557,14 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
 
 // One pass on the state's stream; `dm` holds its matrices in the state's
 // precision (the passes that take their matrix as a kernel argument ignore it).
-static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int precision) {
+static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int precision, int inject = 0) {
     switch (ps.kind) {
         case PASS_TILE: return launch_tile(s->data, s->n, s->dt, ps, dm, s->stream);
         case PASS_DENSE: return launch_dense(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_DIAG: return launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_MONO: return launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
-        case PASS_GEMM: return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream);
+        case PASS_GEMM:
+            return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream, inject);
         case PASS_DIAG_WIDE: return launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream);
         case PASS_DENSE_SMEM: return launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
     }
@@ -650,7 +651,7 @@ qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int co
     for (int pi = first; pi < last; ++pi) {
         const Pass& ps = p->passes[pi];
         const char* dm = (const char*)p->dev_mats + ps.dev_offset * esz;
-        cudaError_t e = launch_pass(s, ps, dm, p->opt.precision);
+        cudaError_t e = launch_pass(s, ps, dm, p->opt.precision, p->opt.inject_mma_timeout);
         if (e != cudaSuccess) return cuda_fail(e, "pass launch");
     }
     return QS_OK;

@@ -233,8 +233,10 @@ cudaError_t launch_diag_wide(void* psi, int n, qs_dtype dt, const WideDiag& w, c
 // Tensor-core pass for a dense 6-qubit gate on a complex64 state (n >= 11);
 // `err` (device int) is set to 1 if a bounded device wait timed out.
 bool gemm_supported(int n, int k);
+// inject = 1 (testing only): in block 0 one producer warp withholds its
+// first "operand ready" arrival, so the MMA issuer's bounded wait runs out
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat_f32,
-                        int precision, int* err, cudaStream_t st);
+                        int precision, int* err, cudaStream_t st, int inject = 0);
 
 cudaError_t launch_init_basis(void* psi, int n, qs_dtype dt, uint64_t index, cudaStream_t st);
 cudaError_t launch_init_uniform(void* psi, int n, qs_dtype dt, cudaStream_t st);

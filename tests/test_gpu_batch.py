@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import oracle
+from oracle import omp
 from oracle.metrics import rel_l2
 from paper_2008_00216_gb300 import binding as B
 from workloads import circuits as C
@@ -79,3 +80,23 @@ def test_bounded_wait_timeout_is_reported(qs):
     good.sync()
     s = specs[0]
     assert rel_l2(good.state(0).cpu().numpy(), oracle.simulate(s.n, s.gates)) < 2e-5
+
+
+def test_batched_workload_sample_matches_oracle(qs):
+    """The batched workload itself (512 grid circuits, n ~ U{10..22}, 8-24
+    cycles, seeds 0..511) in one launch with autotuned options; 16 circuits
+    drawn with a fixed seed (plus the widest) against the oracle."""
+    specs = C.batched_workload(512, seed0=0)
+    circs = [B.circuit_from(s) for s in specs]
+    best = B.batch_autotune(circs, "c64")
+    bt = B.Batch(circs, "c64", opts=best)
+    bt.run()
+    bt.sync()
+    rng = np.random.default_rng(12)
+    pick = sorted(set(rng.choice(len(specs), 16, replace=False).tolist()) |
+                  {max(range(len(specs)), key=lambda i: (specs[i].n, len(specs[i].gates)))})
+    for i in pick:
+        s = specs[i]
+        ref = omp.simulate(s.n, s.gates)
+        got = bt.state(i).to(torch.complex128).cpu().numpy()
+        assert rel_l2(got, ref) < 2e-5, (i, s.n, len(s.gates), rel_l2(got, ref))

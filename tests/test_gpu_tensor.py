@@ -140,3 +140,34 @@ def test_apply_circuit_streamed(qs, prec):
         p.execute(s)
         assert rel_l2(s.amplitudes(), ref) < tol
         s.close(); p.close(); c.close()
+
+
+def test_tensor_pass_bounded_wait_timeout_is_reported(qs):
+    """The tensor-core pass's bounded waits: with the testing option, one
+    producer warp of the first thread block withholds its first "operand
+    ready" arrival, so the MMA issuer's wait runs out (~2 s).  That block
+    stops its other roles, frees its tensor memory and exits; the host reads
+    QS_ERR_TIMEOUT from qs_state_sync, and a correct pass then runs on the
+    same context."""
+    n = 16
+    rng = Xoshiro256ss(91)
+    qubits = [13, 9, 7, 4, 2, 1]
+    m = random_unitary(6, rng)
+    psi0 = random_state(n, 5)
+    c = B.circuit_from(_one_gate_circuit(n, qubits, m))
+    bad = B.Plan(c, "c64", k_max=6, precision="3xtf32", use_tile=False, inject_mma_timeout=True)
+    assert bad.info()["per_kind"] == {"tensor": 1}
+    s = to_state(psi0, n, "c64")
+    bad.execute(s)
+    with pytest.raises(B.QsError) as e:
+        s.sync()
+    assert e.value.status == 5
+    s.sync()                                  # the flag was cleared by the report
+    bad.close()
+    good = B.Plan(c, "c64", k_max=6, precision="3xtf32", use_tile=False)
+    s2 = to_state(psi0, n, "c64")
+    good.execute(s2)
+    s2.sync()
+    assert rel_l2(s2.amplitudes(), oracle.apply_gate(psi0, n, qubits, m)) < GATE_TOL["3xtf32"]
+    good.close()
+    c.close()
