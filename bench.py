@@ -57,7 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--k-max", type=int, default=0, help="0 = pick by a short timing sweep")
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--precision", default="auto",
-                    help="fp32 | 3xtf32 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of fp32 and 3xtf32")
+                    help="fp32 | 3xtf32 | 3xfp16 | 3xbf16 | tf32 for dense k>=5 blocks; auto = fastest of the "
+                         "FP32-accurate modes (fp32, 3xtf32, 3xfp16)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="leave out the adjoint, 32-qubit and batched measurements of the default line")
@@ -311,7 +312,7 @@ def run_own(a):
     # pick (k_max, precision) by timing one execution of each candidate
     # (excluded from the timed region); only modes at FP32-level accuracy
     cands = []
-    precs = ["fp32", "3xtf32"] if a.precision == "auto" else [a.precision]
+    precs = ["fp32", "3xtf32", "3xfp16"] if a.precision == "auto" else [a.precision]
     if a.dtype == "c128":
         precs = ["fp32"]
     dcs = {"auto": [False, True], "on": [True], "off": [False]}[a.diag_clusters]
@@ -470,7 +471,8 @@ def run_own(a):
             torch.cuda.empty_cache()
             extras = (("adjoint_c64", lambda: measure_adjoint(24, 20, 1, "c64", 5, 2)),
                       ("adjoint_c128", lambda: measure_adjoint(24, 20, 1, "c128", 3, 1)),
-                      ("n32", lambda: measure_grid_tensor(32, 20, 1, 3, 1)),
+                      ("n32", lambda: measure_grid_tensor(32, 20, 1, 3, 1,
+                                                          prec_best if prec_best != "fp32" else "3xtf32")),
                       ("batch", lambda: measure_batch(512, "c64", 5, 2)))
             for key, fn in extras:
                 try:
@@ -579,7 +581,7 @@ def measure_adjoint(n, layers, seed, dtype, steps, warmup) -> dict:
     best = None
     # the fastest forward evaluation the library offers (tensor-core
     # 6-qubit blocks included for complex64)
-    cands = [(k, "fp32") for k in (1, 2, 3, 4)] + ([(6, "3xtf32")] if dtype == "c64" else [])
+    cands = [(k, "fp32") for k in (1, 2, 3, 4)] + ([(6, "3xtf32"), (6, "3xfp16")] if dtype == "c64" else [])
     for k, prec in cands:
         p = B.Plan(c, dtype, k_max=k, precision=prec)
         ms = _events_ms(lambda: (psi.init_basis(0), p.execute(psi), B.expectation(psi, h)), 2, 1)
@@ -694,10 +696,10 @@ def run_batch(a):
     print(json.dumps(out), flush=True)
 
 
-def measure_grid_tensor(n, cycles, seed, steps, warmup) -> dict:
-    """The grid circuit at n qubits (complex64, 6-qubit 3xTF32 tensor-core
-    blocks): time per circuit with CUDA events around every pass, passes,
-    and the tensor pass's fraction of the HBM roofline."""
+def measure_grid_tensor(n, cycles, seed, steps, warmup, precision="3xtf32") -> dict:
+    """The grid circuit at n qubits (complex64, 6-qubit tensor-core blocks in
+    a split precision): time per circuit with CUDA events around every pass,
+    passes, and the tensor pass's fraction of the HBM roofline."""
     import torch
     import paper_2008_00216_gb300 as pkg
     from paper_2008_00216_gb300 import binding as B
@@ -705,7 +707,7 @@ def measure_grid_tensor(n, cycles, seed, steps, warmup) -> dict:
     pkg.load()
     spec = C.scale_grid_circuit(n, cycles, seed)
     c = B.circuit_from(spec)
-    plan = B.Plan(c, "c64", k_max=6, precision="3xtf32")
+    plan = B.Plan(c, "c64", k_max=6, precision=precision)
     state = B.State(n, "c64")
     ms, by_kind = time_passes(plan, state, steps, warmup)
     state.sync()
@@ -713,7 +715,8 @@ def measure_grid_tensor(n, cycles, seed, steps, warmup) -> dict:
     nbytes = 2 * (1 << n) * 8
     kinds = {k: {"launches_per_circuit": v[1] / steps, "avg_launch_ms": v[0] / v[1],
                  "hbm_frac": nbytes / (v[0] / v[1] * 1e-3) / 1e9 / peak} for k, v in by_kind.items()}
-    out = {"n": n, "cycles": cycles, "gates": len(spec.gates), "ms_per_circuit": ms, "passes": plan.info()["passes"],
+    out = {"n": n, "cycles": cycles, "gates": len(spec.gates), "precision": precision, "ms_per_circuit": ms,
+           "passes": plan.info()["passes"],
            "pass_kinds": plan.info()["per_kind"], "per_kind": kinds,
            "hbm_frac": kinds.get("tensor", {}).get("hbm_frac"), "peak_gbs": peak, "peak_source": src,
            "steps": steps, "warmup": warmup}
@@ -760,7 +763,7 @@ def run_precision(a):
     rows = []
     st = B.State(n, "c64")
     for k in (5, 6):
-        for prec in ("fp32", "tf32", "3xtf32", "3xbf16"):
+        for prec in ("fp32", "tf32", "3xtf32", "3xfp16", "3xbf16"):
             p = B.Plan(c, "c64", k_max=k, precision=prec)
             ms = _events_ms(lambda: (st.init_basis(0), p.execute(st)), a.steps, 1)
             st.sync()

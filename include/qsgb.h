@@ -55,13 +55,17 @@ typedef enum qs_dtype { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
 /* Arithmetic of dense fused gates with k >= 5 on a complex64 state.  FP32 is
  * plain FP32 on the CUDA cores; the others run the 2^k x 2^k complex
  * product on the tensor cores (tcgen05) with FP32 accumulation: TF32
- * operands, split 3xTF32 (hi*hi + hi*lo + lo*hi) or split 3xBF16.
+ * operands, split 3xTF32 (hi*hi + hi*lo + lo*hi), split 3xBF16, or split
+ * 3xFP16 (IEEE half parts, 11-bit significands like TF32, at the 16-bit
+ * MMA rate; every set of amplitudes and the gate are scaled by powers of
+ * two into FP16's range first, so any finite state is accepted).
  * Ignored for complex128 states (always FP64-accurate arithmetic). */
 typedef enum qs_precision {
     QS_PREC_FP32 = 0,
     QS_PREC_TF32 = 1,
     QS_PREC_3XTF32 = 2,
-    QS_PREC_3XBF16 = 3
+    QS_PREC_3XBF16 = 3,
+    QS_PREC_3XFP16 = 4
 } qs_precision;
 
 /* Kind of a (fused) gate, from its exact FP64 entries. */

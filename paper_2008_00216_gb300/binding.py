@@ -19,8 +19,8 @@ from . import _build
 _lib = None
 
 QS_C64, QS_C128 = 0, 1
-QS_PREC_FP32, QS_PREC_TF32, QS_PREC_3XTF32, QS_PREC_3XBF16 = 0, 1, 2, 3
-PRECISIONS = {"fp32": 0, "tf32": 1, "3xtf32": 2, "3xbf16": 3}
+QS_PREC_FP32, QS_PREC_TF32, QS_PREC_3XTF32, QS_PREC_3XBF16, QS_PREC_3XFP16 = 0, 1, 2, 3, 4
+PRECISIONS = {"fp32": 0, "tf32": 1, "3xtf32": 2, "3xbf16": 3, "3xfp16": 4}
 GATE_KINDS = {0: "dense", 1: "diagonal", 2: "monomial"}
 PASS_KINDS = ["tile", "dense", "diagonal", "monomial", "tensor", "dense_smem", "diagonal_wide", "r7"]
 

@@ -18,6 +18,13 @@
 //   TF32     one product, operands rounded to TF32
 //   3xTF32   A_lo G_hi + A_hi G_lo + A_hi G_hi, hi = TF32(x), lo = x - hi
 //   3xBF16   the same split with bfloat16 parts
+//   3xFP16   the same split with IEEE half parts (11-bit significands like
+//            TF32, at the 16-bit MMA rate).  FP16's exponent range is
+//            narrow, so every set's amplitudes are scaled by a power of two
+//            2^e_s that brings their largest magnitude to [2^14, 2^15), and
+//            the gate by 2^e_G likewise; the epilogue multiplies each
+//            output by 2^-(e_s + e_G).  Power-of-two scaling is exact, so
+//            the split keeps its ~22 bits whatever the state's magnitude.
 // all with FP32 accumulation.
 //
 // One persistent CTA per SM, warp-specialised:
@@ -31,6 +38,7 @@
 // Every mbarrier wait is bounded (about two seconds of clock64); on timeout
 // the CTA sets the error flag, drains its MMAs, frees tensor memory, exits.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 
 #include <algorithm>
@@ -84,6 +92,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err
     }
 }
 
+// named barrier among `count` threads (whole warps)
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -98,11 +110,15 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor: FP32 accumulate, A/B TF32 (kind 0) or BF16
-// (kind 1), both K-major, M = 128, N = kN
+// instruction descriptor: FP32 accumulate, A/B TF32 (kind 0), BF16 (kind
+// 1) or FP16 (kind 2), both K-major, M = 128, N = kN
+template <int KIND>
+__host__ __device__ constexpr uint32_t ab_format() {
+    return KIND == 0 ? 2u : KIND == 1 ? 1u : 0u;
+}
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc() {
-    return (1u << 4) | ((KIND == 0 ? 2u : 1u) << 7) | ((KIND == 0 ? 2u : 1u) << 10) | ((uint32_t)(kN >> 3) << 17) |
+    return (1u << 4) | (ab_format<KIND>() << 7) | (ab_format<KIND>() << 10) | ((uint32_t)(kN >> 3) << 17) |
            ((uint32_t)(128 >> 4) << 24);
 }
 
@@ -158,6 +174,18 @@ __device__ __forceinline__ float tf32_round(float x) {
     return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
+// FP16 scaling: the power-of-two exponent e that brings a largest magnitude
+// m into [2^14, 2^15) (m * 2^e stays below FP16's 65504), within
+// [-113, 126] so that 2^e and 2^-e are normal floats (FP32 subnormal maxima
+// are treated as 2^-126); 0 for m = 0.
+__device__ __forceinline__ int fp16_scale_exp(float m) {
+    if (!(m > 0.f)) return 0;
+    int ex = (int)((__float_as_uint(m) >> 23) & 0xFFu) - 127;   // floor(log2 m) for normal m
+    if (ex < -126) ex = -126;
+    return min(126, max(-113, 14 - ex));
+}
+__device__ __forceinline__ float exp2i(int e) { return __int_as_float((uint32_t)(127 + e) << 23); }
+
 // index of the first amplitude of set x (zero bits inserted at the targets)
 __device__ __forceinline__ uint64_t set_base(uint64_t x, const int* sorted) {
 #pragma unroll
@@ -197,7 +225,10 @@ struct Layout {
     static constexpr int kWarpRaw = 16 * 34 * 8;
     static constexpr int kSlot = kProdWarps * kWarpRaw;
     static constexpr int kR = kG + SPLITS_A * kGBytes;
-    static constexpr int kBar = kR + kRaw * kSlot;               // barriers
+    // FP16: per-set scale exponents of the 4 most recent tiles, and the two
+    // producer warps' half-row maxima of a quadrant
+    static constexpr int kScale = kR + kRaw * kSlot;
+    static constexpr int kBar = kScale + (KIND == 2 ? 4 * 64 * 4 + 2 * 2 * 64 * 4 + 64 : 0);   // barriers
     static constexpr int kTotal = kBar + 128;
 };
 
@@ -219,8 +250,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t* dfull = aempty + 2;
     uint64_t* dempty = dfull + 2;
     uint64_t* drain = dempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* sfull = drain + 1;       // FP16: a tile's set scales written (4 slots)
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sfull + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    unsigned int* gmax_slot = reinterpret_cast<unsigned int*>(tmem_slot + 2);
+    int* escale = reinterpret_cast<int*>(sm + LY::kScale);                 // [4 tiles][64 sets]
+    float* hmax = reinterpret_cast<float*>(sm + LY::kScale + 4 * 64 * 4);   // [2 parities][2 halves][64 sets]
 
     if (threadIdx.x == 0) {
         for (int b = 0; b < 2; ++b) {
@@ -230,8 +265,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&dempty[b], kEpiWarps);
         }
         mbar_init(drain, 1);
+        for (int i = 0; i < 4; ++i) mbar_init(&sfull[i], 4);
         *abort_flag = 0;
+        *gmax_slot = 0u;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // FP16: the gate's largest magnitude sets its scale 2^eG
+    int eG = 0;
+    if constexpr (KIND == 2) {
+        __syncthreads();
+        float mx = 0.f;
+        for (int idx = threadIdx.x; idx < 64 * 64; idx += blockDim.x) {
+            const float2 u = U[idx];
+            mx = fmaxf(mx, fmaxf(fabsf(u.x), fabsf(u.y)));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) atomicMax(gmax_slot, __float_as_uint(mx));   // non-negative floats order as integers
+        __syncthreads();
+        eG = fp16_scale_exp(__uint_as_float(*gmax_slot));
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
@@ -249,12 +301,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float hi = tf32_round(v);
             *reinterpret_cast<float*>(sm + LY::kG + o) = hi;
             if constexpr (SPLITS == 3) *reinterpret_cast<float*>(sm + LY::kG + LY::kGBytes + o) = tf32_round(v - hi);
-        } else {
+        } else if constexpr (KIND == 1) {
             const uint32_t o = swz(n, k >> 3) + 2u * (uint32_t)(k & 7);
             const __nv_bfloat16 hi = __float2bfloat16_rn(v);
             *reinterpret_cast<__nv_bfloat16*>(sm + LY::kG + o) = hi;
             if constexpr (SPLITS == 3)
                 *reinterpret_cast<__nv_bfloat16*>(sm + LY::kG + LY::kGBytes + o) = __float2bfloat16_rn(v - __bfloat162float(hi));
+        } else {
+            const uint32_t o = swz(n, k >> 3) + 2u * (uint32_t)(k & 7);
+            const float vs = v * exp2i(eG);
+            const __half hi = __float2half_rn(vs);
+            *reinterpret_cast<__half*>(sm + LY::kG + o) = hi;
+            if constexpr (SPLITS == 3) *reinterpret_cast<__half*>(sm + LY::kG + LY::kGBytes + o) = __float2half_rn(vs - __half2float(hi));
         }
     }
     fence_async_smem();
@@ -313,8 +371,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             cp_async_wait<LY::kRaw - 1>();
             __syncwarp();  // the warp's copies of tile `it` are visible to all its lanes
             const int b = (int)(it & 1);
-            if (!__all_sync(0xffffffffu, mbar_wait(&aempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag))) break;
-            tc_after();
             const float2* rs = reinterpret_cast<const float2*>(slice + (it % LY::kRaw) * LY::kSlot);
             float v[32];  // part c of x[set][32kh + kl], kl = 0..31
             if constexpr (Q0T) {
@@ -331,6 +387,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                     v[kl] = c ? xv.y : xv.x;
                 }
             }
+            // (the raw slot is warp-private: it was read before the wait below)
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&aempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag));
+            float sc = 1.f;
+            if constexpr (KIND == 2) {
+                // the set's scale: largest magnitude over both parts (lanes c = 0, 1)
+                // and both halves of K (the other producer warp of this quadrant,
+                // through shared memory and a named barrier of the pair); the pair
+                // also agrees on stopping, so both always pass the same barriers
+                float m = 0.f;
+#pragma unroll
+                for (int e = 0; e < 32; ++e) m = fmaxf(m, fabsf(v[e]));
+                m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 16));
+                float* hm = hmax + (int)(it & 1) * 128;                                // [half][set]
+                int* okf = reinterpret_cast<int*>(hmax + 256) + (int)(it & 1) * 8;     // [half][quadrant]
+                if (c == 0) hm[kh * 64 + 16 * q + j] = m;
+                if (lane == 0) okf[kh * 4 + q] = ok ? 1 : 0;
+                named_bar_sync(1 + q, 64);
+                m = fmaxf(m, hm[(kh ^ 1) * 64 + 16 * q + j]);
+                if (!(ok && okf[(kh ^ 1) * 4 + q] != 0)) break;
+                const int e = fp16_scale_exp(m);
+                sc = exp2i(e);
+                if (kh == 0) {
+                    if (c == 0) escale[(int)(it & 3) * 64 + 16 * q + j] = e;
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sfull[it & 3]);
+                }
+            } else {
+                if (!ok) break;
+            }
+            tc_after();
             const uint32_t acol = lane_base + (uint32_t)(b * kTmemABuf);
             if constexpr (KIND == 0) {
 #pragma unroll
@@ -345,7 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_st16(acol + (uint32_t)(32 * kh + 16 * hf), hw);
                     if constexpr (SPLITS == 3) tmem_st16(acol + (uint32_t)(LY::kACols + 32 * kh + 16 * hf), lw);
                 }
-            } else {  // two bf16 per column, lower K index in the low half
+            } else if constexpr (KIND == 1) {  // two bf16 per column, lower K index in the low half
                 uint32_t hw[16], lw[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
@@ -355,6 +441,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const float2 hf = __bfloat1622float2(hb);
                         const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * e] - hf.x, v[2 * e + 1] - hf.y);
                         lw[e] = *reinterpret_cast<const uint32_t*>(&lb);
+                    }
+                }
+                tmem_st16(acol + (uint32_t)(16 * kh), hw);
+                if constexpr (SPLITS == 3) tmem_st16(acol + (uint32_t)(LY::kACols + 16 * kh), lw);
+            } else {  // two scaled halves per column, lower K index in the low half
+                uint32_t hw[16], lw[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const float x0 = v[2 * e] * sc, x1 = v[2 * e + 1] * sc;
+                    const __half2 hh = __floats2half2_rn(x0, x1);
+                    hw[e] = *reinterpret_cast<const uint32_t*>(&hh);
+                    if constexpr (SPLITS == 3) {
+                        const float2 hf = __half22float2(hh);
+                        const __half2 lh = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+                        lw[e] = *reinterpret_cast<const uint32_t*>(&lh);
                     }
                 }
                 tmem_st16(acol + (uint32_t)(16 * kh), hw);
@@ -424,6 +525,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int b = (int)(it & 1);
             if (!__all_sync(0xffffffffu, mbar_wait(&dfull[b], (uint32_t)((it >> 1) & 1), err, abort_flag))) break;
             tc_after();
+            float unscale = 1.f, unscale_g = 1.f;
+            if constexpr (KIND == 2) {  // undo the set's and the gate's power-of-two scales
+                if (!__all_sync(0xffffffffu, mbar_wait(&sfull[it & 3], (uint32_t)((it >> 2) & 1), err, abort_flag))) break;
+                unscale = exp2i(-escale[(int)(it & 3) * 64 + 16 * q + j]);
+                unscale_g = exp2i(-eG);
+            }
             float2* dst = psi + set_base(t * kSets + (uint64_t)(16 * q + j), a.sorted);
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTmemD + b * kN);
 #pragma unroll
@@ -448,6 +555,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     } else {       // own: D[im][.]; partner: D[re][.] of outputs 16ch + 8 + rr
                         y[rr].x = rcv[2 * rr] - d[16 + 2 * rr + 1];
                         y[rr].y = d[16 + 2 * rr] + rcv[2 * rr + 1];
+                    }
+                    if constexpr (KIND == 2) {  // two steps: the product of the scales may leave FP32's range
+                        y[rr].x = (y[rr].x * unscale) * unscale_g;
+                        y[rr].y = (y[rr].y * unscale) * unscale_g;
                     }
                 }
                 if constexpr (Q0T) {
@@ -519,6 +630,7 @@ cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* 
         case QS_PREC_TF32: return tc::run<1, 0>(p, U, a, err, st);
         case QS_PREC_3XTF32: return tc::run<3, 0>(p, U, a, err, st);
         case QS_PREC_3XBF16: return tc::run<3, 1>(p, U, a, err, st);
+        case QS_PREC_3XFP16: return tc::run<3, 2>(p, U, a, err, st);
     }
     return cudaErrorInvalidValue;
 }

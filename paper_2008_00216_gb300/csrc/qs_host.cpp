@@ -457,7 +457,7 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     const int maxL = dt == QS_C64 ? 13 : 12;
     if (opt.tile_qubits != 0 && (opt.tile_qubits < 6 || opt.tile_qubits > maxL))
         return fail(QS_ERR_ARG, "tile_qubits outside 6..%d", maxL);
-    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XBF16)
+    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XFP16)
         return fail(QS_ERR_ARG, "bad precision");
     std::unique_ptr<qs_plan> p(new (std::nothrow) qs_plan);
     if (!p) return fail(QS_ERR_OOM, "host allocation failed");
@@ -664,7 +664,7 @@ qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec) 
     qs_options_default(&opt);
     opt.precision = prec;
     if (prec != QS_PREC_FP32 && s->dt == QS_C64) opt.k_max = 6;  // 6-qubit blocks on the tensor cores
-    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XBF16) return fail(QS_ERR_ARG, "bad precision");
+    if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XFP16) return fail(QS_ERR_ARG, "bad precision");
     if (s->dt == QS_C64 && prec != QS_PREC_FP32 && gemm_supported(s->n, 6)) {
         qs_status st = check_state(s);
         if (st != QS_OK) return st;

@@ -47,7 +47,7 @@ def test_autograd_matches_parameter_shift(qs, dtype, device):
     ps = ref["ps"]
     err = np.linalg.norm(g[ref["params"]] - ps) / np.linalg.norm(ps)
     assert err < TOL[dtype], err
-    assert abs(float(e) - ref["energy"]) < (1e-4 if dtype == "c64" else 1e-10) * max(1.0, abs(ref["energy"]))
+    assert abs(e.item() - ref["energy"]) < (1e-4 if dtype == "c64" else 1e-10) * max(1.0, abs(ref["energy"]))
 
 
 def test_autograd_chain_rule_and_no_grad(qs):
@@ -65,7 +65,7 @@ def test_autograd_chain_rule_and_no_grad(qs):
     assert torch.allclose(gl, (2 + 2 * e.detach()) * g, rtol=1e-12, atol=1e-14)
     with torch.no_grad():
         e3 = mod(theta.detach())
-    assert abs(float(e3) - float(e)) < 1e-11
+    assert abs(e3.item() - e.item()) < 1e-11
     t32 = torch.tensor(ref["theta"], dtype=torch.float32, device="cuda", requires_grad=True)
     (g32,) = torch.autograd.grad(mod(t32), t32)
     assert g32.dtype == torch.float32 and g32.device == t32.device

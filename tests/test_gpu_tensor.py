@@ -15,7 +15,7 @@ from gpu_util import run_plan, to_state
 pytestmark = pytest.mark.gpu
 
 # per-gate relative L2 bounds: TF32 keeps ~11 bits; the split modes ~FP32
-GATE_TOL = {"tf32": 3e-3, "3xtf32": 2e-6, "3xbf16": 3e-5}
+GATE_TOL = {"tf32": 3e-3, "3xtf32": 2e-6, "3xbf16": 3e-5, "3xfp16": 2e-6}
 PLACEMENTS = [[0, 1, 2, 3, 4, 5], [13, 12, 11, 10, 9, 8], [0, 13, 3, 7, 9, 11], [6, 2, 12, 1, 10, 5],
               [1, 2, 3, 4, 5, 6]]
 
@@ -26,7 +26,7 @@ def _one_gate_circuit(n, qubits, m):
     return circ
 
 
-@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "3xbf16"])
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32", "3xbf16", "3xfp16"])
 def test_single_6q_gate_all_placements(qs, prec):
     n = 14
     rng = Xoshiro256ss(77)
@@ -171,3 +171,21 @@ def test_tensor_pass_bounded_wait_timeout_is_reported(qs):
     assert rel_l2(s2.amplitudes(), oracle.apply_gate(psi0, n, qubits, m)) < GATE_TOL["3xtf32"]
     good.close()
     c.close()
+
+
+@pytest.mark.parametrize("scale", [1e-30, 3e-9, 1.0, 5e3, 1e25])
+def test_3xfp16_scales_any_magnitude(qs, scale):
+    """3xFP16 scales every set of amplitudes (and the gate) by a power of two
+    into FP16's range, so states far outside it -- tiny, large, or with sets
+    of very different magnitudes -- keep the split's ~22-bit accuracy."""
+    n = 14
+    rng = Xoshiro256ss(5)
+    psi0 = random_state(n, 8) * scale
+    psi0[: 1 << 7] *= 1e-6            # sets of very different magnitude within one state
+    for qubits in ([13, 9, 7, 4, 2, 1], [0, 3, 5, 8, 10, 12]):
+        m = random_unitary(6, rng)
+        ref = oracle.apply_gate(psi0, n, qubits, m)
+        got, info = run_plan(_one_gate_circuit(n, qubits, m), "c64", psi0=psi0, k_max=6, precision="3xfp16",
+                             use_tile=False)
+        assert info["per_kind"] == {"tensor": 1}, info
+        assert rel_l2(got, ref) < GATE_TOL["3xfp16"], (scale, qubits, rel_l2(got, ref))
