@@ -106,7 +106,11 @@ typedef struct qs_pauli_sum qs_pauli_sum;
  *                 "operand ready" arrival for the first tile, so the MMA
  *                 issuer's bounded wait runs out (~2 s); the block stops
  *                 its other roles, frees its tensor memory and exits, and
- *                 qs_state_sync reports QS_ERR_TIMEOUT.  0 in normal use.  */
+ *                 qs_state_sync reports QS_ERR_TIMEOUT.  0 in normal use.
+ *   tensor_tiles : 3xFP16 plans: 1 = group consecutive 6-qubit blocks whose
+ *                 qubits (with qubits 0 and 1) fit 12 into tensor tile
+ *                 passes of up to two blocks each (one HBM round trip for
+ *                 both).  0 (default) = one round trip per block.  */
 typedef struct qs_options {
     int k_max;
     int tile_qubits;
@@ -117,7 +121,8 @@ typedef struct qs_options {
     int diag_clusters;
     int fusion_effort;
     int inject_mma_timeout;
-    int reserved[4];
+    int tensor_tiles;
+    int reserved[3];
 } qs_options;
 
 const char* qs_version(void);
@@ -211,7 +216,9 @@ qs_status qs_plan_destroy(qs_plan* p);
 
 /* Number of passes (full HBM round trips) and kernel launches of the plan,
  * and the passes of each kind (array of 8: tile, dense, diagonal, monomial,
- * tensor-core, dense-smem, reserved, reserved; may be NULL). */
+ * tensor-core, dense-smem, wide diagonal, tensor tile; may be NULL).  A
+ * tensor tile pass (3xFP16 plans) applies up to two 6-qubit blocks to
+ * 12-qubit tiles held in shared memory, one HBM round trip for all. */
 qs_status qs_plan_info(const qs_plan* p, int* num_passes, int* num_launches, int* per_kind);
 
 /* Enqueue the plan on the state's stream.  n and dtype must match. */

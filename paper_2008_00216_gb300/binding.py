@@ -22,7 +22,7 @@ QS_C64, QS_C128 = 0, 1
 QS_PREC_FP32, QS_PREC_TF32, QS_PREC_3XTF32, QS_PREC_3XBF16, QS_PREC_3XFP16 = 0, 1, 2, 3, 4
 PRECISIONS = {"fp32": 0, "tf32": 1, "3xtf32": 2, "3xbf16": 3, "3xfp16": 4}
 GATE_KINDS = {0: "dense", 1: "diagonal", 2: "monomial"}
-PASS_KINDS = ["tile", "dense", "diagonal", "monomial", "tensor", "dense_smem", "diagonal_wide", "r7"]
+PASS_KINDS = ["tile", "dense", "diagonal", "monomial", "tensor", "dense_smem", "diagonal_wide", "tensor_tile"]
 
 
 class QsError(RuntimeError):
@@ -35,7 +35,7 @@ class Options(ct.Structure):
     _fields_ = [("k_max", ct.c_int), ("tile_qubits", ct.c_int), ("use_tile", ct.c_int),
                 ("precision", ct.c_int), ("fuse", ct.c_int), ("inject_wait_timeout", ct.c_int),
                 ("diag_clusters", ct.c_int), ("fusion_effort", ct.c_int), ("inject_mma_timeout", ct.c_int),
-                ("reserved", ct.c_int * 4)]
+                ("tensor_tiles", ct.c_int), ("reserved", ct.c_int * 3)]
 
 
 _P = ct.c_void_p
@@ -150,11 +150,12 @@ def _stream_ptr(stream=None) -> int:
 
 def options(k_max: int = 4, tile_qubits: int = 0, use_tile: bool = True, precision="fp32",
             fuse: bool = True, inject_wait_timeout: bool = False, diag_clusters: bool = False,
-            fusion_effort: int = 1, inject_mma_timeout: bool = False) -> Options:
+            fusion_effort: int = 1, inject_mma_timeout: bool = False, tensor_tiles: bool = False) -> Options:
     o = Options()
     _call("qs_options_default", ct.byref(o))
     o.inject_wait_timeout = 1 if inject_wait_timeout else 0
     o.inject_mma_timeout = 1 if inject_mma_timeout else 0
+    o.tensor_tiles = 1 if tensor_tiles else 0
     o.diag_clusters = 1 if diag_clusters else 0
     o.fusion_effort = int(fusion_effort)
     o.k_max = int(k_max)
@@ -361,7 +362,7 @@ class Plan:
         kinds = (ct.c_int * 8)()
         _call("qs_plan_info", self.handle, ct.byref(npass), ct.byref(nl), kinds)
         return {"passes": npass.value, "launches": nl.value,
-                "per_kind": {PASS_KINDS[i]: kinds[i] for i in range(7) if kinds[i]}}
+                "per_kind": {PASS_KINDS[i]: kinds[i] for i in range(8) if kinds[i]}}
 
     def execute(self, state: State):
         state.sync_stream()

@@ -548,7 +548,7 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
     if (i < 0 || i >= (int)p->passes.size()) return fail(QS_ERR_ARG, "pass index out of range");
     const Pass& ps = p->passes[i];
     if (kind) *kind = ps.kind;
-    if (width) *width = ps.kind == PASS_TILE ? ps.L : ps.k;
+    if (width) *width = ps.kind == PASS_TILE ? ps.L : ps.kind == PASS_TTILE ? 12 : ps.k;
     if (num_gates) *num_gates = ps.kind == PASS_TILE ? (int)ps.tgates.size() : ps.members;
     return QS_OK;
 }
@@ -566,6 +566,7 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
         case PASS_GEMM:
             return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream, inject);
         case PASS_DIAG_WIDE: return launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream);
+        case PASS_TTILE: return launch_ttile(s->data, s->n, ps.tt, dm, s->errflag, s->stream);
         case PASS_DENSE_SMEM: return launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);
     }
     return cudaErrorInvalidValue;

@@ -108,7 +108,8 @@ enum PassKind {
     PASS_MONO = 3,       // one permutation-with-phase gate
     PASS_GEMM = 4,       // one dense k in {5,6} gate on tensor cores
     PASS_DENSE_SMEM = 5, // one dense gate via a shared-memory block GEMM (SIMT)
-    PASS_DIAG_WIDE = 6   // a cluster of diagonal gates of any width: per-chunk phase tables
+    PASS_DIAG_WIDE = 6,  // a cluster of diagonal gates of any width: per-chunk phase tables
+    PASS_TTILE = 7       // up to two dense 6-qubit blocks per round trip on tensor cores (3xFP16)
 };
 
 struct DiagCross {
@@ -142,8 +143,19 @@ struct TileGate {
 // scalar factor moved to the pass's scale), applied without multiplies
 constexpr uint8_t kTileMulfree = 8;
 
+// A tensor tile pass (PASS_TTILE): up to kTTileMaxBlocks dense 6-qubit
+// blocks applied to 12-qubit tiles held in shared memory.
+constexpr int kTTileMaxBlocks = 2;
+struct TTileDesc {
+    int nb = 0;                        // blocks, applied in order
+    int s[12] = {0};                   // tile qubits: physical bits ascending, s[0] = 0, s[1] = 1
+    int kbit[kTTileMaxBlocks][6] = {};  // block b: tile bit of local-index bit i (LSB first)
+    uint16_t poscol[12] = {0};         // shared-memory position of tile bit i (linear, bijective)
+};
+
 struct Pass {
     int kind = PASS_DENSE;
+    TTileDesc tt;                      // PASS_TTILE
     // single-gate passes
     int k = 0;
     int qubits[kMaxK] = {0};
@@ -233,6 +245,11 @@ cudaError_t launch_diag_wide(void* psi, int n, qs_dtype dt, const WideDiag& w, c
 // Tensor-core pass for a dense 6-qubit gate on a complex64 state (n >= 11);
 // `err` (device int) is set to 1 if a bounded device wait timed out.
 bool gemm_supported(int n, int k);
+// A tensor tile pass on a complex64 state (3xFP16): dmat holds d.nb 64 x 64
+// float2 matrices, each in the one-block pass's local-index order.
+cudaError_t launch_ttile(void* psi, int n, const TTileDesc& d, const void* dmat, int* err, cudaStream_t st);
+bool ttile_supported(int n);
+
 // inject = 1 (testing only): in block 0 one producer warp withholds its
 // first "operand ready" arrival, so the MMA issuer's bounded wait runs out
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat_f32,

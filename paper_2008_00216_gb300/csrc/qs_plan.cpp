@@ -814,6 +814,186 @@ void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec&
     } else p.kind = PASS_DENSE_SMEM;
 }
 
+// Qubits a pass reads or writes (a superset for wide diagonal passes).
+static uint64_t pass_support(int n, const Pass& p) {
+    uint64_t m = 0;
+    switch (p.kind) {
+        case PASS_TILE:
+            for (const TileGate& g : p.tgates)
+                for (int i = 0; i < g.k; ++i) m |= 1ull << p.pos[g.q[i]];
+            return m;
+        case PASS_DIAG_WIDE: return n >= 64 ? ~0ull : (1ull << n) - 1;
+        case PASS_TTILE:
+            for (int i = 0; i < 12; ++i) m |= 1ull << p.tt.s[i];
+            return m;
+        default:
+            for (int i = 0; i < p.k; ++i) m |= 1ull << p.qubits[i];
+            return m;
+    }
+}
+
+static int gf2_rank3(const uint8_t* v, int cnt) {  // rank of cnt vectors in GF(2)^3
+    uint8_t basis[3] = {0, 0, 0};
+    int rank = 0;
+    for (int i = 0; i < cnt; ++i) {
+        uint8_t x = v[i];
+        for (int b = 2; b >= 0; --b) {
+            if (!((x >> b) & 1)) continue;
+            if (basis[b]) x ^= basis[b];
+            else {
+                basis[b] = x;
+                ++rank;
+                break;
+            }
+        }
+    }
+    return rank;
+}
+
+// Shared-memory positions of the 12 tile bits for a tensor tile pass (see
+// the kernel): bit 0 keeps position bit 0; position bits 1-3 (the bank
+// group of an 8-byte access, with bit 0) are a linear map col3 of tile bits
+// 1..11, searched so that for every block the 4 lowest row bits R_b land in
+// distinct bank groups (rank 3 on R_b \ {0}; rank 3 on R_b when the block
+// targets bit 0, whose rows then share bank groups in pairs); the remaining
+// 8 tile bits also get position bits 4-11 in order, which makes the map
+// bijective.
+static void choose_tile_positions(TTileDesc& d) {
+    int R[kTTileMaxBlocks][4];
+    bool has0[kTTileMaxBlocks];
+    for (int b = 0; b < d.nb; ++b) {
+        uint32_t used = 0;
+        for (int i = 0; i < 6; ++i) used |= 1u << d.kbit[b][i];
+        int c = 0;
+        for (int t = 0; t < 12 && c < 4; ++t)
+            if (!((used >> t) & 1)) R[b][c++] = t;
+        has0[b] = !(used & 1u);
+    }
+    auto score = [&](const uint8_t* col3) {
+        int ok = 0;
+        for (int b = 0; b < d.nb; ++b) {
+            uint8_t v[4];
+            int cnt = 0;
+            for (int i = 0; i < 4; ++i)
+                if (R[b][i] != 0) v[cnt++] = col3[R[b][i]];
+            ok += gf2_rank3(v, cnt) == 3;
+        }
+        return ok;
+    };
+    uint8_t best[12] = {0}, cur[12] = {0};
+    int best_score = -1;
+    uint64_t x = 0x9E3779B97F4A7C15ull;  // fixed-seed generator: the same plan every time
+    for (int trial = 0; trial < 4096 && best_score < d.nb; ++trial) {
+        for (int t = 1; t < 12; ++t) {
+            x ^= x << 13;
+            x ^= x >> 7;
+            x ^= x << 17;
+            cur[t] = (uint8_t)(x & 7);
+        }
+        if (trial == 0)  // first try: the plain identity on tile bits 1..3
+            for (int t = 1; t < 12; ++t) cur[t] = t <= 3 ? (uint8_t)(1 << (t - 1)) : 0;
+        const int sc = score(cur);
+        if (sc > best_score) {
+            best_score = sc;
+            std::copy(cur, cur + 12, best);
+        }
+    }
+    // three tile bits (not 0) whose col3 values are independent
+    int P[3] = {-1, -1, -1};
+    for (int a1 = 1; a1 < 12 && P[0] < 0; ++a1)
+        for (int a2 = a1 + 1; a2 < 12 && P[0] < 0; ++a2)
+            for (int a3 = a2 + 1; a3 < 12 && P[0] < 0; ++a3) {
+                const uint8_t v[3] = {best[a1], best[a2], best[a3]};
+                if (gf2_rank3(v, 3) == 3) {
+                    P[0] = a1;
+                    P[1] = a2;
+                    P[2] = a3;
+                }
+            }
+    if (P[0] < 0) {  // no independent triple: fall back to the identity on bits 1..3
+        for (int t = 1; t < 12; ++t) best[t] = t <= 3 ? (uint8_t)(1 << (t - 1)) : 0;
+        P[0] = 1;
+        P[1] = 2;
+        P[2] = 3;
+    }
+    d.poscol[0] = 1;
+    int rank = 0;
+    for (int t = 1; t < 12; ++t) {
+        const bool inP = t == P[0] || t == P[1] || t == P[2];
+        d.poscol[t] = (uint16_t)((best[t] << 1) | (inP ? 0 : (1u << (4 + rank++))));
+    }
+}
+
+// Group 6-qubit tensor-core passes into tensor tile passes: a pass joins the
+// group when it commutes with every pass it moves ahead of (disjoint
+// qubits) and the group's qubits together with bits 0 and 1 stay within 12;
+// among the candidates the one adding the fewest qubits is taken, up to
+// kTTileMaxBlocks blocks.  Members keep their circuit order.
+static void group_tensor_tiles(int n, std::vector<Pass>& passes) {
+    const int P = (int)passes.size();
+    std::vector<uint64_t> supp(P);
+    for (int i = 0; i < P; ++i) supp[i] = pass_support(n, passes[i]);
+    std::vector<char> placed(P, 0);
+    std::vector<Pass> out;
+    for (int a = 0; a < P; ++a) {
+        if (placed[a]) continue;
+        placed[a] = 1;
+        if (passes[a].kind != PASS_GEMM) {
+            out.push_back(std::move(passes[a]));
+            continue;
+        }
+        std::vector<int> members{a};
+        uint64_t cur = supp[a] | 3ull;
+        while ((int)members.size() < kTTileMaxBlocks) {
+            int best = -1, best_size = 13;
+            // every unplaced pass between the group's start and a candidate
+            // stays after the group, so the candidate must commute with it
+            uint64_t blocked = 0;
+            for (int b = a + 1; b < P; ++b) {
+                if (placed[b]) continue;
+                if (b > members.back() && passes[b].kind == PASS_GEMM && !(supp[b] & blocked)) {
+                    const int sz = __builtin_popcountll(cur | supp[b]);
+                    if (sz <= 12 && sz < best_size) {
+                        best = b;
+                        best_size = sz;
+                    }
+                }
+                blocked |= supp[b];
+            }
+            if (best < 0) break;
+            members.push_back(best);
+            placed[best] = 1;
+            cur |= supp[best];
+        }
+        if (members.size() == 1) {
+            out.push_back(std::move(passes[a]));
+            continue;
+        }
+        Pass t;
+        t.kind = PASS_TTILE;
+        uint64_t S = cur;
+        for (int q = 0; q < n && __builtin_popcountll(S) < 12; ++q) S |= 1ull << q;
+        int tile_of[kMaxQubits];
+        int j = 0;
+        for (int q = 0; q < n; ++q)
+            if ((S >> q) & 1) {
+                tile_of[q] = j;
+                t.tt.s[j++] = q;
+            }
+        t.tt.nb = (int)members.size();
+        t.members = 0;
+        for (int b = 0; b < t.tt.nb; ++b) {
+            const Pass& m = passes[members[b]];
+            for (int i = 0; i < 6; ++i) t.tt.kbit[b][5 - i] = tile_of[m.qubits[i]];
+            t.mats.insert(t.mats.end(), m.mats.begin(), m.mats.end());
+            t.members += m.members;
+        }
+        choose_tile_positions(t.tt);
+        out.push_back(std::move(t));
+    }
+    passes.swap(out);
+}
+
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes) {
     passes.clear();
@@ -876,6 +1056,9 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
         }
         passes.push_back(std::move(p));
     }
+    // 3xFP16 on the tensor cores: several 6-qubit blocks per HBM round trip
+    if (opt.tensor_tiles && dt == QS_C64 && opt.precision == QS_PREC_3XFP16 && ttile_supported(n))
+        group_tensor_tiles(n, passes);
     return QS_OK;
 }
 
