@@ -38,7 +38,7 @@ FALLBACK_HBM_GBS = 6800.0
 # in proportion to the amplitudes, so a launch at n qubits moves
 # bytes_per_amp * 2^n).  Must be cleared when the kernel changes.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "tensor": (537.038848e6 + 476.093184e6) / (1 << 26),   # k_gemm6_grid26_3xtf32.md
+    "tensor": None,
     "tile": None,
     "dense": None,
 }

@@ -225,7 +225,11 @@ qs_status qs_plan_info(const qs_plan* p, int* num_passes, int* num_launches, int
 qs_status qs_plan_execute(qs_state* s, const qs_plan* p);
 
 /* Enqueue passes [first, first+count) only (count < 0: to the end); used to
- * time passes one by one.  Running every range in order equals execute. */
+ * time passes one by one.  Running every range in order equals execute.
+ * Between passes the state may be stored with the index bits of qubit 0 and
+ * one other qubit exchanged (runs of 6-qubit tensor-core passes keep qubit 0
+ * out of their targets that way); each run, and so the plan, ends in the
+ * standard order. */
 qs_status qs_plan_execute_range(qs_state* s, const qs_plan* p, int first, int count);
 
 /* Describe pass i: its kind (index as in qs_plan_info), qubits touched per

@@ -64,6 +64,13 @@ struct Args {
     int sorted[6];      // target bits ascending
     uint64_t ntiles;    // 2^(n-6) / 64
     int inject;         // testing: block 0's first producer warp skips its first arrival
+    int swap_p;         // > 0: writes exchange index bits 0 and swap_p (two of the set bits)
+    int store_mode;     // 0: 8-byte stores (pairs when qubit 0 is a target); 1: qubit 1 a target
+                        // and 0 not, lane pairs exchange; 2: qubits 0 and 1 targets, 32-byte stores
+    int sidx[4];        // slot position bit of set bit a (a < 4) in a producer's raw slice
+    int lidx[5];        // slot position bit of local bit b (b < 5)
+    uint64_t hoff[5];   // amplitude offset of slot position bits 4..8
+    int wsw[5];         // swizzle: slot bit 4 + h set flips slot bits 1..3 by wsw[h]
 };
 
 template <int SPLITS, int KIND>
@@ -75,9 +82,8 @@ struct Layout {
     static constexpr int kG = 0;
     static constexpr int kRaw = 4;                               // gathered tiles in flight
     // one producer warp's slice of a raw slot: 16 sets x 32 local indices,
-    // [32 l][16 sets] float2, or with qubit 0 a target [16 sets][34] float2
-    // (the padding spreads the rows over the banks)
-    static constexpr int kWarpRaw = 16 * 34 * 8;
+    // 32 memory lines of 16 amplitudes (float2)
+    static constexpr int kWarpRaw = 512 * 8;
     static constexpr int kSlot = kProdWarps * kWarpRaw;
     static constexpr int kR = kG + SPLITS_A * kGBytes;
     // FP16: per-set scale exponents of the 4 most recent tiles, and the two
@@ -183,31 +189,56 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int pw = warp - kEpiWarps, q = warp & 3, kh = pw >> 2;
         const int j = lane & 15, c = lane >> 4;  // this lane's TMEM row: set 16q + j, part c
         unsigned char* slice = sm + LY::kR + pw * LY::kWarpRaw;
-        // per-lane constant part of the eight gather addresses and their
-        // destinations (float2 units within the warp's slice)
+        // The warp's slice of a tile (16 sets x 32 local indices = 512
+        // amplitudes) is gathered by 128-byte memory lines: every amplitude
+        // index bit 0..3 is one of the slice's bits (a low set bit or a low
+        // target), so the slice is 32 whole lines.  Copy i: lanes 8u..8u+7
+        // move line 4i + u, 16 bytes each (index bits 1..3 = lane & 7), into
+        // 128 contiguous bytes of the warp's raw slot -- one memory request
+        // per line, whatever the targets.  Slot position of slice element
+        // (set j, local kl): low 4 bits = index bits 0..3, high 5 bits = the
+        // other slice bits (a.sidx, a.lidx give each slice bit's position).
         uint64_t goff[8];
         int gdst[8];
-        if constexpr (Q0T) {
-            // lane -> set 16q + (lane & 15); copy i moves the pair (l, l+1),
-            // l = 32kh + 2p, p = (lane >> 4) + 2i
-            const uint64_t pj = set_base((uint64_t)(16 * q + j), a.sorted);
+        {
+            const int u = lane >> 3, piece = lane & 7;
+            const uint64_t fixed = set_base((uint64_t)(16 * q), a.sorted) + a.off[32 * kh] + (uint64_t)(piece << 1);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
-                const int p = c + 2 * i;
-                goff[i] = pj + a.off[32 * kh + 2 * p];
-                gdst[i] = j * 34 + 2 * p;
-            }
-        } else {
-            // lane -> the set pair 16q + 2sp, +1 of one l = 32kh + kl,
-            // kl = (lane >> 3) + 4i
-            const int sp = lane & 7;
-            const uint64_t pj = set_base((uint64_t)(16 * q + 2 * sp), a.sorted);
+                const int L = 4 * i + u;
+                uint64_t hp = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int kl = (lane >> 3) + 4 * i;
-                goff[i] = pj + a.off[32 * kh + kl];
-                gdst[i] = kl * 16 + 2 * sp;
+                for (int h = 0; h < 5; ++h) hp += ((L >> h) & 1) ? a.hoff[h] : 0ull;
+                goff[i] = fixed + hp;
+                int wl = 0;
+#pragma unroll
+                for (int h = 0; h < 5; ++h) wl ^= ((L >> h) & 1) ? a.wsw[h] : 0;
+                gdst[i] = L * 16 + ((2 * piece) ^ (wl << 1));   // swizzled: see rswz
             }
+        }
+        // slot position of (set j, local kl) = rp_lo[kl & 3] ^ rp_hi[kl >> 2], after
+        // the swizzle rswz(p) = p ^ (XOR of wsw[h] over slot bits 4 + h of p) << 1:
+        // chosen per pass so the 16 sets a warp reads at once fall into distinct
+        // bank groups; bit 0 stays (16-byte pairs stay whole), each line maps
+        // onto itself, and rswz is linear, so parts combine by XOR
+        auto rswz = [&](uint32_t p) {
+            int w = 0;
+#pragma unroll
+            for (int h = 0; h < 5; ++h) w ^= ((p >> (4 + h)) & 1) ? a.wsw[h] : 0;
+            return p ^ ((uint32_t)w << 1);
+        };
+        uint32_t rp_lo[4], rp_hi[8];
+        {
+            uint32_t pj = 0;
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) pj |= (uint32_t)((j >> s2) & 1) << a.sidx[s2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                rp_lo[i] = rswz(pj | ((i & 1) ? 1u << a.lidx[0] : 0u) | ((i & 2) ? 1u << a.lidx[1] : 0u));
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                rp_hi[i] = rswz(((i & 1) ? 1u << a.lidx[2] : 0u) | ((i & 2) ? 1u << a.lidx[3] : 0u) |
+                                ((i & 4) ? 1u << a.lidx[4] : 0u));
         }
         auto issue = [&](uint64_t itx) {
             const uint64_t tt = blockIdx.x + itx * gridDim.x;
@@ -230,19 +261,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int b = (int)(it & 1);
             const float2* rs = reinterpret_cast<const float2*>(slice + (it % LY::kRaw) * LY::kSlot);
             float v[32];  // part c of x[set][32kh + kl], kl = 0..31
-            if constexpr (Q0T) {
 #pragma unroll
-                for (int p = 0; p < 16; ++p) {
-                    const float4 pr = *reinterpret_cast<const float4*>(rs + j * 34 + 2 * p);
-                    v[2 * p] = c ? pr.y : pr.x;
-                    v[2 * p + 1] = c ? pr.w : pr.z;
-                }
-            } else {
-#pragma unroll
-                for (int kl = 0; kl < 32; ++kl) {
-                    const float2 xv = rs[kl * 16 + j];
-                    v[kl] = c ? xv.y : xv.x;
-                }
+            for (int kl = 0; kl < 32; ++kl) {
+                const float2 xv = rs[rp_lo[kl & 3] ^ rp_hi[kl >> 2]];
+                v[kl] = c ? xv.y : xv.x;
             }
             // (the raw slot is warp-private: it was read before the wait below)
             const bool ok = __all_sync(0xffffffffu, mbar_wait(&aempty[b], (uint32_t)(((it >> 1) & 1) ^ 1), err, abort_flag));
@@ -388,7 +410,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unscale = exp2i(-escale[(int)(it & 3) * 64 + 16 * q + j]);
                 unscale_g = exp2i(-eG);
             }
-            float2* dst = psi + set_base(t * kSets + (uint64_t)(16 * q + j), a.sorted);
+            uint64_t sb = set_base(t * kSets + (uint64_t)(16 * q + j), a.sorted);
+            if (!Q0T && a.swap_p > 0) {  // the tile's footprint maps onto itself: in place
+                const uint64_t dbit = (sb ^ (sb >> a.swap_p)) & 1u;
+                sb ^= dbit | (dbit << a.swap_p);
+            }
+            float2* dst = psi + sb;
             const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kTmemD + b * kN);
 #pragma unroll
             for (int ch = 0; ch < 4; ++ch) {
@@ -419,11 +446,42 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 if constexpr (Q0T) {
-                    // pairs (r, r+1) are adjacent amplitudes
+                    if (a.store_mode == 2) {
+                        // qubits 0 and 1 both targets: outputs r..r+3 are 32
+                        // contiguous bytes, one 256-bit store each (full sectors)
+#pragma unroll
+                        for (int rr = 0; rr < 8; rr += 4) {
+                            const uint64_t o = c ? a.off[16 * ch + 8 + rr] : a.off[16 * ch + rr];
+                            asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(dst + o),
+                                         "f"(y[rr].x), "f"(y[rr].y), "f"(y[rr + 1].x), "f"(y[rr + 1].y), "f"(y[rr + 2].x),
+                                         "f"(y[rr + 2].y), "f"(y[rr + 3].x), "f"(y[rr + 3].y)
+                                         : "memory");
+                        }
+                    } else {
+                        // pairs (r, r+1) are adjacent amplitudes
+#pragma unroll
+                        for (int rr = 0; rr < 8; rr += 2) {
+                            const uint64_t o = c ? a.off[16 * ch + 8 + rr] : a.off[16 * ch + rr];
+                            *reinterpret_cast<float4*>(dst + o) = make_float4(y[rr].x, y[rr].y, y[rr + 1].x, y[rr + 1].y);
+                        }
+                    }
+                } else if (a.store_mode == 1) {
+                    // qubit 1 a target, qubit 0 not: the 32 bytes of sets (s, s+1) x
+                    // outputs (r, r+1) sit in lanes j, j+1; one exchange lets each
+                    // lane store 16 bytes, so every instruction writes full sectors
+                    const bool odd = (j & 1) != 0;
 #pragma unroll
                     for (int rr = 0; rr < 8; rr += 2) {
-                        const uint64_t o = c ? a.off[16 * ch + 8 + rr] : a.off[16 * ch + rr];
-                        *reinterpret_cast<float4*>(dst + o) = make_float4(y[rr].x, y[rr].y, y[rr + 1].x, y[rr + 1].y);
+                        const float2 send = odd ? y[rr] : y[rr + 1];
+                        float2 got;
+                        got.x = __shfl_xor_sync(0xffffffffu, send.x, 1);
+                        got.y = __shfl_xor_sync(0xffffffffu, send.y, 1);
+                        const int r = 16 * ch + 8 * c + rr;
+                        // one store instruction for both lanes of the pair
+                        float2* const p = odd ? dst - 1 + a.off[r + 1] : dst + a.off[r];
+                        const float4 val = odd ? make_float4(got.x, got.y, y[rr + 1].x, y[rr + 1].y)
+                                               : make_float4(y[rr].x, y[rr].y, got.x, got.y);
+                        *reinterpret_cast<float4*>(p) = val;
                     }
                 } else {
 #pragma unroll
@@ -466,7 +524,7 @@ static cudaError_t run(float2* psi, const float2* U, const Args& a, int* err, cu
 bool gemm_supported(int n, int k) { return k == 6 && n >= 12; }
 
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat, int precision, int* err,
-                        cudaStream_t st, int inject) {
+                        cudaStream_t st, int inject, int swap_p) {
     if (!gemm_supported(n, k)) return cudaErrorInvalidValue;
     for (int i = 0; i + 1 < 6; ++i)  // the planner hands over descending qubit lists
         if (qubits[i] <= qubits[i + 1]) return cudaErrorInvalidValue;
@@ -481,6 +539,73 @@ cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* 
     std::sort(a.sorted, a.sorted + 6);
     a.ntiles = (1ull << (n - 6)) / tc::kSets;
     a.inject = inject ? 1 : 0;
+    a.swap_p = -1;
+    a.store_mode = 0;
+    if (swap_p >= 0) {  // bit 0 and swap_p must be among the set bits 0..3 (the 4 lowest non-targets)
+        uint64_t tmask = 0;
+        for (int i = 0; i < 6; ++i) tmask |= 1ull << qubits[i];
+        int rank = 0, found = -1;
+        for (int b = 0; b < n && rank < 4; ++b) {
+            if ((tmask >> b) & 1) continue;
+            if (b == swap_p) found = rank;
+            ++rank;
+        }
+        if (tmask & 1 || found < 1) return cudaErrorInvalidValue;
+        a.swap_p = swap_p;
+    }
+    {
+        uint64_t tmask = 0;
+        for (int i = 0; i < 6; ++i) tmask |= 1ull << qubits[i];
+        if ((tmask & 3) == 3 && ((uintptr_t)psi & 31) == 0) a.store_mode = 2;
+        else if ((tmask & 3) == 2 && a.swap_p < 0) a.store_mode = 1;
+        // a producer's slice: set bits 0..3 (the 4 lowest non-targets) and
+        // local bits 0..4 (the 5 lowest targets); index bits 0..3 keep their
+        // place, the other 5 slice bits take slot position bits 4..8
+        int np[4], cnt = 0;
+        for (int b = 0; b < n && cnt < 4; ++b)
+            if (!((tmask >> b) & 1)) np[cnt++] = b;
+        int hi = 4;
+        for (int s2 = 0; s2 < 4; ++s2) {
+            if (np[s2] < 4) a.sidx[s2] = np[s2];
+            else {
+                a.sidx[s2] = hi;
+                a.hoff[hi - 4] = 1ull << np[s2];
+                ++hi;
+            }
+        }
+        for (int l = 0; l < 5; ++l) {
+            if (a.sorted[l] < 4) a.lidx[l] = a.sorted[l];
+            else {
+                a.lidx[l] = hi;
+                a.hoff[hi - 4] = 1ull << a.sorted[l];
+                ++hi;
+            }
+        }
+        if (hi != 9) return cudaErrorInvalidValue;   // cannot happen: bits 0..3 are slice bits
+        // swizzle: give each set bit held in a high slot bit a flip of bits 1..3
+        // outside the span of the set bits already placed (bank group = slot
+        // bits 0..3), so the 16 sets of a warp's read spread over the banks
+        for (int h = 0; h < 5; ++h) a.wsw[h] = 0;
+        uint32_t span[16] = {0};
+        int nspan = 1;  // span of the placed bank-group vectors (starts with 0)
+        auto add = [&](uint32_t v) {
+            bool in = false;
+            for (int i = 0; i < nspan; ++i) in |= span[i] == v;
+            if (in) return false;
+            for (int i = 0, m = nspan; i < m; ++i) span[nspan++] = span[i] ^ v;
+            return true;
+        };
+        for (int s2 = 0; s2 < 4; ++s2)
+            if (a.sidx[s2] < 4) add(1u << a.sidx[s2]);
+        for (int s2 = 0; s2 < 4; ++s2) {
+            if (a.sidx[s2] < 4) continue;
+            for (int w = 1; w < 8; ++w)
+                if (add((uint32_t)w << 1)) {
+                    a.wsw[a.sidx[s2] - 4] = w;
+                    break;
+                }
+        }
+    }
     float2* p = (float2*)psi;
     const float2* U = (const float2*)dmat;
     switch (precision) {

@@ -564,7 +564,7 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
         case PASS_DIAG: return launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_MONO: return launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_GEMM:
-            return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream, inject);
+            return launch_gemm(s->data, s->n, ps.k, ps.qubits, dm, precision, s->errflag, s->stream, inject, ps.swap_p);
         case PASS_DIAG_WIDE: return launch_diag_wide(s->data, s->n, s->dt, ps.wide, dm, s->stream);
         case PASS_TTILE: return launch_ttile(s->data, s->n, ps.tt, dm, s->errflag, s->stream);
         case PASS_DENSE_SMEM: return launch_dense_smem(s->data, s->n, s->dt, ps.k, ps.qubits, dm, s->stream);

@@ -166,6 +166,9 @@ struct Pass {
     std::vector<TileGate> tgates;
     WideDiag wide;                  // PASS_DIAG_WIDE
     int members = 1;                // gates applied by a single-block pass
+    // PASS_GEMM: physical bit exchanged with bit 0 in the pass's writes (-1:
+    // none); the state after the pass is stored with those two bits swapped
+    int swap_p = -1;
     // tile passes: product of the scalars factored out of kTileMulfree gates,
     // applied at write-back.  mode 1: mag * exp(i pi s / 4); mode 2: scale_c
     int scale_mode = 0;
@@ -252,8 +255,10 @@ bool ttile_supported(int n);
 
 // inject = 1 (testing only): in block 0 one producer warp withholds its
 // first "operand ready" arrival, so the MMA issuer's bounded wait runs out
+// swap_p >= 0: the pass writes each amplitude with index bits 0 and swap_p
+// exchanged (both must be among the pass's four lowest non-target bits)
 cudaError_t launch_gemm(void* psi, int n, int k, const int* qubits, const void* dmat_f32,
-                        int precision, int* err, cudaStream_t st, int inject = 0);
+                        int precision, int* err, cudaStream_t st, int inject = 0, int swap_p = -1);
 
 cudaError_t launch_init_basis(void* psi, int n, qs_dtype dt, uint64_t index, cudaStream_t st);
 cudaError_t launch_init_uniform(void* psi, int n, qs_dtype dt, cudaStream_t st);

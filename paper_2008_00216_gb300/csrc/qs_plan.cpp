@@ -994,6 +994,103 @@ static void group_tensor_tiles(int n, std::vector<Pass>& passes) {
     passes.swap(out);
 }
 
+// Qubit 0 out of the targets of 6-qubit tensor-core passes: a reordering of
+// index bits, the GPU form of the paper's bit-permuting recursive transform
+// (Section 5.1), folded into passes that run anyway.  A pass whose targets
+// leave bit 0 free may write its tile with bit 0 exchanged with one of its
+// next three lowest non-target bits (the tile maps onto itself and the
+// stores stay coalesced), so the state is then stored with two qubits'
+// index bits exchanged.  Over each run of consecutive 6-qubit passes a
+// dynamic program over the states {standard order} and {qubits 0 and a
+// exchanged} picks the exchanges that leave the fewest passes with bit 0
+// among their physical targets (those passes gather 16-byte pairs along
+// bit 0, the slower form), starting and ending the run in standard order.
+// Each pass's qubits become physical bits (its matrix reordered to match).
+static void place_bit0_run(int n, std::vector<Pass>& passes, size_t i0, size_t i1) {
+    const int K = (int)(i1 - i0), S = n + 1;   // state index s + 1; s = -1: standard order
+    auto phys = [](int s, int x) { return s < 0 ? x : x == 0 ? s : x == s ? 0 : x; };
+    std::vector<uint64_t> T(K, 0);
+    for (int k = 0; k < K; ++k)
+        for (int i = 0; i < passes[i0 + k].k; ++i) T[k] |= 1ull << passes[i0 + k].qubits[i];
+    auto ptargets = [&](int k, int s) {
+        uint64_t m = 0;
+        for (int x = 0; x < n; ++x)
+            if ((T[k] >> x) & 1) m |= 1ull << phys(s, x);
+        return m;
+    };
+    auto candidates = [&](uint64_t pt, int* c) {  // non-target bits of rank 1..3
+        int rank = 0, cnt = 0;
+        for (int b = 0; b < n && rank <= 3; ++b) {
+            if ((pt >> b) & 1) continue;
+            if (rank >= 1) c[cnt++] = b;
+            ++rank;
+        }
+        return cnt;
+    };
+    const int INF = 1 << 28;
+    std::vector<int> cost((size_t)(K + 1) * S, INF), choice((size_t)K * S, -2);  // -2 keep, -1 back, else new a
+    cost[(size_t)K * S] = 0;
+    for (int k = K - 1; k >= 0; --k)
+        for (int idx = 0; idx < S; ++idx) {
+            const int s = idx - 1;
+            if (s == 0) continue;
+            const uint64_t pt = ptargets(k, s);
+            const int q0t = (int)(pt & 1);
+            int best = q0t + cost[(size_t)(k + 1) * S + idx], bc = -2;
+            if (!q0t) {
+                int c[3];
+                const int cnt = candidates(pt, c);
+                for (int i = 0; i < cnt; ++i) {
+                    if (s < 0) {
+                        const int v = cost[(size_t)(k + 1) * S + c[i] + 1];
+                        if (v < best) {
+                            best = v;
+                            bc = c[i];
+                        }
+                    } else if (c[i] == s) {
+                        const int v = cost[(size_t)(k + 1) * S];
+                        if (v < best) {
+                            best = v;
+                            bc = -1;
+                        }
+                    }
+                }
+            }
+            cost[(size_t)k * S + idx] = best;
+            choice[(size_t)k * S + idx] = bc;
+        }
+    int s = -1;
+    for (int k = 0; k < K; ++k) {
+        Pass& p = passes[i0 + k];
+        const int bc = choice[(size_t)k * S + s + 1];
+        for (int i = 0; i < p.k; ++i) p.qubits[i] = phys(s, p.qubits[i]);
+        sort_qubits_descending(p);
+        if (bc == -2) {
+            p.swap_p = -1;
+        } else if (bc == -1) {
+            p.swap_p = s;
+            s = -1;
+        } else {
+            p.swap_p = bc;
+            s = bc;
+        }
+    }
+}
+
+static void place_bit0(int n, std::vector<Pass>& passes) {
+    size_t i = 0;
+    while (i < passes.size()) {
+        if (passes[i].kind != PASS_GEMM) {
+            ++i;
+            continue;
+        }
+        size_t j = i;
+        while (j < passes.size() && passes[j].kind == PASS_GEMM) ++j;
+        if (j - i >= 2) place_bit0_run(n, passes, i, j);
+        i = j;
+    }
+}
+
 qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes) {
     passes.clear();
@@ -1059,6 +1156,7 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
     // 3xFP16 on the tensor cores: several 6-qubit blocks per HBM round trip
     if (opt.tensor_tiles && dt == QS_C64 && opt.precision == QS_PREC_3XFP16 && ttile_supported(n))
         group_tensor_tiles(n, passes);
+    place_bit0(n, passes);
     return QS_OK;
 }
 

@@ -189,3 +189,49 @@ def test_3xfp16_scales_any_magnitude(qs, scale):
                              use_tile=False)
         assert info["per_kind"] == {"tensor": 1}, info
         assert rel_l2(got, ref) < GATE_TOL["3xfp16"], (scale, qubits, rel_l2(got, ref))
+
+
+@pytest.mark.parametrize("prec", ["3xtf32", "3xfp16"])
+def test_qubit0_kept_out_of_targets(qs, prec):
+    """Runs of 6-qubit passes where several blocks touch qubit 0: the planner
+    exchanges qubit 0's index bit with another qubit's inside earlier passes
+    (and back), so the state between passes is stored permuted; the plan's
+    result is in standard order and matches the oracle."""
+    n = 16
+    rng = Xoshiro256ss(17)
+    circ = C.Circuit(n)
+    for qs_ in ([15, 13, 9, 7, 5, 3], [0, 2, 4, 6, 8, 10], [1, 3, 11, 12, 14, 15], [0, 1, 5, 9, 13, 15],
+                [2, 6, 7, 8, 12, 14], [0, 3, 4, 10, 11, 12]):
+        circ.append(qs_, random_unitary(6, rng))
+    psi0 = random_state(n, 23)
+    ref = oracle.simulate(n, circ.gates, psi0)
+    got, info = run_plan(circ, "c64", psi0=psi0, k_max=6, precision=prec, fuse=False, use_tile=False)
+    assert info["per_kind"] == {"tensor": 6}, info
+    assert rel_l2(got, ref) < 6 * GATE_TOL[prec], rel_l2(got, ref)
+
+
+def test_low_qubit_store_forms_and_alignment(qs):
+    """The pass's store forms for blocks on qubit 1 (lane pairs exchange
+    values) and on qubits 0 and 1 (32-byte stores, used only when the state
+    is 32-byte aligned): a torch state and a state wrapped 16 bytes into a
+    larger buffer (16-byte aligned only), both against the oracle."""
+    import torch
+    n = 14
+    rng = Xoshiro256ss(29)
+    psi0 = random_state(n, 31)
+    for qubits in ([1, 4, 6, 9, 11, 13], [0, 1, 5, 8, 10, 12], [1, 2, 3, 7, 8, 13], [0, 1, 2, 3, 12, 13]):
+        m = random_unitary(6, rng)
+        ref = oracle.apply_gate(psi0, n, qubits, m)
+        circ = _one_gate_circuit(n, qubits, m)
+        for offset in (0, 2):   # amplitudes (8 bytes each) into the buffer
+            buf = torch.zeros((1 << n) + 4, dtype=torch.complex64, device="cuda")
+            t = buf[offset:offset + (1 << n)]
+            t.copy_(torch.from_numpy(psi0).to(torch.complex64))
+            s = B.State(n, "c64", tensor=t, init=None)
+            c = B.circuit_from(circ)
+            p = B.Plan(c, "c64", k_max=6, precision="3xtf32", use_tile=False)
+            p.execute(s)
+            got = s.amplitudes()
+            assert rel_l2(got, ref) < GATE_TOL["3xtf32"], (qubits, offset, rel_l2(got, ref))
+            assert buf[:offset].abs().sum().item() == 0 and buf[offset + (1 << n):].abs().sum().item() == 0
+            p.close(); c.close(); s.close()
