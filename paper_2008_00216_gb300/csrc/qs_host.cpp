@@ -477,7 +477,10 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     }
     st = build_passes(c->n, dt, blocks, opt, p->passes);
     if (st != QS_OK) return st;
-    for (Pass& ps : p->passes) factor_tile_scalars(ps);
+    for (Pass& ps : p->passes) {
+        factor_tile_scalars(ps);
+        if (ps.kind == PASS_TILE && !build_rtile_program(dt, ps, ps.rt)) ps.rt.nops = 0;
+    }
     // upload every pass's matrices, converted to the state's precision
     size_t total = 0;
     for (Pass& ps : p->passes) {
@@ -559,7 +562,9 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
 // precision (the passes that take their matrix as a kernel argument ignore it).
 static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int precision, int inject = 0) {
     switch (ps.kind) {
-        case PASS_TILE: return launch_tile(s->data, s->n, s->dt, ps, dm, s->stream);
+        case PASS_TILE:
+            return ps.rt.nops > 0 ? launch_rtile(s->data, s->n, s->dt, ps, dm, s->stream)
+                                  : launch_tile(s->data, s->n, s->dt, ps, dm, s->stream);
         case PASS_DENSE: return launch_dense(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_DIAG: return launch_diag(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);
         case PASS_MONO: return launch_mono(s->data, s->n, s->dt, ps.k, ps.qubits, ps.mats.data(), s->stream);

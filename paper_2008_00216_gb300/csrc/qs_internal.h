@@ -143,6 +143,40 @@ struct TileGate {
 // scalar factor moved to the pass's scale), applied without multiplies
 constexpr uint8_t kTileMulfree = 8;
 
+// Register tile program of a tile pass (k_rtile): the tile's amplitudes live
+// in registers, 2^RB per thread of a 256-thread block (L = RB + 8 tile bits:
+// 5 on the lanes, RB on a thread's registers, 3 on the warps).  A layout
+// says which tile bit each lane, register and warp bit holds; ops run in
+// the current layout and LAYOUT ops move the tile between layouts through a
+// swizzled shared-memory transpose.
+constexpr int kRTMaxLayouts = 12, kRTMaxOps = 160;
+enum RTOpType : uint8_t {
+    RT_GATE = 0,    // k-qubit gate on register bits 0..k-1 (local bit i = register bit i)
+    RT_GATE1 = 1,   // one-qubit gate on register bit `arg`
+    RT_LANE1 = 2,   // one-qubit gate on lane bit `arg` (warp shuffles)
+    RT_DIAG = 3,    // diagonal gate on tile bits q[] (Kronecker order), any layout
+    RT_LAYOUT = 4   // move to layout `arg`
+};
+struct RTLayout {
+    uint8_t lane[5];
+    uint8_t reg[4];
+    uint8_t warp[3];
+};
+struct RTOp {
+    uint8_t type, k, arg, mulfree;
+    uint8_t q[6];
+    uint32_t mat;   // element offset of the gate's matrix in the pass buffer
+};
+struct RTProgram {
+    int nops = 0, nlay = 0;
+    int load_lay = 0, store_lay = 0;
+    RTLayout lay[kRTMaxLayouts];
+    RTOp ops[kRTMaxOps];
+    uint16_t poscol[12] = {0};   // shared-memory position of tile bit i (linear, bijective)
+};
+// The register tile size of a dtype: 12 tile bits for complex64, 11 for complex128.
+int rtile_bits(qs_dtype dt);
+
 // A tensor tile pass (PASS_TTILE): up to kTTileMaxBlocks dense 6-qubit
 // blocks applied to 12-qubit tiles held in shared memory.
 constexpr int kTTileMaxBlocks = 2;
@@ -169,6 +203,7 @@ struct Pass {
     // PASS_GEMM: physical bit exchanged with bit 0 in the pass's writes (-1:
     // none); the state after the pass is stored with those two bits swapped
     int swap_p = -1;
+    RTProgram rt;                   // PASS_TILE: register tile program (rt.nops > 0: k_rtile)
     // tile passes: product of the scalars factored out of kTileMulfree gates,
     // applied at write-back.  mode 1: mag * exp(i pi s / 4); mode 2: scale_c
     int scale_mode = 0;
@@ -179,6 +214,11 @@ struct Pass {
     std::vector<double> mats;       // concatenated interleaved matrices
     size_t dev_offset = 0;          // element offset in the plan's device buffer
 };
+
+// Compile a tile pass into a register tile program (false: the pass keeps
+// the shared-memory tile kernel).
+bool build_rtile_program(qs_dtype dt, const Pass& p, RTProgram& prog);
+cudaError_t launch_rtile(void* psi, int n, qs_dtype dt, const Pass& ps, const void* dmats, cudaStream_t st);
 
 }  // namespace qsgb
 

@@ -994,6 +994,266 @@ static void group_tensor_tiles(int n, std::vector<Pass>& passes) {
     passes.swap(out);
 }
 
+// Register tile program of a tile pass (see the kernel): lanes hold tile
+// bits 0..4 when the tile is loaded and stored; a gate whose qubits are not
+// where its op needs them gets a new layout first (its qubits on register
+// bits 0..k-1, the other register bits filled with the tile bits used
+// soonest by later gates).  The shared-memory positions of the transposes
+// are a linear map of the tile bits whose bank-group part is searched so that
+// every layout's lane bits hit all bank groups.
+bool build_rtile_program(qs_dtype dt, const Pass& p, RTProgram& prog) {
+    const int L = rtile_bits(dt), RB = L - 8;
+    if (p.kind != PASS_TILE || p.L != L) return false;
+    for (const TileGate& g : p.tgates)
+        if (g.kind != QS_GATE_DIAGONAL && g.k > RB) return false;
+    prog = RTProgram{};
+    const int G = (int)p.tgates.size();
+    auto next_use = [&](int from, int bit) {
+        for (int i = from; i < G; ++i) {
+            const TileGate& g = p.tgates[i];
+            if (g.kind == QS_GATE_DIAGONAL) continue;
+            for (int j = 0; j < g.k; ++j)
+                if (g.q[j] == bit) return i;
+        }
+        return G + 1;
+    };
+    struct Lay {
+        int lane[5], reg[4], warp[3];
+    };
+    std::vector<Lay> lays;
+    auto finish = [&](Lay& l) {  // warps: the tile bits on neither lanes nor registers
+        uint32_t used = 0;
+        for (int i = 0; i < 5; ++i) used |= 1u << l.lane[i];
+        for (int i = 0; i < RB; ++i) used |= 1u << l.reg[i];
+        int w = 0;
+        for (int b = 0; b < L; ++b)
+            if (!((used >> b) & 1)) {
+                if (w >= 3) return false;
+                l.warp[w++] = b;
+            }
+        for (int i = RB; i < 4; ++i) l.reg[i] = 0;
+        return w == 3;
+    };
+    auto index_of = [&](const Lay& l) {
+        for (size_t i = 0; i < lays.size(); ++i) {
+            bool eq = true;
+            for (int j = 0; j < 5; ++j) eq &= lays[i].lane[j] == l.lane[j];
+            for (int j = 0; j < RB; ++j) eq &= lays[i].reg[j] == l.reg[j];
+            if (eq) return (int)i;
+        }
+        if ((int)lays.size() >= kRTMaxLayouts) return -1;
+        lays.push_back(l);
+        return (int)lays.size() - 1;
+    };
+    auto find = [](const int* arr, int cnt, int v) {
+        for (int i = 0; i < cnt; ++i)
+            if (arr[i] == v) return i;
+        return -1;
+    };
+    std::vector<RTOp> ops;
+    // initial layout: lanes 0..4, registers the RB high bits used soonest
+    Lay cur{};
+    for (int i = 0; i < 5; ++i) cur.lane[i] = i;
+    {
+        std::vector<int> high;
+        for (int b = 5; b < L; ++b) high.push_back(b);
+        std::stable_sort(high.begin(), high.end(), [&](int x, int y) { return next_use(0, x) < next_use(0, y); });
+        for (int i = 0; i < RB; ++i) cur.reg[i] = high[i];
+        if (!finish(cur)) return false;
+    }
+    int curi = index_of(cur);
+    prog.load_lay = curi;
+    auto move_to = [&](Lay& nl) {
+        if (!finish(nl)) return false;
+        const int idx = index_of(nl);
+        if (idx < 0) return false;
+        RTOp op{};
+        op.type = RT_LAYOUT;
+        op.arg = (uint8_t)idx;
+        ops.push_back(op);
+        cur = nl;
+        curi = idx;
+        return true;
+    };
+    for (int gi = 0; gi < G; ++gi) {
+        const TileGate& g = p.tgates[gi];
+        RTOp op{};
+        op.k = g.k;
+        op.mat = g.mat;
+        for (int i = 0; i < g.k; ++i) op.q[i] = g.q[i];
+        op.mulfree = g.kind == kTileMulfree ? 1 : 0;
+        if (g.kind == QS_GATE_DIAGONAL) {
+            op.type = RT_DIAG;
+            ops.push_back(op);
+            continue;
+        }
+        if (g.k == 1) {
+            const int q = g.q[0];
+            int r = find(cur.reg, RB, q);
+            if (r >= 0) {
+                op.type = RT_GATE1;
+                op.arg = (uint8_t)r;
+                ops.push_back(op);
+                continue;
+            }
+            const int ln = find(cur.lane, 5, q);
+            if (ln >= 0) {
+                op.type = RT_LANE1;
+                op.arg = (uint8_t)ln;
+                ops.push_back(op);
+                continue;
+            }
+            // a warp bit: it replaces the register bit used latest
+            int worst = 0;
+            for (int i = 1; i < RB; ++i)
+                if (next_use(gi + 1, cur.reg[i]) > next_use(gi + 1, cur.reg[worst])) worst = i;
+            Lay nl = cur;
+            nl.reg[worst] = q;
+            if (!move_to(nl)) return false;
+            op.type = RT_GATE1;
+            op.arg = (uint8_t)worst;
+            ops.push_back(op);
+            continue;
+        }
+        bool in_place = true;  // local bit i = q[k-1-i] on register bit i
+        for (int i = 0; i < g.k; ++i) in_place &= cur.reg[i] == g.q[g.k - 1 - i];
+        if (!in_place) {
+            Lay nl{};
+            uint32_t taken = 0;
+            for (int i = 0; i < g.k; ++i) {
+                nl.reg[i] = g.q[g.k - 1 - i];
+                taken |= 1u << nl.reg[i];
+            }
+            // fill the other register bits: current registers, then warps, used soonest first
+            std::vector<int> cand;
+            for (int i = 0; i < RB; ++i)
+                if (!((taken >> cur.reg[i]) & 1)) cand.push_back(cur.reg[i]);
+            std::stable_sort(cand.begin(), cand.end(), [&](int x, int y) { return next_use(gi + 1, x) < next_use(gi + 1, y); });
+            std::vector<int> cw;
+            for (int i = 0; i < 3; ++i)
+                if (!((taken >> cur.warp[i]) & 1)) cw.push_back(cur.warp[i]);
+            std::stable_sort(cw.begin(), cw.end(), [&](int x, int y) { return next_use(gi + 1, x) < next_use(gi + 1, y); });
+            cand.insert(cand.end(), cw.begin(), cw.end());
+            int fill = g.k;
+            for (int b : cand)
+                if (fill < RB) {
+                    nl.reg[fill++] = b;
+                    taken |= 1u << b;
+                }
+            if (fill < RB) return false;
+            // lanes: the current lanes, a lane bit now in the registers replaced
+            // by the lowest tile bit that is free
+            for (int i = 0; i < 5; ++i) {
+                int b = cur.lane[i];
+                if ((taken >> b) & 1) {
+                    b = -1;
+                    for (int c = 0; c < L && b < 0; ++c) {
+                        bool on_lane = false;
+                        for (int j = 0; j < 5; ++j) on_lane |= (j < i ? nl.lane[j] : cur.lane[j]) == c;
+                        if (!((taken >> c) & 1) && !on_lane) b = c;
+                    }
+                    if (b < 0) return false;
+                }
+                nl.lane[i] = b;
+                taken |= 1u << b;
+            }
+            if (!move_to(nl)) return false;
+        }
+        op.type = RT_GATE;
+        ops.push_back(op);
+    }
+    // the store layout: lanes back on tile bits 0..4
+    bool natural = true;
+    for (int i = 0; i < 5; ++i) natural &= cur.lane[i] == i;
+    if (!natural) {
+        Lay nl{};
+        uint32_t taken = 0x1Fu;
+        for (int i = 0; i < 5; ++i) nl.lane[i] = i;
+        int fill = 0;
+        for (int i = 0; i < RB; ++i)
+            if (cur.reg[i] >= 5) {
+                nl.reg[fill++] = cur.reg[i];
+                taken |= 1u << cur.reg[i];
+            }
+        for (int b = 5; b < L && fill < RB; ++b)
+            if (!((taken >> b) & 1)) {
+                nl.reg[fill++] = b;
+                taken |= 1u << b;
+            }
+        if (!move_to(nl)) return false;
+    }
+    prog.store_lay = curi;
+    if ((int)ops.size() > kRTMaxOps) return false;
+    prog.nops = (int)ops.size();
+    for (int i = 0; i < prog.nops; ++i) prog.ops[i] = ops[i];
+    prog.nlay = (int)lays.size();
+    for (int i = 0; i < prog.nlay; ++i) {
+        for (int j = 0; j < 5; ++j) prog.lay[i].lane[j] = (uint8_t)lays[i].lane[j];
+        for (int j = 0; j < 4; ++j) prog.lay[i].reg[j] = (uint8_t)lays[i].reg[j];
+        for (int j = 0; j < 3; ++j) prog.lay[i].warp[j] = (uint8_t)lays[i].warp[j];
+    }
+    // positions: bank-group bits (nb = 4 for 8-byte, 3 for 16-byte elements)
+    // a linear map of the tile bits with full rank on every layout's lanes
+    const int nb = dt == QS_C64 ? 4 : 3;
+    auto rank_of = [&](const uint8_t* col, const int* bits, int cnt) {
+        uint8_t basis[4] = {0, 0, 0, 0};
+        int rank = 0;
+        for (int i = 0; i < cnt; ++i) {
+            uint8_t x = col[bits[i]];
+            for (int b = nb - 1; b >= 0 && x; --b) {
+                if (!((x >> b) & 1)) continue;
+                if (basis[b]) x ^= basis[b];
+                else {
+                    basis[b] = x;
+                    ++rank;
+                    x = 0;
+                }
+            }
+        }
+        return rank;
+    };
+    uint8_t best[12] = {0}, col[12] = {0};
+    int best_ok = -1;
+    uint64_t x = 0x2545F4914F6CDD1Dull;  // fixed-seed generator: the same plan every time
+    for (int trial = 0; trial < 4096 && best_ok < (int)lays.size(); ++trial) {
+        for (int b = 0; b < L; ++b) {
+            if (trial == 0) col[b] = b < nb ? (uint8_t)(1u << b) : 0;   // first try: the identity on bits 0..nb-1
+            else {
+                x ^= x << 13;
+                x ^= x >> 7;
+                x ^= x << 17;
+                col[b] = (uint8_t)(x & ((1u << nb) - 1));
+            }
+        }
+        int ok = 0;
+        for (const Lay& l : lays) ok += rank_of(col, l.lane, 5) == nb;
+        if (ok > best_ok) {
+            best_ok = ok;
+            std::copy(col, col + L, best);
+        }
+    }
+    int P[4] = {-1, -1, -1, -1};  // nb tile bits on which the map is invertible
+    {
+        std::vector<int> chosen;
+        for (int b = 0; b < L && (int)chosen.size() < nb; ++b) {
+            chosen.push_back(b);
+            if (rank_of(best, chosen.data(), (int)chosen.size()) < (int)chosen.size()) chosen.pop_back();
+        }
+        if ((int)chosen.size() < nb) {  // no full rank: the identity on bits 0..nb-1
+            for (int b = 0; b < L; ++b) best[b] = b < nb ? (uint8_t)(1u << b) : 0;
+            chosen.clear();
+            for (int b = 0; b < nb; ++b) chosen.push_back(b);
+        }
+        for (int i = 0; i < nb; ++i) P[i] = chosen[i];
+    }
+    int hi = 0;
+    for (int b = 0; b < L; ++b) {
+        const bool inP = find(P, nb, b) >= 0;
+        prog.poscol[b] = (uint16_t)(best[b] | (inP ? 0u : 1u << (nb + hi++)));
+    }
+    return true;
+}
+
 // Qubit 0 out of the targets of 6-qubit tensor-core passes: a reordering of
 // index bits, the GPU form of the paper's bit-permuting recursive transform
 // (Section 5.1), folded into passes that run anyway.  A pass whose targets

@@ -1,0 +1,336 @@
+// Register tile pass: every gate of a tile pass applied to a 2^L-amplitude
+// tile held in registers (the GPU form of the paper's cache blocking,
+// Section 5.1: all gates whose qubits lie in the tile before write-back).
+//
+// A 256-thread block holds the tile as 2^RB amplitudes per thread, L = RB + 8
+// (complex64: RB = 4, L = 12; complex128: RB = 3, L = 11).  A layout gives
+// the tile bit that each lane bit (5), register bit (RB) and warp bit (3)
+// stands for.  The tile is loaded and stored in a layout whose lanes are
+// tile bits 0..4 (the lowest physical qubits: coalesced rows).  Ops, from a
+// program compiled on the host for the pass:
+//   RT_GATE   a k-qubit gate (k = 2..RB) whose qubits are register bits
+//             0..k-1: each thread applies it to its own 2^(RB-k) sets
+//   RT_GATE1  a one-qubit gate on register bit r: within the thread
+//   RT_LANE1  a one-qubit gate on lane bit b: the partner amplitude comes
+//             from lane ^ (1 << b) with __shfl_xor_sync
+//   RT_DIAG   a diagonal gate on any tile bits: each amplitude's phase from
+//             its own index, in any layout (no data movement)
+//   RT_LAYOUT the tile moves to another layout through shared memory, in a
+//             swizzled order chosen per pass so that every layout's warp
+//             accesses are free of bank conflicts
+// Multiply-free one-qubit gates (entries in {0, +-1, +-i}; Section 4.1) are
+// applied with additions and swaps only.  While a tile is processed, the
+// next tile's loads are already in flight into a second register set.
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "qs_device.cuh"
+#include "qs_internal.h"
+#include "qs_tile.cuh"
+
+namespace qsgb {
+
+namespace {
+
+constexpr int kRTThreads = 256;
+
+struct RTArgs {
+    RTProgram p;
+    int pos[13];          // tile bit i -> qubit
+    uint64_t ntiles;
+    uint32_t mat_elems;
+    int scale_mode, scale_s;
+    double scale_mag, scale_c[2];
+};
+
+// one-qubit gate on register bit r: the pairs (j0, j0 | 1 << r) of a thread
+template <typename T, int RB, int r>
+__device__ __forceinline__ void rt_gate1(T (&v)[1 << RB], const T* m, int mulfree) {
+    if (mulfree) {
+        const int c00 = mulfree_code(m[0]), c01 = mulfree_code(m[1]), c10 = mulfree_code(m[2]), c11 = mulfree_code(m[3]);
+#pragma unroll
+        for (int p = 0; p < (1 << (RB - 1)); ++p) {
+            const int j0 = ((p >> r) << (r + 1)) | (p & ((1 << r) - 1)), j1 = j0 | (1 << r);
+            const T x = v[j0], y = v[j1];
+            v[j0] = mulfree_sum(x, c00, y, c01);
+            v[j1] = mulfree_sum(x, c10, y, c11);
+        }
+    } else {
+        const T m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
+#pragma unroll
+        for (int p = 0; p < (1 << (RB - 1)); ++p) {
+            const int j0 = ((p >> r) << (r + 1)) | (p & ((1 << r) - 1)), j1 = j0 | (1 << r);
+            const T x = v[j0], y = v[j1];
+            T o0 = cmul(m00, x), o1 = cmul(m10, x);
+            cmac(o0, m01, y);
+            cmac(o1, m11, y);
+            v[j0] = o0;
+            v[j1] = o1;
+        }
+    }
+}
+
+template <typename T, int RB>
+__device__ __forceinline__ void rt_gate1_any(T (&v)[1 << RB], const T* m, int r, int mulfree) {
+    switch (r) {
+        case 0: rt_gate1<T, RB, 0>(v, m, mulfree); break;
+        case 1: rt_gate1<T, RB, 1>(v, m, mulfree); break;
+        case 2: rt_gate1<T, RB, 2>(v, m, mulfree); break;
+        default: rt_gate1<T, RB, RB - 1>(v, m, mulfree); break;
+    }
+}
+
+// k-qubit gate on register bits 0..k-1 (local index = the element's low k
+// bits): each thread applies it to its 2^(RB-k) sets; every matrix entry is
+// read once per thread (a broadcast shared-memory load)
+template <typename T, int RB, int K>
+__device__ __forceinline__ void rt_gate(T (&v)[1 << RB], const T* m) {
+    constexpr int D = 1 << K, S = 1 << (RB - K);
+    T nv[1 << RB];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        T acc[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) acc[s].x = acc[s].y = 0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const T mm = m[r * D + l];
+#pragma unroll
+            for (int s = 0; s < S; ++s) cmac(acc[s], mm, v[(s << K) | l]);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) nv[(s << K) | r] = acc[s];
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) v[j] = nv[j];
+}
+
+template <typename T, int RB>
+__device__ __forceinline__ void rt_gate_any(T (&v)[1 << RB], const T* m, int k) {
+    if (k == 2) rt_gate<T, RB, 2>(v, m);
+    else if (k == 3) rt_gate<T, RB, 3>(v, m);
+    else if constexpr (RB >= 4) rt_gate<T, RB, 4>(v, m);
+}
+
+template <typename R, int RB>
+__global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __restrict__ psi,
+                                                         const typename C2<R>::T* __restrict__ mats,
+                                                         const __grid_constant__ RTArgs a) {
+    using T = typename C2<R>::T;
+    constexpr int PER = 1 << RB, L = RB + 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* buf = reinterpret_cast<T*>(smem_raw);   // 2^L: transposes
+    T* smat = buf + (1u << L);                 // the pass's matrices
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    for (uint32_t i = tid; i < a.mat_elems; i += kRTThreads) smat[i] = mats[i];
+    __syncthreads();
+
+    // tile bits of this thread's lane and warp in a layout
+    auto ebase = [&](const RTLayout& ly) {
+        uint32_t e = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) e |= (uint32_t)((lane >> i) & 1) << ly.lane[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e |= (uint32_t)((wp >> i) & 1) << ly.warp[i];
+        return e;
+    };
+    auto pos_of = [&](uint32_t e) {
+        uint32_t p = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) p ^= ((e >> i) & 1) ? (uint32_t)a.p.poscol[i] : 0u;
+        return p;
+    };
+    auto phys_of = [&](uint32_t e) {
+        uint64_t x = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) x |= (uint64_t)((e >> i) & 1) << a.pos[i];
+        return x;
+    };
+    // HBM offsets of a thread's elements in layout ly for a tile
+    auto tile_base = [&](uint64_t tile) {
+        uint64_t base = tile;
+#pragma unroll
+        for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
+        return base;
+    };
+    const RTLayout& ld = a.p.lay[a.p.load_lay];
+    const RTLayout& stl = a.p.lay[a.p.store_lay];
+    const uint64_t ld_thr = phys_of(ebase(ld)), st_thr = phys_of(ebase(stl));
+    uint64_t ld_col[RB], st_col[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+        ld_col[i] = 1ull << a.pos[ld.reg[i]];
+        st_col[i] = 1ull << a.pos[stl.reg[i]];
+    }
+    auto gload = [&](T (&v)[PER], uint64_t tile) {
+        const uint64_t b = tile_base(tile) | ld_thr;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            uint64_t o = b;
+#pragma unroll
+            for (int i = 0; i < RB; ++i) o |= ((j >> i) & 1) ? ld_col[i] : 0ull;
+            v[j] = psi[o];
+        }
+    };
+
+    T cur[PER], nxt[PER];
+    uint64_t tile = blockIdx.x;
+    if (tile < a.ntiles) gload(cur, tile);
+    for (; tile < a.ntiles; tile += gridDim.x) {
+        const uint64_t tnext = tile + gridDim.x;
+        if (tnext < a.ntiles) gload(nxt, tnext);   // in flight while this tile is processed
+        int lay = a.p.load_lay;
+        for (int o = 0; o < a.p.nops; ++o) {
+            const RTOp& op = a.p.ops[o];
+            if (op.type == RT_LAYOUT) {
+                const RTLayout& A = a.p.lay[lay];
+                const RTLayout& Bl = a.p.lay[op.arg];
+                __syncthreads();  // earlier readers of buf are done
+                {
+                    const uint32_t pb = pos_of(ebase(A));
+                    uint32_t pc[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) pc[i] = a.p.poscol[A.reg[i]];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        uint32_t p = pb;
+#pragma unroll
+                        for (int i = 0; i < RB; ++i) p ^= ((j >> i) & 1) ? pc[i] : 0u;
+                        buf[p] = cur[j];
+                    }
+                }
+                __syncthreads();
+                {
+                    const uint32_t pb = pos_of(ebase(Bl));
+                    uint32_t pc[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) pc[i] = a.p.poscol[Bl.reg[i]];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        uint32_t p = pb;
+#pragma unroll
+                        for (int i = 0; i < RB; ++i) p ^= ((j >> i) & 1) ? pc[i] : 0u;
+                        cur[j] = buf[p];
+                    }
+                }
+                lay = op.arg;
+            } else if (op.type == RT_DIAG) {
+                // local index = its lane/warp part | its register part
+                const RTLayout& ly = a.p.lay[lay];
+                const int k = op.k, D = 1 << k;
+                const uint32_t e0 = ebase(ly);
+                uint32_t lb = 0;
+                for (int i = 0; i < k; ++i) lb |= ((e0 >> op.q[i]) & 1u) << (k - 1 - i);
+                uint32_t cm[RB];
+#pragma unroll
+                for (int m = 0; m < RB; ++m) {
+                    cm[m] = 0;
+                    for (int i = 0; i < k; ++i)
+                        if (ly.reg[m] == op.q[i]) cm[m] = 1u << (k - 1 - i);
+                }
+                const T* dm = smat + op.mat;
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    uint32_t l = lb;
+#pragma unroll
+                    for (int m = 0; m < RB; ++m) l |= ((j >> m) & 1) ? cm[m] : 0u;
+                    cur[j] = cmul(dm[l * (uint32_t)(D + 1)], cur[j]);
+                }
+            } else if (op.type == RT_LANE1) {
+                const T* m = smat + op.mat;
+                const int b = op.arg, sel = (lane >> b) & 1;
+                if (op.mulfree) {
+                    // out_sel = u[sel][sel] own + u[sel][1-sel] partner, each a phase i^c or 0
+                    const int co = mulfree_code(m[sel * 3]), cp = mulfree_code(m[sel ? 2 : 1]);
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        T pv;
+                        pv.x = __shfl_xor_sync(0xffffffffu, cur[j].x, 1 << b);
+                        pv.y = __shfl_xor_sync(0xffffffffu, cur[j].y, 1 << b);
+                        cur[j] = mulfree_sum(cur[j], co, pv, cp);
+                    }
+                } else {
+                    const T co = m[sel * 3], cp = m[sel ? 2 : 1];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        T pv;
+                        pv.x = __shfl_xor_sync(0xffffffffu, cur[j].x, 1 << b);
+                        pv.y = __shfl_xor_sync(0xffffffffu, cur[j].y, 1 << b);
+                        T out = cmul(co, cur[j]);
+                        cmac(out, cp, pv);
+                        cur[j] = out;
+                    }
+                }
+            } else if (op.type == RT_GATE1) {
+                rt_gate1_any<T, RB>(cur, smat + op.mat, op.arg, op.mulfree);
+            } else {  // RT_GATE, k = 2..RB
+                rt_gate_any<T, RB>(cur, smat + op.mat, op.k);
+            }
+        }
+        // store in the store layout (lanes = tile bits 0..4), with the scalar
+        // factored out of the pass's multiply-free gates
+        {
+            const uint64_t b = tile_base(tile) | st_thr;
+            const R mag = (R)a.scale_mag;
+            T c;
+            c.x = (R)a.scale_c[0];
+            c.y = (R)a.scale_c[1];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                uint64_t o = b;
+#pragma unroll
+                for (int i = 0; i < RB; ++i) o |= ((j >> i) & 1) ? st_col[i] : 0ull;
+                T v = cur[j];
+                if (a.scale_mode == 1) {
+                    v = rot_i(v, a.scale_s >> 1);
+                    if (a.scale_s & 1) {  // times (1 + i) (the 1/sqrt(2) is in mag)
+                        const R re = v.x - v.y, im = v.x + v.y;
+                        v.x = re;
+                        v.y = im;
+                    }
+                    v.x *= mag;
+                    v.y *= mag;
+                } else if (a.scale_mode == 2) {
+                    v = cmul(c, v);
+                }
+                psi[o] = v;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < PER; ++j) cur[j] = nxt[j];
+    }
+}
+
+template <typename R, int RB>
+cudaError_t run_rtile(void* psi, const RTArgs& a, const void* dmats, cudaStream_t st) {
+    using T = typename C2<R>::T;
+    const size_t smem = sizeof(T) * (((size_t)1 << (RB + 8)) + a.mat_elems);
+    cudaError_t e = allow_max_dynamic_smem(k_rtile<R, RB>);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * 2);
+    k_rtile<R, RB><<<grid, kRTThreads, smem, st>>>((T*)psi, (const T*)dmats, a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int rtile_bits(qs_dtype dt) { return dt == QS_C64 ? 12 : 11; }
+
+cudaError_t launch_rtile(void* psi, int n, qs_dtype dt, const Pass& ps, const void* dmats, cudaStream_t st) {
+    const int L = rtile_bits(dt);
+    if (ps.L != L || n < L || ps.rt.nops < 1 || ps.rt.nops > kRTMaxOps || ps.rt.nlay < 1) return cudaErrorInvalidValue;
+    RTArgs a{};
+    a.p = ps.rt;
+    for (int i = 0; i < L; ++i) a.pos[i] = ps.pos[i];
+    a.ntiles = 1ull << (n - L);
+    a.mat_elems = (uint32_t)(ps.mats.size() / 2);
+    a.scale_mode = ps.scale_mode;
+    a.scale_s = ps.scale_s;
+    a.scale_mag = ps.scale_mag * ((ps.scale_s & 1) ? 0.70710678118654752440 : 1.0);
+    a.scale_c[0] = ps.scale_c[0];
+    a.scale_c[1] = ps.scale_c[1];
+    return dt == QS_C64 ? run_rtile<float, 4>(psi, a, dmats, st) : run_rtile<double, 3>(psi, a, dmats, st);
+}
+
+}  // namespace qsgb
