@@ -24,6 +24,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "qs_device.cuh"
 #include "qs_internal.h"
@@ -44,9 +45,18 @@ struct RTArgs {
     double scale_mag, scale_c[2];
 };
 
+// Complex64 multiply-accumulate in two packed f32x2 FMAs: with the matrix
+// entry stored as e = (m.re, m.re, -m.im, m.im) and the swapped amplitude
+// vs = (v.im, v.re), acc += m v is acc += e.xy * v + e.zw * vs componentwise.
+__device__ __forceinline__ float2 pmac(float2 acc, const float4& e, float2 v, float2 vs) {
+    acc = cfma(make_float2(e.x, e.y), v, acc);
+    return cfma(make_float2(e.z, e.w), vs, acc);
+}
+__device__ __forceinline__ float2 swapri(float2 v) { return make_float2(v.y, v.x); }
+
 // one-qubit gate on register bit r: the pairs (j0, j0 | 1 << r) of a thread
 template <typename T, int RB, int r>
-__device__ __forceinline__ void rt_gate1(T (&v)[1 << RB], const T* m, int mulfree) {
+__device__ __forceinline__ void rt_gate1(T (&v)[1 << RB], const T* m, const float4* m4, int mulfree) {
     if (mulfree) {
         const int c00 = mulfree_code(m[0]), c01 = mulfree_code(m[1]), c10 = mulfree_code(m[2]), c11 = mulfree_code(m[3]);
 #pragma unroll
@@ -55,6 +65,16 @@ __device__ __forceinline__ void rt_gate1(T (&v)[1 << RB], const T* m, int mulfre
             const T x = v[j0], y = v[j1];
             v[j0] = mulfree_sum(x, c00, y, c01);
             v[j1] = mulfree_sum(x, c10, y, c11);
+        }
+    } else if constexpr (std::is_same<T, float2>::value) {
+        const float4 e00 = m4[0], e01 = m4[1], e10 = m4[2], e11 = m4[3];
+#pragma unroll
+        for (int p = 0; p < (1 << (RB - 1)); ++p) {
+            const int j0 = ((p >> r) << (r + 1)) | (p & ((1 << r) - 1)), j1 = j0 | (1 << r);
+            const float2 x = v[j0], y = v[j1], xs = swapri(x), ys = swapri(y);
+            const float2 z = make_float2(0.f, 0.f);
+            v[j0] = pmac(pmac(z, e00, x, xs), e01, y, ys);
+            v[j1] = pmac(pmac(z, e10, x, xs), e11, y, ys);
         }
     } else {
         const T m00 = m[0], m01 = m[1], m10 = m[2], m11 = m[3];
@@ -72,12 +92,12 @@ __device__ __forceinline__ void rt_gate1(T (&v)[1 << RB], const T* m, int mulfre
 }
 
 template <typename T, int RB>
-__device__ __forceinline__ void rt_gate1_any(T (&v)[1 << RB], const T* m, int r, int mulfree) {
+__device__ __forceinline__ void rt_gate1_any(T (&v)[1 << RB], const T* m, const float4* m4, int r, int mulfree) {
     switch (r) {
-        case 0: rt_gate1<T, RB, 0>(v, m, mulfree); break;
-        case 1: rt_gate1<T, RB, 1>(v, m, mulfree); break;
-        case 2: rt_gate1<T, RB, 2>(v, m, mulfree); break;
-        default: rt_gate1<T, RB, RB - 1>(v, m, mulfree); break;
+        case 0: rt_gate1<T, RB, 0>(v, m, m4, mulfree); break;
+        case 1: rt_gate1<T, RB, 1>(v, m, m4, mulfree); break;
+        case 2: rt_gate1<T, RB, 2>(v, m, m4, mulfree); break;
+        default: rt_gate1<T, RB, RB - 1>(v, m, m4, mulfree); break;
     }
 }
 
@@ -85,32 +105,52 @@ __device__ __forceinline__ void rt_gate1_any(T (&v)[1 << RB], const T* m, int r,
 // bits): each thread applies it to its 2^(RB-k) sets; every matrix entry is
 // read once per thread (a broadcast shared-memory load)
 template <typename T, int RB, int K>
-__device__ __forceinline__ void rt_gate(T (&v)[1 << RB], const T* m) {
+__device__ __forceinline__ void rt_gate(T (&v)[1 << RB], const T* m, const float4* m4) {
     constexpr int D = 1 << K, S = 1 << (RB - K);
     T nv[1 << RB];
+    if constexpr (std::is_same<T, float2>::value) {
+        float2 vs[1 << RB];
 #pragma unroll
-    for (int r = 0; r < D; ++r) {
-        T acc[S];
+        for (int j = 0; j < (1 << RB); ++j) vs[j] = swapri(v[j]);
 #pragma unroll
-        for (int s = 0; s < S; ++s) acc[s].x = acc[s].y = 0;
+        for (int r = 0; r < D; ++r) {
+            float2 acc[S];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            const T mm = m[r * D + l];
+            for (int s = 0; s < S; ++s) acc[s] = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int s = 0; s < S; ++s) cmac(acc[s], mm, v[(s << K) | l]);
+            for (int l = 0; l < D; ++l) {
+                const float4 e = m4[r * D + l];
+#pragma unroll
+                for (int s = 0; s < S; ++s) acc[s] = pmac(acc[s], e, v[(s << K) | l], vs[(s << K) | l]);
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) nv[(s << K) | r] = acc[s];
         }
+    } else {
 #pragma unroll
-        for (int s = 0; s < S; ++s) nv[(s << K) | r] = acc[s];
+        for (int r = 0; r < D; ++r) {
+            T acc[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) acc[s].x = acc[s].y = 0;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                const T mm = m[r * D + l];
+#pragma unroll
+                for (int s = 0; s < S; ++s) cmac(acc[s], mm, v[(s << K) | l]);
+            }
+#pragma unroll
+            for (int s = 0; s < S; ++s) nv[(s << K) | r] = acc[s];
+        }
     }
 #pragma unroll
     for (int j = 0; j < (1 << RB); ++j) v[j] = nv[j];
 }
 
 template <typename T, int RB>
-__device__ __forceinline__ void rt_gate_any(T (&v)[1 << RB], const T* m, int k) {
-    if (k == 2) rt_gate<T, RB, 2>(v, m);
-    else if (k == 3) rt_gate<T, RB, 3>(v, m);
-    else if constexpr (RB >= 4) rt_gate<T, RB, 4>(v, m);
+__device__ __forceinline__ void rt_gate_any(T (&v)[1 << RB], const T* m, const float4* m4, int k) {
+    if (k == 2) rt_gate<T, RB, 2>(v, m, m4);
+    else if (k == 3) rt_gate<T, RB, 3>(v, m, m4);
+    else if constexpr (RB >= 4) rt_gate<T, RB, 4>(v, m, m4);
 }
 
 template <typename R, int RB>
@@ -122,8 +162,14 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* buf = reinterpret_cast<T*>(smem_raw);   // 2^L: transposes
     T* smat = buf + (1u << L);                 // the pass's matrices
+    // complex64: the matrices again as packed-FMA operands (re, re, -im, im)
+    float4* smat4 = reinterpret_cast<float4*>(smat + ((a.mat_elems + 1) & ~1u));
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-    for (uint32_t i = tid; i < a.mat_elems; i += kRTThreads) smat[i] = mats[i];
+    for (uint32_t i = tid; i < a.mat_elems; i += kRTThreads) {
+        const T m = mats[i];
+        smat[i] = m;
+        if constexpr (std::is_same<T, float2>::value) smat4[i] = make_float4(m.x, m.x, -m.y, m.y);
+    }
     __syncthreads();
 
     // tile bits of this thread's lane and warp in a layout
@@ -250,6 +296,15 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
                         pv.y = __shfl_xor_sync(0xffffffffu, cur[j].y, 1 << b);
                         cur[j] = mulfree_sum(cur[j], co, pv, cp);
                     }
+                } else if constexpr (std::is_same<T, float2>::value) {
+                    const float4 eo = smat4[op.mat + sel * 3], ep = smat4[op.mat + (sel ? 2 : 1)];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        float2 pv;
+                        pv.x = __shfl_xor_sync(0xffffffffu, cur[j].x, 1 << b);
+                        pv.y = __shfl_xor_sync(0xffffffffu, cur[j].y, 1 << b);
+                        cur[j] = pmac(pmac(make_float2(0.f, 0.f), eo, cur[j], swapri(cur[j])), ep, pv, swapri(pv));
+                    }
                 } else {
                     const T co = m[sel * 3], cp = m[sel ? 2 : 1];
 #pragma unroll
@@ -263,9 +318,9 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
                     }
                 }
             } else if (op.type == RT_GATE1) {
-                rt_gate1_any<T, RB>(cur, smat + op.mat, op.arg, op.mulfree);
+                rt_gate1_any<T, RB>(cur, smat + op.mat, smat4 + op.mat, op.arg, op.mulfree);
             } else {  // RT_GATE, k = 2..RB
-                rt_gate_any<T, RB>(cur, smat + op.mat, op.k);
+                rt_gate_any<T, RB>(cur, smat + op.mat, smat4 + op.mat, op.k);
             }
         }
         // store in the store layout (lanes = tile bits 0..4), with the scalar
@@ -305,7 +360,8 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
 template <typename R, int RB>
 cudaError_t run_rtile(void* psi, const RTArgs& a, const void* dmats, cudaStream_t st) {
     using T = typename C2<R>::T;
-    const size_t smem = sizeof(T) * (((size_t)1 << (RB + 8)) + a.mat_elems);
+    const size_t smem = sizeof(T) * (((size_t)1 << (RB + 8)) + ((a.mat_elems + 1) & ~1u)) +
+                        (std::is_same<T, float2>::value ? sizeof(float4) * a.mat_elems : 0);
     cudaError_t e = allow_max_dynamic_smem(k_rtile<R, RB>);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * 2);
