@@ -283,6 +283,29 @@ qs_status qs_norm(const qs_state* s, double* out);
  * must be serialised by the caller. */
 qs_status qs_norm_noalloc(const void* device_amplitudes, int n, qs_dtype dt, void* stream, double* out);
 
+/* ------------------------------------------------- Schroedinger-Feynman */
+
+/* Amplitudes <x|U|0...0> of circuit c by the paper's Schroedinger-Feynman
+ * mode (Sections 1 and 6): the qubits in the bit mask part_a form half A,
+ * the others half B; each gate across the cut (it must act on two qubits,
+ * one in each half) is written as a sum of r <= 4 products X_k (x) Y_k
+ * (elimination with full pivoting on the gate's realigned 4 x 4 matrix:
+ * r = 2 for CZ, 4 for fSim), and every choice of one term per crossing gate
+ * is a path.  Both halves of every path are simulated from |0...0> by the
+ * batched kernel (one launch per half); then
+ *   out[i] = sum over paths psi_A(path)[x_A] psi_B(path)[x_B],
+ * x = indices[i], x_A / x_B its bits in each half, summed in FP64.
+ *   dt: state precision of the half simulations.
+ *   indices: count amplitude indices (host), each < 2^n.
+ *   out: 2 * count doubles (host), interleaved (re, im).
+ *   num_paths: if not NULL, receives the number of paths (also when
+ *   count == 0: a way to cost a cut without simulating).
+ * Each half has at most 30 qubits; at most 65536 paths (QS_ERR_UNSUPPORTED
+ * otherwise).  Device memory: every path's two half states, allocated and
+ * freed in `stream`'s order; the call synchronises `stream`. */
+qs_status qs_sf_amplitudes(const qs_circuit* c, uint64_t part_a, qs_dtype dt, const uint64_t* indices,
+                           uint64_t count, void* stream, double* out, uint64_t* num_paths);
+
 /* ------------------------------------------------------------ observables */
 
 qs_status qs_pauli_sum_create(int n, qs_pauli_sum** out);

@@ -92,6 +92,8 @@ _SIGS = {
     "qs_batch_sync": (ct.c_int, [_P]),
     "qs_batch_destroy": (ct.c_int, [_P]),
     "qs_batch_autotune": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.c_int, _P, _P, ct.POINTER(Options)]),
+    "qs_sf_amplitudes": (ct.c_int, [_P, ct.c_uint64, ct.c_int, ct.POINTER(ct.c_uint64), ct.c_uint64, _P,
+                                    ct.POINTER(ct.c_double), ct.POINTER(ct.c_uint64)]),
 }
 
 
@@ -529,6 +531,22 @@ def batch_autotune(circuits: Sequence[Circuit], dtype="c64", stream=None) -> Opt
           ct.c_void_p(probe.states.data_ptr()), ct.c_void_p(_stream_ptr(stream)), ct.byref(best))
     probe.close()
     return best
+
+
+def sf_amplitudes(circ: Circuit, part_a: Sequence[int], indices, dtype="c64", stream=None):
+    """Amplitudes at `indices` by the Schroedinger-Feynman mode
+    (qs_sf_amplitudes): qubits `part_a` form one half, the rest the other.
+    Returns (complex128 array, number of paths)."""
+    mask = 0
+    for q in part_a:
+        mask |= 1 << int(q)
+    idx = np.ascontiguousarray(np.asarray(indices, dtype=np.uint64).ravel())
+    out = np.zeros(2 * max(1, idx.size), dtype=np.float64)
+    paths = ct.c_uint64()
+    _call("qs_sf_amplitudes", circ.handle, ct.c_uint64(mask), QS_C64 if dtype == "c64" else QS_C128,
+          idx.ctypes.data_as(ct.POINTER(ct.c_uint64)), ct.c_uint64(idx.size), ct.c_void_p(_stream_ptr(stream)),
+          out.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(paths))
+    return out[:2 * idx.size].view(np.complex128), int(paths.value)
 
 
 def version() -> str:
