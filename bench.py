@@ -70,9 +70,11 @@ def parse_args(argv=None):
     ap.add_argument("--depth", type=int, default=26, help="cycles of the paper-gate-set circuit")
     ap.add_argument("--diag-clusters", choices=["auto", "on", "off"], default="auto",
                     help="cluster diagonal gates of any width into one pass (Sections 4.2, 4.5); auto: timed choice")
-    ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "batch_adjoint", "precision"], default="grid",
+    ap.add_argument("--workload", choices=["grid", "adjoint", "batch", "batch_adjoint", "precision", "sf"],
+                    default="grid",
                     help="grid: the headline circuit; adjoint: gradient vs forward on the ansatz; "
-                         "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q")
+                         "batch: 512 uneven circuits in one launch; precision: tensor-core modes at 32q; "
+                         "sf: Schroedinger-Feynman amplitudes of the paper's gate set across a grid cut")
     ap.add_argument("--layers", type=int, default=20)
     ap.add_argument("--count", type=int, default=None, help="circuits (batch: 512) or gradients (batch_adjoint: 256)")
     return ap.parse_args(argv)
@@ -776,6 +778,40 @@ def run_precision(a):
     print(json.dumps(out), flush=True)
 
 
+def run_sf(a):
+    """Schroedinger-Feynman amplitudes (the paper's hybrid mode): the paper's
+    gate-set circuit on the near-square grid, cut between the middle grid
+    columns; `--count` amplitudes (default 4096: the first ones) from all
+    paths.  Wall-clock time of the call (host path set-up included)."""
+    import torch
+    import paper_2008_00216_gb300 as pkg
+    from paper_2008_00216_gb300 import binding as B
+    from workloads import circuits as C
+    pkg.load()
+    n = a.n
+    circ = C.paper_circuit(n, a.depth, a.seed)
+    rows, cols = C.grid_shape(n)
+    part_a = [r * cols + cc for r in range(rows) for cc in range(cols // 2) if r * cols + cc < n]
+    c = B.circuit_from(circ)
+    count = a.count or 4096
+    idx = np.arange(count, dtype=np.uint64)
+    _, paths = B.sf_amplitudes(c, part_a, [], a.dtype)
+    for _ in range(max(1, a.warmup)):
+        B.sf_amplitudes(c, part_a, idx, a.dtype)
+    times = []
+    for _ in range(a.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.sf_amplitudes(c, part_a, idx, a.dtype)
+        times.append(time.perf_counter() - t0)
+    sec = sorted(times)[len(times) // 2]
+    out = {"metric": "Schroedinger-Feynman amplitudes", "workload": "sf", "value": sec, "unit": "s per call",
+           "higher_is_better": False, "n": n, "depth": f"1+{a.depth}+1", "dtype": a.dtype, "paths": paths,
+           "half_qubits": [len(part_a), n - len(part_a)], "amplitudes": count, "steps": a.steps,
+           "timing": "wall clock of the synchronous call (path circuits built on the host included)"}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     a = parse_args()
     if a.impl == "reference":
@@ -788,6 +824,8 @@ def main():
         run_precision(a)
     elif a.workload == "batch_adjoint":
         run_batch_adjoint(a)
+    elif a.workload == "sf":
+        run_sf(a)
     else:
         run_own(a)
 

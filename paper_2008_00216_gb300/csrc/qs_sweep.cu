@@ -294,6 +294,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 ls[j] = *reinterpret_cast<const T*>(pl + o);
             }
         }
+        // the next tile of psi and lambda on its way into L2 while this one is processed
+        if (tile + gridDim.x < a.ntiles) {
+            uint64_t nb = tile + gridDim.x;
+            for (int i = 0; i < L; ++i) nb = insert_zero(nb, a.pos[i]);
+            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(T);
+            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(T);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xo[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xo[j]));
+            }
+        }
         int lay = 0;
         gdone = 0;
         for (int o = 0; o < a.nops; ++o) {
