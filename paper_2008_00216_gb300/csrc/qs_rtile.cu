@@ -23,6 +23,8 @@
 // next tile's loads are already in flight into a second register set.
 #include <stdint.h>
 
+#include <math.h>
+
 #include <algorithm>
 #include <type_traits>
 
@@ -357,6 +359,346 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
     }
 }
 
+// ---------------------------------------------------------------- complex128
+// Complex128 tiles in float-float arithmetic: each amplitude d is held as
+// hi + lo with hi = float(d) and lo = float(d - hi) (about 48 significant
+// bits), and every product and sum runs on the FP32 pipe with error-free
+// transformations (FMA-based TwoProd, Knuth's TwoSum), accumulating the
+// rounding errors of a sum of products in a second float.  Only the loads
+// and stores convert to and from FP64.
+struct FFC {
+    float2 h, l;   // (re, im) high parts, (re, im) low parts
+};
+// d = hi + lo with integer operations only (the FP64 pipe is the scarce one):
+// hi keeps the top 24 significant bits (truncated), lo the next 29 rounded
+// to 24 (total relative error below 2^-48).  Magnitudes whose low part would
+// leave float's normal range (zeros, |d| < 2^-74, |d| >= 2^128) take the
+// plain FP64 conversion.
+__device__ __forceinline__ void ff_split(double d, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const int e = (int)((b >> 52) & 0x7FFu) - 1023;
+    if (e < -74 || e > 127) {
+        hi = (float)d;
+        lo = (float)(d - (double)hi);
+        return;
+    }
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
+    const unsigned r = (unsigned)(m & 0x1FFFFFFFu);            // r * 2^(e - 52)
+    const float lm = __uint2float_rn(r) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
+    lo = sign ? -lm : lm;
+}
+// hi + lo to FP64 with integer operations: hi + lo needs at most 49
+// significant bits when |lo| <= ulp(hi) (as after ffa_get), so it is
+// summed exactly in 64-bit fixed point at hi's scale and normalised.
+__device__ __forceinline__ double ff_merge(float hi, float lo) {
+    const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
+    const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
+    if (eh == 0 || eh == 255 || el == 255 || (el != 0 && eh - el > 60)) return (double)hi + (double)lo;
+    // 53-bit fixed point: value = T * 2^(eh - 127 - 52)
+    long long T = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
+    if (el != 0) {
+        const long long L = (long long)((lb & 0x7FFFFFu) | 0x800000u);
+        const int sh = 29 - (eh - el);
+        const long long Ls = sh >= 0 ? (L << sh) : (L >> (-sh));
+        T += ((hb ^ lb) >> 31) ? -Ls : Ls;
+    }
+    if (T <= 0) return (double)hi + (double)lo;   // cannot happen for |lo| <= ulp(hi)
+    // normalise to a 53-bit significand: leading bit at position 52
+    const int lead = 63 - __clzll(T);
+    int ex = eh - 127 + (lead - 52);
+    unsigned long long M = (unsigned long long)T;
+    M = lead >= 52 ? (M >> (lead - 52)) : (M << (52 - lead));   // lead > 52 drops no set bits here (sum of 49 bits)
+    const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) | ((unsigned long long)(ex + 1023) << 52) |
+                                    (M & 0xFFFFFFFFFFFFFull);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ FFC ff_from(double2 d) {
+    FFC r;
+    ff_split(d.x, r.h.x, r.l.x);
+    ff_split(d.y, r.h.y, r.l.y);
+    return r;
+}
+__device__ __forceinline__ double2 ff_to(const FFC& v) { return make_double2(ff_merge(v.h.x, v.l.x), ff_merge(v.h.y, v.l.y)); }
+struct FFAcc {
+    float sr, er, si, ei;   // running sums of high parts and of everything else
+};
+__device__ __forceinline__ FFAcc ffa_zero() { return FFAcc{0.f, 0.f, 0.f, 0.f}; }
+// S + E += (ah + al)(bh + bl), dropping al * bl (2^-48 relative)
+__device__ __forceinline__ void ffa_term(float& S, float& E, float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, e);
+    e = fmaf(al, bh, e);
+    float s, t;
+    two_sum(S, p, s, t);
+    S = s;
+    E += t + e;
+}
+__device__ __forceinline__ void ffa_cmac(FFAcc& a, const FFC& m, const FFC& v) {
+    ffa_term(a.sr, a.er, m.h.x, m.l.x, v.h.x, v.l.x);
+    ffa_term(a.sr, a.er, -m.h.y, -m.l.y, v.h.y, v.l.y);
+    ffa_term(a.si, a.ei, m.h.x, m.l.x, v.h.y, v.l.y);
+    ffa_term(a.si, a.ei, m.h.y, m.l.y, v.h.x, v.l.x);
+}
+__device__ __forceinline__ void ffa_add(FFAcc& a, const FFC& v) {
+    float s, t;
+    two_sum(a.sr, v.h.x, s, t);
+    a.sr = s;
+    a.er += t + v.l.x;
+    two_sum(a.si, v.h.y, s, t);
+    a.si = s;
+    a.ei += t + v.l.y;
+}
+__device__ __forceinline__ FFC ffa_get(const FFAcc& a) {
+    FFC r;
+    r.h.x = a.sr + a.er;
+    r.l.x = a.er - (r.h.x - a.sr);
+    r.h.y = a.si + a.ei;
+    r.l.y = a.ei - (r.h.y - a.si);
+    return r;
+}
+__device__ __forceinline__ FFC ff_rot(const FFC& v, int code) {   // i^code v
+    FFC r;
+    r.h = rot_i(v.h, code);
+    r.l = rot_i(v.l, code);
+    return r;
+}
+__device__ __forceinline__ FFC ff_cmul(const FFC& m, const FFC& v) {
+    FFAcc a = ffa_zero();
+    ffa_cmac(a, m, v);
+    return ffa_get(a);
+}
+// out = i^ca a + i^cb b, a zero code (-1) dropping its term: additions only
+__device__ __forceinline__ FFC ff_mulfree_sum(const FFC& a, int ca, const FFC& b, int cb) {
+    FFAcc acc = ffa_zero();
+    if (ca >= 0) ffa_add(acc, ff_rot(a, ca));
+    if (cb >= 0) ffa_add(acc, ff_rot(b, cb));
+    return ffa_get(acc);
+}
+__device__ __forceinline__ FFC ff_shfl_xor(const FFC& v, int mask) {
+    FFC r;
+    r.h.x = __shfl_xor_sync(0xffffffffu, v.h.x, mask);
+    r.h.y = __shfl_xor_sync(0xffffffffu, v.h.y, mask);
+    r.l.x = __shfl_xor_sync(0xffffffffu, v.l.x, mask);
+    r.l.y = __shfl_xor_sync(0xffffffffu, v.l.y, mask);
+    return r;
+}
+
+template <int RB, int r>
+__device__ __forceinline__ void ff_gate1(FFC (&v)[1 << RB], const FFC* m, int mulfree) {
+#pragma unroll
+    for (int p = 0; p < (1 << (RB - 1)); ++p) {
+        const int j0 = ((p >> r) << (r + 1)) | (p & ((1 << r) - 1)), j1 = j0 | (1 << r);
+        const FFC x = v[j0], y = v[j1];
+        if (mulfree) {
+            const int c00 = mulfree_code(m[0].h), c01 = mulfree_code(m[1].h), c10 = mulfree_code(m[2].h),
+                      c11 = mulfree_code(m[3].h);
+            v[j0] = ff_mulfree_sum(x, c00, y, c01);
+            v[j1] = ff_mulfree_sum(x, c10, y, c11);
+        } else {
+            FFAcc a0 = ffa_zero(), a1 = ffa_zero();
+            ffa_cmac(a0, m[0], x);
+            ffa_cmac(a0, m[1], y);
+            ffa_cmac(a1, m[2], x);
+            ffa_cmac(a1, m[3], y);
+            v[j0] = ffa_get(a0);
+            v[j1] = ffa_get(a1);
+        }
+    }
+}
+template <int RB, int K>
+__device__ __forceinline__ void ff_gate(FFC (&v)[1 << RB], const FFC* m) {
+    constexpr int D = 1 << K, S = 1 << (RB - K);
+    FFC nv[1 << RB];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+        FFAcc acc[S];
+#pragma unroll
+        for (int s = 0; s < S; ++s) acc[s] = ffa_zero();
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            const FFC mm = m[r * D + l];
+#pragma unroll
+            for (int s = 0; s < S; ++s) ffa_cmac(acc[s], mm, v[(s << K) | l]);
+        }
+#pragma unroll
+        for (int s = 0; s < S; ++s) nv[(s << K) | r] = ffa_get(acc[s]);
+    }
+#pragma unroll
+    for (int j = 0; j < (1 << RB); ++j) v[j] = nv[j];
+}
+
+template <int RB>
+__global__ void __launch_bounds__(kRTThreads, 2) k_rtile_ff(double2* __restrict__ psi, const double2* __restrict__ mats,
+                                                            const __grid_constant__ RTArgs a) {
+    constexpr int PER = 1 << RB, L = RB + 8;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* buf = reinterpret_cast<float4*>(smem_raw);            // 2^L: transposes, (h.x, h.y, l.x, l.y)
+    FFC* smat = reinterpret_cast<FFC*>(buf + (1u << L));          // the pass's matrices, float-float
+    const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+    for (uint32_t i = tid; i < a.mat_elems; i += kRTThreads) smat[i] = ff_from(mats[i]);
+    __syncthreads();
+    auto ebase = [&](const RTLayout& ly) {
+        uint32_t e = 0;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) e |= (uint32_t)((lane >> i) & 1) << ly.lane[i];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) e |= (uint32_t)((wp >> i) & 1) << ly.warp[i];
+        return e;
+    };
+    auto pos_of = [&](uint32_t e) {
+        uint32_t p = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) p ^= ((e >> i) & 1) ? (uint32_t)a.p.poscol[i] : 0u;
+        return p;
+    };
+    auto phys_of = [&](uint32_t e) {
+        uint64_t x = 0;
+#pragma unroll
+        for (int i = 0; i < L; ++i) x |= (uint64_t)((e >> i) & 1) << a.pos[i];
+        return x;
+    };
+    auto tile_base = [&](uint64_t tile) {
+        uint64_t base = tile;
+#pragma unroll
+        for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
+        return base;
+    };
+    const RTLayout& ld = a.p.lay[a.p.load_lay];
+    const RTLayout& stl = a.p.lay[a.p.store_lay];
+    const uint64_t ld_thr = phys_of(ebase(ld)), st_thr = phys_of(ebase(stl));
+    uint64_t ld_col[RB], st_col[RB];
+#pragma unroll
+    for (int i = 0; i < RB; ++i) {
+        ld_col[i] = 1ull << a.pos[ld.reg[i]];
+        st_col[i] = 1ull << a.pos[stl.reg[i]];
+    }
+    auto gload = [&](double2 (&v)[PER], uint64_t tile) {
+        const uint64_t b = tile_base(tile) | ld_thr;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            uint64_t o = b;
+#pragma unroll
+            for (int i = 0; i < RB; ++i) o |= ((j >> i) & 1) ? ld_col[i] : 0ull;
+            v[j] = psi[o];
+        }
+    };
+    // the scalar factored out of the pass's multiply-free gates, as float-float
+    FFC scale;
+    scale.h = make_float2(1.f, 0.f);
+    scale.l = make_float2(0.f, 0.f);
+    if (a.scale_mode) scale = ff_from(make_double2(a.scale_c[0], a.scale_c[1]));
+
+    double2 nxt[PER];
+    FFC cur[PER];
+    uint64_t tile = blockIdx.x;
+    if (tile < a.ntiles) gload(nxt, tile);
+    for (; tile < a.ntiles; tile += gridDim.x) {
+#pragma unroll
+        for (int j = 0; j < PER; ++j) cur[j] = ff_from(nxt[j]);
+        const uint64_t tnext = tile + gridDim.x;
+        if (tnext < a.ntiles) gload(nxt, tnext);   // in flight while this tile is processed
+        int lay = a.p.load_lay;
+        for (int o = 0; o < a.p.nops; ++o) {
+            const RTOp& op = a.p.ops[o];
+            if (op.type == RT_LAYOUT) {
+                const RTLayout& A = a.p.lay[lay];
+                const RTLayout& Bl = a.p.lay[op.arg];
+                __syncthreads();
+                {
+                    const uint32_t pb = pos_of(ebase(A));
+                    uint32_t pc[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) pc[i] = a.p.poscol[A.reg[i]];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        uint32_t p = pb;
+#pragma unroll
+                        for (int i = 0; i < RB; ++i) p ^= ((j >> i) & 1) ? pc[i] : 0u;
+                        buf[p] = make_float4(cur[j].h.x, cur[j].h.y, cur[j].l.x, cur[j].l.y);
+                    }
+                }
+                __syncthreads();
+                {
+                    const uint32_t pb = pos_of(ebase(Bl));
+                    uint32_t pc[RB];
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) pc[i] = a.p.poscol[Bl.reg[i]];
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        uint32_t p = pb;
+#pragma unroll
+                        for (int i = 0; i < RB; ++i) p ^= ((j >> i) & 1) ? pc[i] : 0u;
+                        const float4 w = buf[p];
+                        cur[j].h = make_float2(w.x, w.y);
+                        cur[j].l = make_float2(w.z, w.w);
+                    }
+                }
+                lay = op.arg;
+            } else if (op.type == RT_DIAG) {
+                const RTLayout& ly = a.p.lay[lay];
+                const int k = op.k, D = 1 << k;
+                const uint32_t e0 = ebase(ly);
+                uint32_t lb = 0;
+                for (int i = 0; i < k; ++i) lb |= ((e0 >> op.q[i]) & 1u) << (k - 1 - i);
+                uint32_t cm[RB];
+#pragma unroll
+                for (int m = 0; m < RB; ++m) {
+                    cm[m] = 0;
+                    for (int i = 0; i < k; ++i)
+                        if (ly.reg[m] == op.q[i]) cm[m] = 1u << (k - 1 - i);
+                }
+                const FFC* dm = smat + op.mat;
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    uint32_t l = lb;
+#pragma unroll
+                    for (int m = 0; m < RB; ++m) l |= ((j >> m) & 1) ? cm[m] : 0u;
+                    cur[j] = ff_cmul(dm[l * (uint32_t)(D + 1)], cur[j]);
+                }
+            } else if (op.type == RT_LANE1) {
+                const FFC* m = smat + op.mat;
+                const int b = op.arg, sel = (lane >> b) & 1;
+                const FFC co = m[sel * 3], cp = m[sel ? 2 : 1];
+                if (op.mulfree) {
+                    const int ko = mulfree_code(co.h), kp = mulfree_code(cp.h);
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) cur[j] = ff_mulfree_sum(cur[j], ko, ff_shfl_xor(cur[j], 1 << b), kp);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < PER; ++j) {
+                        const FFC pv = ff_shfl_xor(cur[j], 1 << b);
+                        FFAcc acc = ffa_zero();
+                        ffa_cmac(acc, co, cur[j]);
+                        ffa_cmac(acc, cp, pv);
+                        cur[j] = ffa_get(acc);
+                    }
+                }
+            } else if (op.type == RT_GATE1) {
+                const FFC* m = smat + op.mat;
+                switch (op.arg) {
+                    case 0: ff_gate1<RB, 0>(cur, m, op.mulfree); break;
+                    case 1: ff_gate1<RB, 1>(cur, m, op.mulfree); break;
+                    default: ff_gate1<RB, RB - 1>(cur, m, op.mulfree); break;
+                }
+            } else {  // RT_GATE, k = 2..RB
+                if (op.k == 2) ff_gate<RB, 2>(cur, smat + op.mat);
+                else ff_gate<RB, 3>(cur, smat + op.mat);
+            }
+        }
+        const uint64_t b = tile_base(tile) | st_thr;
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            uint64_t o = b;
+#pragma unroll
+            for (int i = 0; i < RB; ++i) o |= ((j >> i) & 1) ? st_col[i] : 0ull;
+            psi[o] = ff_to(a.scale_mode ? ff_cmul(scale, cur[j]) : cur[j]);
+        }
+    }
+}
+
 template <typename R, int RB>
 cudaError_t run_rtile(void* psi, const RTArgs& a, const void* dmats, cudaStream_t st) {
     using T = typename C2<R>::T;
@@ -386,7 +728,21 @@ cudaError_t launch_rtile(void* psi, int n, qs_dtype dt, const Pass& ps, const vo
     a.scale_mag = ps.scale_mag * ((ps.scale_s & 1) ? 0.70710678118654752440 : 1.0);
     a.scale_c[0] = ps.scale_c[0];
     a.scale_c[1] = ps.scale_c[1];
-    return dt == QS_C64 ? run_rtile<float, 4>(psi, a, dmats, st) : run_rtile<double, 3>(psi, a, dmats, st);
+    if (dt == QS_C64) return run_rtile<float, 4>(psi, a, dmats, st);
+    // complex128: float-float arithmetic; the scale as one complex factor
+    if (a.scale_mode == 1) {
+        const double ang = 0.78539816339744830962 * (double)a.scale_s;   // pi/4 per step
+        const double mag = ps.scale_mag;
+        a.scale_c[0] = mag * cos(ang);
+        a.scale_c[1] = mag * sin(ang);
+        a.scale_mode = 2;
+    }
+    const size_t smem = 16 * ((size_t)1 << 11) + 16 * (size_t)a.mat_elems;
+    cudaError_t e = allow_max_dynamic_smem(k_rtile_ff<3>);
+    if (e != cudaSuccess) return e;
+    const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * 2);
+    k_rtile_ff<3><<<grid, kRTThreads, smem, st>>>((double2*)psi, (const double2*)dmats, a);
+    return cudaGetLastError();
 }
 
 }  // namespace qsgb
