@@ -618,29 +618,64 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
             for (int l = 0; l < nlay; ++l)
                 if (l != cur && l != last) order.push_back(l);
             if (last != cur) order.push_back(last);
+            struct G1Op {
+                SweepOpRec op;
+                double c8[8];
+                int param;
+            };
             for (int l : order) {
-                bool any = false;
+                std::vector<G1Op> gl;  // this step's gates on the layout's register bits
                 for (int gi : st.gates) {
                     const GateRec& g = c.gates[gi];
                     const int bit = local_of[g.qubits[0]];
                     if (layout_of(bit) != l) continue;
-                    if (!any && l != cur) {
-                        p.ops.push_back({SWEEP_LAYOUT, (uint8_t)l, 0, 0, 0});
-                        cur = l;
-                    }
-                    any = true;
                     GateRec u;
                     conj_transpose(g, u);
-                    SweepOpRec op{SWEEP_G1, (uint8_t)(bit - lay_a[l]), 0, 0, (uint32_t)(p.mats.size() / 8)};
+                    G1Op e{};
+                    e.op = SweepOpRec{SWEEP_G1, (uint8_t)(bit - lay_a[l]), 0, 0, 0};
+                    e.param = -1;
                     if (g.param >= 0) {
                         const char P = g.paulis[0];
-                        op.gen = P == 'X' ? 1 : P == 'Y' ? 2 : P == 'Z' ? 3 : 0;
-                        if (op.gen) p.slots.push_back(g.param);
+                        e.op.gen = P == 'X' ? 1 : P == 'Y' ? 2 : P == 'Z' ? 3 : 0;
+                        if (e.op.gen) e.param = g.param;
                     }
-                    double c8[8];
-                    op.form = (uint8_t)g1_coefficients(u, op.gen, c8);
-                    p.mats.insert(p.mats.end(), c8, c8 + 8);
-                    p.ops.push_back(op);
+                    if (dt == QS_C128) {  // float-float pass: U^dagger's four entries
+                        bool real = true;
+                        for (int i = 0; i < 8; ++i) {
+                            e.c8[i] = u.m[i];
+                            real = real && (i % 2 == 0 || u.m[i] == 0.0);
+                        }
+                        e.op.form = (uint8_t)(real ? G1_FF_REAL : G1_FF_CPLX);
+                    } else {
+                        e.op.form = (uint8_t)g1_coefficients(u, e.op.gen, e.c8);
+                    }
+                    gl.push_back(e);
+                }
+                if (gl.empty()) continue;
+                if (l != cur) {
+                    p.ops.push_back({SWEEP_LAYOUT, (uint8_t)l, 0, 0, 0});
+                    cur = l;
+                }
+                // one gate of one form on every register bit: a single op (the
+                // gates commute, so bit order is as good as circuit order)
+                bool all = (int)gl.size() == RB;
+                unsigned bits = 0;
+                for (const G1Op& e : gl) {
+                    all = all && e.op.form == gl[0].op.form && e.op.gen == gl[0].op.gen;
+                    bits |= 1u << e.op.arg;
+                }
+                const int f0 = gl[0].op.form;
+                all = all && bits == (1u << RB) - 1 &&
+                      (f0 == G1_RSHEAR || f0 == G1_RSHEAR_Y || f0 == G1_CSHEAR_X || f0 == G1_FF_REAL || f0 == G1_FF_CPLX);
+                if (all) {
+                    std::sort(gl.begin(), gl.end(), [](const G1Op& x, const G1Op& y) { return x.op.arg < y.op.arg; });
+                    p.ops.push_back({SWEEP_G1ALL, 0, (uint8_t)f0, gl[0].op.gen, (uint32_t)(p.mats.size() / 8)});
+                }
+                for (G1Op& e : gl) {
+                    e.op.idx = (uint32_t)(p.mats.size() / 8);
+                    p.mats.insert(p.mats.end(), e.c8, e.c8 + 8);
+                    if (e.param >= 0) p.slots.push_back(e.param);
+                    if (!all) p.ops.push_back(e.op);
                 }
             }
         }

@@ -581,8 +581,13 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
 // runs the block search and hands over each group as soon as it is found;
 // this thread forms the group's block and pass (each block its own pass),
 // uploads the pass's matrix and launches it in stream order, so the GPU runs
-// pass i while the search looks for block i + 1.
+// pass i while the search looks for block i + 1.  Passes wait in a short
+// look-ahead window so that the bit-0 placement of the planned path
+// (bit0_plan) can keep qubit 0 out of the 6-qubit passes' targets here too:
+// the window's leading run of 6-qubit passes is planned from the current
+// exchange state, the first pass is committed and launched.
 static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
+    constexpr size_t kWindow = 3;  // passes formed ahead of the one launched
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::vector<int>> queue;
@@ -603,23 +608,10 @@ static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_optio
         cv.notify_one();
     });
     qs_status st = QS_OK;
+    const int n = c->n;
     const size_t esz = s->amp_bytes();
     std::vector<char> host;
-    for (;;) {
-        std::vector<int> g;
-        {
-            std::unique_lock<std::mutex> lk(mu);
-            cv.wait(lk, [&]() { return !queue.empty() || done; });
-            if (queue.empty()) break;
-            g = std::move(queue.front());
-            queue.pop_front();
-        }
-        if (st != QS_OK) continue;  // drain the search after a failure
-        GateRec b;
-        block_product(c->n, c->gates, g, b);
-        Pass p;
-        single_block_pass(c->n, s->dt, opt, b, p);
-        factor_tile_scalars(p);
+    auto launch_one = [&](Pass& p) {
         void* dm = nullptr;
         const size_t elems = p.mats.size() / 2;
         cudaError_t e = cudaSuccess;
@@ -636,9 +628,70 @@ static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_optio
         if (e == cudaSuccess) e = launch_pass(s, p, dm, opt.precision);
         if (dm) cudaFreeAsync(dm, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "streamed pass");
+    };
+    int xs = -1;  // exchange state: -1 standard order, else the bit exchanged with bit 0
+    auto restore = [&]() {  // back to standard order with a permutation pass
+        GateRec g;
+        g.k = 2;
+        g.qubits[0] = xs;
+        g.qubits[1] = 0;
+        g.m.assign(32, 0.0);
+        const int perm[4] = {0, 2, 1, 3};
+        for (int r = 0; r < 4; ++r) g.m[2 * (r * 4 + perm[r])] = 1.0;
+        g.kind = QS_GATE_MONOMIAL;
+        Pass p;
+        single_block_pass(n, s->dt, opt, g, p);
+        launch_one(p);
+        xs = -1;
+    };
+    std::deque<Pass> pending;
+    size_t launched = 0;  // the window grows with the passes already queued, so the GPU starts at once
+    auto drain = [&](bool final) {
+        while (st == QS_OK && !pending.empty() && (final || pending.size() > std::min(kWindow, launched))) {
+            Pass& p0 = pending.front();
+            if (p0.kind == PASS_GEMM) {
+                std::vector<const Pass*> run;
+                size_t k = 0;
+                while (k < pending.size() && pending[k].kind == PASS_GEMM) run.push_back(&pending[k++]);
+                const bool end_free = !final && k == pending.size();  // the run may go on past the window
+                std::vector<int> choice;
+                const int bc = bit0_plan(n, run, xs, end_free, choice) >= 0 ? choice[0] : -2;
+                xs = bit0_apply(p0, xs, bc);
+            } else if (xs >= 0) {
+                if (p0.kind == PASS_DENSE || p0.kind == PASS_DIAG || p0.kind == PASS_MONO) {
+                    for (int i = 0; i < p0.k; ++i)  // any qubit order: relabel in place
+                        p0.qubits[i] = p0.qubits[i] == 0 ? xs : p0.qubits[i] == xs ? 0 : p0.qubits[i];
+                } else {
+                    restore();
+                }
+            }
+            launch_one(p0);
+            pending.pop_front();
+            ++launched;
+        }
+        if (final && st == QS_OK && xs >= 0) restore();
+    };
+    for (;;) {
+        std::vector<int> g;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&]() { return !queue.empty() || done; });
+            if (queue.empty()) break;
+            g = std::move(queue.front());
+            queue.pop_front();
+        }
+        if (st != QS_OK) continue;  // drain the search after a failure
+        GateRec b;
+        block_product(n, c->gates, g, b);
+        Pass p;
+        single_block_pass(n, s->dt, opt, b, p);
+        factor_tile_scalars(p);
+        pending.push_back(std::move(p));
+        drain(false);
     }
     search.join();
     if (fst != QS_OK) return fail(fst, "%s", fmsg.c_str());
+    drain(true);
     return st;
 }
 

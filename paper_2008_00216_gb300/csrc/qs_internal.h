@@ -252,6 +252,9 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 // The pass of one fused block on its own (no tile grouping).
 void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec& g, Pass& p);
+// bit-0 placement over 6-qubit passes (qs_plan.cpp)
+int bit0_plan(int n, const std::vector<const Pass*>& run, int s0, bool end_free, std::vector<int>& choice);
+int bit0_apply(Pass& p, int s, int bc);
 // One group's fused block (see fuse_gates): the FP64 product of in[taken].
 void block_product(int n, const std::vector<GateRec>& in, const std::vector<int>& taken, GateRec& b);
 // fuse_gates in stream form: each group of gate indices goes to `emit` as soon
@@ -379,7 +382,10 @@ constexpr int kSweepMaxLayouts = 4;
 constexpr int kSweepDiagGens = 40;    // Z generators of one diagonal op
 constexpr int kSweepDiagCross = 32;
 inline uint32_t sweep_tab_budget(qs_dtype dt) { return dt == QS_C64 ? 3072u : 1536u; }
-enum SweepOpType { SWEEP_LAYOUT = 0, SWEEP_G1 = 1, SWEEP_DIAG = 2 };
+// SWEEP_G1ALL: one-qubit gates of one form (G1_RSHEAR, G1_RSHEAR_Y or
+// G1_CSHEAR_X) and generator on every register bit, in bit order, with
+// consecutive coefficient sets from idx
+enum SweepOpType { SWEEP_LAYOUT = 0, SWEEP_G1 = 1, SWEEP_DIAG = 2, SWEEP_G1ALL = 3 };
 // One-qubit op forms.  U^dagger, times a phase common to psi and lambda (it
 // cancels in Im <lambda|P|psi>), is M = [[a, -conj(b)], [b, conj(a)]] with
 // Re a >= 0, applied as three in-place shears p0 += z p1, p1 += y p0,
@@ -391,7 +397,9 @@ enum SweepG1Form {
     G1_RSHEAR_NEG = 3,     // p1 negated, then real shears (a reflection), no gradient
     G1_CSHEAR = 4,         // complex shears, no gradient
     G1_CSHEAR_X = 5,       // complex shears, generator X
-    G1_FORMS = 6
+    G1_FF_CPLX = 6,        // complex128 in float-float: U^dagger's four entries
+    G1_FF_REAL = 7,        // the same, all four real
+    G1_FORMS = 8
 };
 struct SweepOpRec {
     uint8_t type;          // SweepOpType

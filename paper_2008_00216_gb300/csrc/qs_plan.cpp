@@ -1254,24 +1254,18 @@ bool build_rtile_program(qs_dtype dt, const Pass& p, RTProgram& prog) {
     return true;
 }
 
-// Qubit 0 out of the targets of 6-qubit tensor-core passes: a reordering of
-// index bits, the GPU form of the paper's bit-permuting recursive transform
-// (Section 5.1), folded into passes that run anyway.  A pass whose targets
-// leave bit 0 free may write its tile with bit 0 exchanged with one of its
-// next three lowest non-target bits (the tile maps onto itself and the
-// stores stay coalesced), so the state is then stored with two qubits'
-// index bits exchanged.  Over each run of consecutive 6-qubit passes a
-// dynamic program over the states {standard order} and {qubits 0 and a
-// exchanged} picks the exchanges that leave the fewest passes with bit 0
-// among their physical targets (those passes gather 16-byte pairs along
-// bit 0, the slower form), starting and ending the run in standard order.
-// Each pass's qubits become physical bits (its matrix reordered to match).
-static void place_bit0_run(int n, std::vector<Pass>& passes, size_t i0, size_t i1) {
-    const int K = (int)(i1 - i0), S = n + 1;   // state index s + 1; s = -1: standard order
+// The dynamic program of the bit-0 placement over a run of 6-qubit passes
+// (described below), from state s0 (-1 standard order, else the bit that
+// qubit 0's index bit is exchanged with); end_free: the run may end in any
+// state.  choice[k]: -2 keep, -1 restore, else the new exchange bit.
+// Returns the number of passes left with bit 0 a target, or -1 if the run
+// cannot end in standard order.
+int bit0_plan(int n, const std::vector<const Pass*>& run, int s0, bool end_free, std::vector<int>& choice) {
+    const int K = (int)run.size(), S = n + 1;   // state index s + 1; s = -1: standard order
     auto phys = [](int s, int x) { return s < 0 ? x : x == 0 ? s : x == s ? 0 : x; };
     std::vector<uint64_t> T(K, 0);
     for (int k = 0; k < K; ++k)
-        for (int i = 0; i < passes[i0 + k].k; ++i) T[k] |= 1ull << passes[i0 + k].qubits[i];
+        for (int i = 0; i < run[k]->k; ++i) T[k] |= 1ull << run[k]->qubits[i];
     auto ptargets = [&](int k, int s) {
         uint64_t m = 0;
         for (int x = 0; x < n; ++x)
@@ -1288,15 +1282,16 @@ static void place_bit0_run(int n, std::vector<Pass>& passes, size_t i0, size_t i
         return cnt;
     };
     const int INF = 1 << 28;
-    std::vector<int> cost((size_t)(K + 1) * S, INF), choice((size_t)K * S, -2);  // -2 keep, -1 back, else new a
-    cost[(size_t)K * S] = 0;
+    std::vector<int> cost((size_t)(K + 1) * S, INF), ch((size_t)K * S, -2);  // -2 keep, -1 back, else new a
+    for (int idx = 0; idx < S; ++idx)
+        if (end_free || idx == 0) cost[(size_t)K * S + idx] = 0;
     for (int k = K - 1; k >= 0; --k)
         for (int idx = 0; idx < S; ++idx) {
             const int s = idx - 1;
             if (s == 0) continue;
             const uint64_t pt = ptargets(k, s);
             const int q0t = (int)(pt & 1);
-            int best = q0t + cost[(size_t)(k + 1) * S + idx], bc = -2;
+            int best = std::min(INF, q0t + cost[(size_t)(k + 1) * S + idx]), bc = -2;
             if (!q0t) {
                 int c[3];
                 const int cnt = candidates(pt, c);
@@ -1317,24 +1312,55 @@ static void place_bit0_run(int n, std::vector<Pass>& passes, size_t i0, size_t i
                 }
             }
             cost[(size_t)k * S + idx] = best;
-            choice[(size_t)k * S + idx] = bc;
+            ch[(size_t)k * S + idx] = bc;
         }
-    int s = -1;
-    for (int k = 0; k < K; ++k) {
-        Pass& p = passes[i0 + k];
-        const int bc = choice[(size_t)k * S + s + 1];
-        for (int i = 0; i < p.k; ++i) p.qubits[i] = phys(s, p.qubits[i]);
-        sort_qubits_descending(p);
-        if (bc == -2) {
-            p.swap_p = -1;
-        } else if (bc == -1) {
-            p.swap_p = s;
-            s = -1;
-        } else {
-            p.swap_p = bc;
-            s = bc;
-        }
+    const int total = cost[(size_t)s0 + 1];
+    choice.assign(K, -2);
+    int s = s0;
+    for (int k = 0; k < K && total < INF; ++k) {
+        const int bc = ch[(size_t)k * S + s + 1];
+        choice[k] = bc;
+        s = bc == -2 ? s : bc == -1 ? -1 : bc;
     }
+    return total < INF ? total : -1;
+}
+
+int bit0_apply(Pass& p, int s, int bc) {
+    auto phys = [](int s, int x) { return s < 0 ? x : x == 0 ? s : x == s ? 0 : x; };
+    for (int i = 0; i < p.k; ++i) p.qubits[i] = phys(s, p.qubits[i]);
+    sort_qubits_descending(p);
+    if (bc == -2) {
+        p.swap_p = -1;
+        return s;
+    }
+    if (bc == -1) {
+        p.swap_p = s;
+        return -1;
+    }
+    p.swap_p = bc;
+    return bc;
+}
+
+// Qubit 0 out of the targets of 6-qubit tensor-core passes: a reordering of
+// index bits, the GPU form of the paper's bit-permuting recursive transform
+// (Section 5.1), folded into passes that run anyway.  A pass whose targets
+// leave bit 0 free may write its tile with bit 0 exchanged with one of its
+// next three lowest non-target bits (the tile maps onto itself and the
+// stores stay coalesced), so the state is then stored with two qubits'
+// index bits exchanged.  Over each run of consecutive 6-qubit passes a
+// dynamic program over the states {standard order} and {qubits 0 and a
+// exchanged} (bit0_plan) picks the exchanges that leave the fewest passes
+// with bit 0 among their physical targets (those passes gather 16-byte
+// pairs along bit 0, the slower form), starting and ending the run in
+// standard order.  Each pass's qubits become physical bits (its matrix
+// reordered to match).
+static void place_bit0_run(int n, std::vector<Pass>& passes, size_t i0, size_t i1) {
+    std::vector<const Pass*> run;
+    for (size_t i = i0; i < i1; ++i) run.push_back(&passes[i]);
+    std::vector<int> choice;
+    if (bit0_plan(n, run, -1, false, choice) < 0) return;   // cannot happen: keeping standard order is feasible
+    int s = -1;
+    for (size_t i = i0; i < i1; ++i) s = bit0_apply(passes[i], s, choice[i - i0]);
 }
 
 static void place_bit0(int n, std::vector<Pass>& passes) {

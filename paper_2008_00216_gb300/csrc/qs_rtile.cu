@@ -29,6 +29,7 @@
 #include <type_traits>
 
 #include "qs_device.cuh"
+#include "qs_ff.cuh"
 #include "qs_internal.h"
 #include "qs_tile.cuh"
 
@@ -360,131 +361,8 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile(typename C2<R>::T* __re
 }
 
 // ---------------------------------------------------------------- complex128
-// Complex128 tiles in float-float arithmetic: each amplitude d is held as
-// hi + lo with hi = float(d) and lo = float(d - hi) (about 48 significant
-// bits), and every product and sum runs on the FP32 pipe with error-free
-// transformations (FMA-based TwoProd, Knuth's TwoSum), accumulating the
-// rounding errors of a sum of products in a second float.  Only the loads
-// and stores convert to and from FP64.
-struct FFC {
-    float2 h, l;   // (re, im) high parts, (re, im) low parts
-};
-// d = hi + lo with integer operations only (the FP64 pipe is the scarce one):
-// hi keeps the top 24 significant bits (truncated), lo the next 29 rounded
-// to 24 (total relative error below 2^-48).  Magnitudes whose low part would
-// leave float's normal range (zeros, |d| < 2^-74, |d| >= 2^128) take the
-// plain FP64 conversion.
-__device__ __forceinline__ void ff_split(double d, float& hi, float& lo) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    const int e = (int)((b >> 52) & 0x7FFu) - 1023;
-    if (e < -74 || e > 127) {
-        hi = (float)d;
-        lo = (float)(d - (double)hi);
-        return;
-    }
-    const unsigned sign = (unsigned)(b >> 63) << 31;
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29));
-    const unsigned r = (unsigned)(m & 0x1FFFFFFFu);            // r * 2^(e - 52)
-    const float lm = __uint2float_rn(r) * __uint_as_float((unsigned)(e - 52 + 127) << 23);
-    lo = sign ? -lm : lm;
-}
-// hi + lo to FP64 with integer operations: hi + lo needs at most 49
-// significant bits when |lo| <= ulp(hi) (as after ffa_get), so it is
-// summed exactly in 64-bit fixed point at hi's scale and normalised.
-__device__ __forceinline__ double ff_merge(float hi, float lo) {
-    const unsigned hb = __float_as_uint(hi), lb = __float_as_uint(lo);
-    const int eh = (int)((hb >> 23) & 0xFFu), el = (int)((lb >> 23) & 0xFFu);
-    if (eh == 0 || eh == 255 || el == 255 || (el != 0 && eh - el > 60)) return (double)hi + (double)lo;
-    // 53-bit fixed point: value = T * 2^(eh - 127 - 52)
-    long long T = (long long)((hb & 0x7FFFFFu) | 0x800000u) << 29;
-    if (el != 0) {
-        const long long L = (long long)((lb & 0x7FFFFFu) | 0x800000u);
-        const int sh = 29 - (eh - el);
-        const long long Ls = sh >= 0 ? (L << sh) : (L >> (-sh));
-        T += ((hb ^ lb) >> 31) ? -Ls : Ls;
-    }
-    if (T <= 0) return (double)hi + (double)lo;   // cannot happen for |lo| <= ulp(hi)
-    // normalise to a 53-bit significand: leading bit at position 52
-    const int lead = 63 - __clzll(T);
-    int ex = eh - 127 + (lead - 52);
-    unsigned long long M = (unsigned long long)T;
-    M = lead >= 52 ? (M >> (lead - 52)) : (M << (52 - lead));   // lead > 52 drops no set bits here (sum of 49 bits)
-    const unsigned long long bits = ((unsigned long long)(hb >> 31) << 63) | ((unsigned long long)(ex + 1023) << 52) |
-                                    (M & 0xFFFFFFFFFFFFFull);
-    return __longlong_as_double((long long)bits);
-}
-__device__ __forceinline__ FFC ff_from(double2 d) {
-    FFC r;
-    ff_split(d.x, r.h.x, r.l.x);
-    ff_split(d.y, r.h.y, r.l.y);
-    return r;
-}
-__device__ __forceinline__ double2 ff_to(const FFC& v) { return make_double2(ff_merge(v.h.x, v.l.x), ff_merge(v.h.y, v.l.y)); }
-struct FFAcc {
-    float sr, er, si, ei;   // running sums of high parts and of everything else
-};
-__device__ __forceinline__ FFAcc ffa_zero() { return FFAcc{0.f, 0.f, 0.f, 0.f}; }
-// S + E += (ah + al)(bh + bl), dropping al * bl (2^-48 relative)
-__device__ __forceinline__ void ffa_term(float& S, float& E, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
-    float e = fmaf(ah, bh, -p);
-    e = fmaf(ah, bl, e);
-    e = fmaf(al, bh, e);
-    float s, t;
-    two_sum(S, p, s, t);
-    S = s;
-    E += t + e;
-}
-__device__ __forceinline__ void ffa_cmac(FFAcc& a, const FFC& m, const FFC& v) {
-    ffa_term(a.sr, a.er, m.h.x, m.l.x, v.h.x, v.l.x);
-    ffa_term(a.sr, a.er, -m.h.y, -m.l.y, v.h.y, v.l.y);
-    ffa_term(a.si, a.ei, m.h.x, m.l.x, v.h.y, v.l.y);
-    ffa_term(a.si, a.ei, m.h.y, m.l.y, v.h.x, v.l.x);
-}
-__device__ __forceinline__ void ffa_add(FFAcc& a, const FFC& v) {
-    float s, t;
-    two_sum(a.sr, v.h.x, s, t);
-    a.sr = s;
-    a.er += t + v.l.x;
-    two_sum(a.si, v.h.y, s, t);
-    a.si = s;
-    a.ei += t + v.l.y;
-}
-__device__ __forceinline__ FFC ffa_get(const FFAcc& a) {
-    FFC r;
-    r.h.x = a.sr + a.er;
-    r.l.x = a.er - (r.h.x - a.sr);
-    r.h.y = a.si + a.ei;
-    r.l.y = a.ei - (r.h.y - a.si);
-    return r;
-}
-__device__ __forceinline__ FFC ff_rot(const FFC& v, int code) {   // i^code v
-    FFC r;
-    r.h = rot_i(v.h, code);
-    r.l = rot_i(v.l, code);
-    return r;
-}
-__device__ __forceinline__ FFC ff_cmul(const FFC& m, const FFC& v) {
-    FFAcc a = ffa_zero();
-    ffa_cmac(a, m, v);
-    return ffa_get(a);
-}
-// out = i^ca a + i^cb b, a zero code (-1) dropping its term: additions only
-__device__ __forceinline__ FFC ff_mulfree_sum(const FFC& a, int ca, const FFC& b, int cb) {
-    FFAcc acc = ffa_zero();
-    if (ca >= 0) ffa_add(acc, ff_rot(a, ca));
-    if (cb >= 0) ffa_add(acc, ff_rot(b, cb));
-    return ffa_get(acc);
-}
-__device__ __forceinline__ FFC ff_shfl_xor(const FFC& v, int mask) {
-    FFC r;
-    r.h.x = __shfl_xor_sync(0xffffffffu, v.h.x, mask);
-    r.h.y = __shfl_xor_sync(0xffffffffu, v.h.y, mask);
-    r.l.x = __shfl_xor_sync(0xffffffffu, v.l.x, mask);
-    r.l.y = __shfl_xor_sync(0xffffffffu, v.l.y, mask);
-    return r;
-}
+// (float-float helpers: qs_ff.cuh)
+
 
 template <int RB, int r>
 __device__ __forceinline__ void ff_gate1(FFC (&v)[1 << RB], const FFC* m, int mulfree) {
@@ -498,36 +376,43 @@ __device__ __forceinline__ void ff_gate1(FFC (&v)[1 << RB], const FFC* m, int mu
             v[j0] = ff_mulfree_sum(x, c00, y, c01);
             v[j1] = ff_mulfree_sum(x, c10, y, c11);
         } else {
-            FFAcc a0 = ffa_zero(), a1 = ffa_zero();
-            ffa_cmac(a0, m[0], x);
-            ffa_cmac(a0, m[1], y);
-            ffa_cmac(a1, m[2], x);
-            ffa_cmac(a1, m[3], y);
-            v[j0] = ffa_get(a0);
-            v[j1] = ffa_get(a1);
+            v[j0] = ff_cmac2(m[0], x, m[1], y);
+            v[j1] = ff_cmac2(m[2], x, m[3], y);
         }
     }
 }
+// A k-qubit gate (k = 2..RB) on register bits 0..k-1.  Its rows run in a
+// loop that is not unrolled (unrolled, the gate sizes together overflowed the
+// instruction cache and instruction fetch became the top stall); each row's
+// outputs go to the thread's own scratch slots in shared memory, read back
+// once the gate is done.
 template <int RB, int K>
-__device__ __forceinline__ void ff_gate(FFC (&v)[1 << RB], const FFC* m) {
+__device__ __forceinline__ void ff_gate(FFC (&v)[1 << RB], const FFC* m, float4* scr) {
     constexpr int D = 1 << K, S = 1 << (RB - K);
-    FFC nv[1 << RB];
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < D; ++r) {
         FFAcc acc[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) acc[s] = ffa_zero();
+        const FFC* mr = m + r * D;
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            const FFC mm = m[r * D + l];
+            const FFC mm = mr[l];
 #pragma unroll
             for (int s = 0; s < S; ++s) ffa_cmac(acc[s], mm, v[(s << K) | l]);
         }
 #pragma unroll
-        for (int s = 0; s < S; ++s) nv[(s << K) | r] = ffa_get(acc[s]);
+        for (int s = 0; s < S; ++s) {
+            const FFC o = ffa_get(acc[s]);
+            scr[((s << K) | r) * kRTThreads] = make_float4(o.h.x, o.h.y, o.l.x, o.l.y);
+        }
     }
 #pragma unroll
-    for (int j = 0; j < (1 << RB); ++j) v[j] = nv[j];
+    for (int j = 0; j < (1 << RB); ++j) {
+        const float4 w = scr[j * kRTThreads];
+        v[j].h = make_float2(w.x, w.y);
+        v[j].l = make_float2(w.z, w.w);
+    }
 }
 
 template <int RB>
@@ -536,7 +421,8 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile_ff(double2* __restrict_
     constexpr int PER = 1 << RB, L = RB + 8;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float4* buf = reinterpret_cast<float4*>(smem_raw);            // 2^L: transposes, (h.x, h.y, l.x, l.y)
-    FFC* smat = reinterpret_cast<FFC*>(buf + (1u << L));          // the pass's matrices, float-float
+    float4* scr = buf + (1u << L) + threadIdx.x;                  // PER x kRTThreads: this thread's gate outputs
+    FFC* smat = reinterpret_cast<FFC*>(buf + (1u << L) + PER * kRTThreads);   // the pass's matrices, float-float
     const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
     for (uint32_t i = tid; i < a.mat_elems; i += kRTThreads) smat[i] = ff_from(mats[i]);
     __syncthreads();
@@ -670,10 +556,7 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile_ff(double2* __restrict_
 #pragma unroll
                     for (int j = 0; j < PER; ++j) {
                         const FFC pv = ff_shfl_xor(cur[j], 1 << b);
-                        FFAcc acc = ffa_zero();
-                        ffa_cmac(acc, co, cur[j]);
-                        ffa_cmac(acc, cp, pv);
-                        cur[j] = ffa_get(acc);
+                        cur[j] = ff_cmac2(co, cur[j], cp, pv);
                     }
                 }
             } else if (op.type == RT_GATE1) {
@@ -684,8 +567,8 @@ __global__ void __launch_bounds__(kRTThreads, 2) k_rtile_ff(double2* __restrict_
                     default: ff_gate1<RB, RB - 1>(cur, m, op.mulfree); break;
                 }
             } else {  // RT_GATE, k = 2..RB
-                if (op.k == 2) ff_gate<RB, 2>(cur, smat + op.mat);
-                else ff_gate<RB, 3>(cur, smat + op.mat);
+                if (op.k == 2) ff_gate<RB, 2>(cur, smat + op.mat, scr);
+                else ff_gate<RB, 3>(cur, smat + op.mat, scr);
             }
         }
         const uint64_t b = tile_base(tile) | st_thr;
@@ -737,7 +620,7 @@ cudaError_t launch_rtile(void* psi, int n, qs_dtype dt, const Pass& ps, const vo
         a.scale_c[1] = mag * sin(ang);
         a.scale_mode = 2;
     }
-    const size_t smem = 16 * ((size_t)1 << 11) + 16 * (size_t)a.mat_elems;
+    const size_t smem = 16 * ((size_t)1 << 11) + 16 * (size_t)8 * kRTThreads + 16 * (size_t)a.mat_elems;
     cudaError_t e = allow_max_dynamic_smem(k_rtile_ff<3>);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms() * 2);

@@ -18,13 +18,16 @@
 // Stage members commute, so each G1's gradient may be taken after the
 // inverses of the stage's other members.  Per tile, each gradient is one
 // value per thread, staged in shared memory and summed over the block in a
-// fixed order (in the state's precision within a tile, FP64 across tiles):
-// deterministic.
+// fixed order: complex64 with error-free TwoSum steps into a (sum, error)
+// float pair, FP64 from the tile's sum on across tiles; deterministic.
+// Complex64 runs k_sweep_pass<float>; complex128 runs k_sweep_pass_ff, the
+// same pass in float-float arithmetic on the FP32 pipe.
 #include <stdint.h>
 
 #include <algorithm>
 
 #include "qs_device.cuh"
+#include "qs_ff.cuh"
 #include "qs_internal.h"
 
 namespace qsgb {
@@ -76,11 +79,15 @@ __host__ __device__ constexpr uint32_t swz(uint32_t e) {
     return e ^ ((e >> SW) & ((1u << SW) - 1u));
 }
 
+// A transpose needs one barrier, between its writes and its reads.  A slot
+// belongs to one tile element, so the slots a thread writes (its elements
+// in the current layout) are exactly the slots it alone read in the
+// previous transpose, which brought it into this layout (tiles start and
+// end in layout 0): no other thread can still be reading them.
 template <typename T, int L, int SW, int AF, int AT>
 __device__ __forceinline__ void transpose_ct(T* buf, T (&ps)[1 << (L - 8)], T (&ls)[1 << (L - 8)]) {
     constexpr int RB = L - 8, PER = 1 << RB;
     const uint32_t s0 = swz<SW>(layout_base<RB>(threadIdx.x, AF)), s1 = swz<SW>(layout_base<RB>(threadIdx.x, AT));
-    __syncthreads();  // earlier readers of buf are done
 #pragma unroll
     for (int j = 0; j < PER; ++j) {
         const uint32_t s = s0 ^ swz<SW>((uint32_t)j << AF);
@@ -96,16 +103,49 @@ __device__ __forceinline__ void transpose_ct(T* buf, T (&ps)[1 << (L - 8)], T (&
     }
 }
 
+// Complex64: psi and lambda of one tile element share a 16-byte slot, so a
+// transpose moves both with one 128-bit store and one 128-bit load per
+// element.  A 128-bit access is served in four phases of 8 lanes; the slot's
+// low 3 bits (its 16-byte bank group) are XORed with tile bits 4..6, which
+// makes the 8 lanes of every phase hit 8 different groups in all three
+// layouts (in layouts 0 and 1 they differ in tile bits 0..2; in layout 2 in
+// tile bits 4..6).  Linear over XOR like swz, so a slot is the thread's base
+// slot XOR a constant.
+__host__ __device__ constexpr uint32_t swz16(uint32_t e) { return e ^ ((e >> 4) & 7u); }
+
+template <int L, int AF, int AT>
+__device__ __forceinline__ void transpose_pl(float4* buf, float2 (&ps)[1 << (L - 8)], float2 (&ls)[1 << (L - 8)]) {
+    constexpr int RB = L - 8, PER = 1 << RB;
+    const uint32_t s0 = swz16(layout_base<RB>(threadIdx.x, AF)), s1 = swz16(layout_base<RB>(threadIdx.x, AT));
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+        buf[s0 ^ swz16((uint32_t)j << AF)] = make_float4(ps[j].x, ps[j].y, ls[j].x, ls[j].y);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const float4 v = buf[s1 ^ swz16((uint32_t)j << AT)];
+        ps[j] = make_float2(v.x, v.y);
+        ls[j] = make_float2(v.z, v.w);
+    }
+}
+
+template <typename R, int AF, int AT>
+__device__ __forceinline__ void transpose_to(typename C2<R>::T* buf, typename C2<R>::T (&ps)[1 << (SweepShape<R>::L - 8)],
+                                             typename C2<R>::T (&ls)[1 << (SweepShape<R>::L - 8)]) {
+    using S = SweepShape<R>;
+    if constexpr (sizeof(R) == 4) transpose_pl<S::L, AF, AT>(reinterpret_cast<float4*>(buf), ps, ls);
+    else transpose_ct<typename C2<R>::T, S::L, S::SW, AF, AT>(buf, ps, ls);
+}
+
 template <typename R, int F>
 __device__ __forceinline__ void transpose_from(typename C2<R>::T* buf, typename C2<R>::T (&ps)[1 << (SweepShape<R>::L - 8)],
                                                typename C2<R>::T (&ls)[1 << (SweepShape<R>::L - 8)], int to) {
     using S = SweepShape<R>;
-    using T = typename C2<R>::T;
     switch (to) {
-        case 0: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(0)>(buf, ps, ls); break;
-        case 1: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(1)>(buf, ps, ls); break;
-        case 2: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(2)>(buf, ps, ls); break;
-        default: transpose_ct<T, S::L, S::SW, S::lay(F), S::lay(S::NLAY - 1)>(buf, ps, ls); break;
+        case 0: transpose_to<R, S::lay(F), S::lay(0)>(buf, ps, ls); break;
+        case 1: transpose_to<R, S::lay(F), S::lay(1)>(buf, ps, ls); break;
+        case 2: transpose_to<R, S::lay(F), S::lay(2)>(buf, ps, ls); break;
+        default: transpose_to<R, S::lay(F), S::lay(S::NLAY - 1)>(buf, ps, ls); break;
     }
 }
 
@@ -223,6 +263,28 @@ __device__ __forceinline__ auto g1_any(T (&ps)[1 << RB], T (&ls)[1 << RB], const
     }
 }
 
+// One-qubit gates of one form on register bits 0 .. RB-1 in that order (they
+// commute: one stage), coefficients m, m + 4, ...: one dispatch, and the
+// gates' arithmetic in one basic block.  Gradients in g[0 .. RB-1].
+template <typename T, int RB, int V>
+__device__ __forceinline__ void g1_seq(T (&ps)[1 << RB], T (&ls)[1 << RB], const T* m, int gen,
+                                       decltype(T{}.x) (&g)[RB]) {
+    g[0] = g1<T, RB, 0, V>(ps, ls, m, gen);
+    g[1] = g1<T, RB, 1, V>(ps, ls, m + 4, gen);
+    g[2] = g1<T, RB, 2, V>(ps, ls, m + 8, gen);
+    if constexpr (RB == 4) g[3] = g1<T, RB, 3, V>(ps, ls, m + 12, gen);
+}
+
+template <typename T, int RB>
+__device__ __forceinline__ void g1_all(T (&ps)[1 << RB], T (&ls)[1 << RB], const T* m, int form, int gen,
+                                       decltype(T{}.x) (&g)[RB]) {
+    switch (form) {
+        case G1_RSHEAR_Y: g1_seq<T, RB, G1_RSHEAR_Y>(ps, ls, m, gen, g); break;
+        case G1_RSHEAR: g1_seq<T, RB, G1_RSHEAR>(ps, ls, m, gen, g); break;
+        default: g1_seq<T, RB, G1_CSHEAR_X>(ps, ls, m, gen, g); break;
+    }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* __restrict__ psi,
                                                             typename C2<R>::T* __restrict__ lam,
@@ -238,11 +300,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* buf = reinterpret_cast<T*>(smem_raw);                                    // 2 x 2^L (psi, lambda)
     T* tab = buf + 2 * (1u << L);                                               // a.tab_elems
-    R* gs = reinterpret_cast<R*>(tab + a.tab_elems);                            // kRows x kThreads
-    double* red = reinterpret_cast<double*>(gs + kRows * kThreads);             // a.ngrad (even count: 16-byte alignment below)
+    R* gs = reinterpret_cast<R*>(tab + a.tab_elems);                            // 2 banks x kRows x kThreads
+    double* red = reinterpret_cast<double*>(gs + 2 * kRows * kThreads);         // a.ngrad (even count: 16-byte alignment below)
     uint64_t* xo = reinterpret_cast<uint64_t*>(red + ((a.ngrad + 1) & ~1));    // PER: byte offset of j
-    R* dred = reinterpret_cast<R*>(xo + PER);                                   // 8 warps x (6 + RB)
-    T* cm = reinterpret_cast<T*>(dred + (kThreads / 32) * (6 + RB));            // 4 x a.nmat coefficients
+    R* dred = reinterpret_cast<R*>(xo + PER);                                   // 8 warps x (6 + RB) x (sum, error)
+    T* cm = reinterpret_cast<T*>(dred + 2 * (kThreads / 32) * (6 + RB));        // 4 x a.nmat coefficients
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = tabs[i];
     for (int i = tid; i < 4 * a.nmat; i += kThreads) cm[i] = mats[i];
@@ -259,30 +321,56 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         return x;
     };
     const uint64_t xg0 = global_of(layout_base<RB>(tid, S::lay(0)));  // the thread's bits, natural layout
+    const uint64_t xl0 = global_of(layout_base<RB>(tid, 0));          // the thread's bits, low layout
+    auto tile_base = [&](uint64_t t) {
+        for (int i = 0; i < L; ++i) t = insert_zero(t, a.pos[i]);
+        return t;
+    };
     __syncthreads();
 
     int gdone = 0, srow = 0;  // gradients of this tile already added to red; rows staged since
-    auto flush = [&]() {  // block-uniform: add the staged rows to red
+    // block-uniform: add the staged rows to red.  Complex64: each row's 256
+    // values are summed with error-free TwoSum steps into a float pair (sum,
+    // rounding errors), so the tile's sum reaches FP64 as if it had been
+    // accumulated there; complex128 sums in FP64 throughout.
+    // The rows are double-buffered: staging goes on in the other bank while
+    // slower threads still read this one, so the flush needs no barrier at
+    // its end (the next flush's barrier orders this bank's reuse).
+    int bank = 0;
+    auto flush = [&]() {
         __syncthreads();
         const int row = tid / TPR, part = tid % TPR;
-        R v = 0;
+        const R* gb = gs + bank * kRows * kThreads;
+        if constexpr (sizeof(R) == 4) {
+            F2Acc v;
 #pragma unroll
-        for (int k = 0; k < kThreads / TPR; ++k) v += gs[row * kThreads + part + TPR * k];
+            for (int k = 0; k < kThreads / TPR; ++k) v.add(gb[row * kThreads + part + TPR * k]);
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
-        if (part == 0 && row < srow) red[gdone + row] += (double)v;
+            for (int o = TPR / 2; o > 0; o >>= 1) {
+                const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR), l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
+                v.add(h);
+                v.lo += l;
+            }
+            if (part == 0 && row < srow) red[gdone + row] += (double)v.hi + (double)v.lo;
+        } else {
+            R v = 0;
+#pragma unroll
+            for (int k = 0; k < kThreads / TPR; ++k) v += gb[row * kThreads + part + TPR * k];
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
+            if (part == 0 && row < srow) red[gdone + row] += (double)v;
+        }
         gdone += srow;
         srow = 0;
-        __syncthreads();
+        bank ^= 1;
     };
     auto stage = [&](R v) {
-        gs[srow * kThreads + tid] = v;
+        gs[(bank * kRows + srow) * kThreads + tid] = v;
         if (++srow == kRows) flush();
     };
 
+    uint64_t base = tile_base(blockIdx.x);
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        uint64_t base = tile;
-        for (int i = 0; i < L; ++i) base = insert_zero(base, a.pos[i]);
         T ps[PER], ls[PER];
         {
             const char* pp = reinterpret_cast<const char*>(psi) + (base | xg0) * sizeof(T);
@@ -295,9 +383,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
             }
         }
         // the next tile of psi and lambda on its way into L2 while this one is processed
+        uint64_t nb = 0;
         if (tile + gridDim.x < a.ntiles) {
-            uint64_t nb = tile + gridDim.x;
-            for (int i = 0; i < L; ++i) nb = insert_zero(nb, a.pos[i]);
+            nb = tile_base(tile + gridDim.x);
             const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(T);
             const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(T);
 #pragma unroll
@@ -316,10 +404,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
             } else if (op.type == SWEEP_G1) {
                 const R v = g1_any<T, RB>(ps, ls, cm + 4 * op.idx, op.arg, op.form, op.gen);
                 if (op.gen) stage(v);
+            } else if (op.type == SWEEP_G1ALL) {
+                R g[RB];
+                g1_all<T, RB>(ps, ls, cm + 4 * op.idx, op.form, op.gen, g);
+                if (op.gen)
+#pragma unroll
+                    for (int i = 0; i < RB; ++i) stage(g[i]);
             } else {  // DIAG, in the low layout: register index j = bits 0 .. RB-1 of the index
                 const SweepDiagRec d = a.diag[op.idx];
                 const T* dtab = tab + d.tab;
-                const uint64_t xt = base | global_of(layout_base<RB>(tid, 0));
+                const uint64_t xt = base | xl0;
                 T pc;  // chunks 1.. and the cross gates without a register qubit
                 pc.x = 1;
                 pc.y = 0;
@@ -359,26 +453,46 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 }
                 if (d.ngen > d.nstaged) {  // block generators: warp sums of S, W_b (lane bits), U_k
                     const int lane = tid & 31, warp = tid >> 5;
+                    // warp sums as (sum, rounding errors) pairs for complex64
+                    // (TwoSum steps), then FP64 across the warps
 #pragma unroll
                     for (int i = 0; i < 6 + RB; ++i) {
-                        R w = i == 0 ? tsum : i < 6 ? (((lane >> (i - 1)) & 1) ? tsum : (R)0) : u[i < 6 ? 0 : i - 6];
+                        const R w0 = i == 0 ? tsum : i < 6 ? (((lane >> (i - 1)) & 1) ? tsum : (R)0) : u[i < 6 ? 0 : i - 6];
+                        R hi = w0, lo = 0;
+                        if constexpr (sizeof(R) == 4) {
+                            F2Acc w;
+                            w.hi = w0;
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-                        if (lane == 0) dred[warp * (6 + RB) + i] = w;
+                            for (int o = 16; o > 0; o >>= 1) {
+                                const float h = __shfl_xor_sync(0xffffffffu, w.hi, o), l = __shfl_xor_sync(0xffffffffu, w.lo, o);
+                                w.add(h);
+                                w.lo += l;
+                            }
+                            hi = w.hi;
+                            lo = w.lo;
+                        } else {
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
+                        }
+                        if (lane == 0) {
+                            dred[2 * (warp * (6 + RB) + i)] = hi;
+                            dred[2 * (warp * (6 + RB) + i) + 1] = lo;
+                        }
                     }
                     __syncthreads();
                     for (int g = d.nstaged + tid; g < d.ngen; g += kThreads) {
                         const SweepZGen z = a.gens[d.gen0 + g];
-                        R S = 0, X = 0;
+                        double S = 0, X = 0;
                         for (int q = 0; q < kThreads / 32; ++q) {  // fixed order
-                            const R* wq = dred + q * (6 + RB);
-                            S += wq[0];
-                            if (z.src >= 1 && z.src <= RB) X += wq[5 + z.src];
-                            else if (z.src > RB && z.src <= RB + 5) X += wq[z.src - RB];
-                            else if (z.src > RB + 5 && ((q >> (z.src - RB - 6)) & 1)) X += wq[0];
+                            const R* wq = dred + 2 * q * (6 + RB);
+                            auto at = [&](int i) { return (double)wq[2 * i] + (double)wq[2 * i + 1]; };
+                            S += at(0);
+                            if (z.src >= 1 && z.src <= RB) X += at(5 + z.src);
+                            else if (z.src > RB && z.src <= RB + 5) X += at(z.src - RB);
+                            else if (z.src > RB + 5 && ((q >> (z.src - RB - 6)) & 1)) X += at(0);
                         }
-                        const R v = S - 2 * X;
-                        red[z.local] += (double)((__popcll(base & z.mthr) & 1) ? -v : v);
+                        const double v = S - 2 * X;
+                        red[z.local] += (__popcll(base & z.mthr) & 1) ? -v : v;
                     }
                     __syncthreads();  // dred is reused by the next diagonal op
                 }
@@ -404,6 +518,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
             }
         }
         if (srow) flush();
+        base = nb;
     }
     __syncthreads();
     for (int s = tid; s < a.ngrad; s += kThreads) {
@@ -413,13 +528,406 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     }
 }
 
+// ------------------------------------------------------------ complex128
+// The complex128 sweep pass in float-float arithmetic (qs_ff.cuh): psi and
+// lambda are held as hi + lo floats in registers, every product and sum runs
+// on the FP32 pipe with error-free transformations, and only the loads and
+// stores convert to and from FP64.  Tile and layouts as the FP64 form (L = 11,
+// 3 register bits).  One-qubit ops take U^dagger's four entries (forms
+// G1_FF_REAL / G1_FF_CPLX) and always act on register bit 0: the thread's
+// registers are rotated (bit 0 <- bit 1 <- bit 2 <- bit 0) around the op, so
+// one copy of the gate code serves every register bit.
+struct FFV {
+    float h, l;  // a float-float real value
+};
+
+// rotate the 8 register elements: new index (j >> 1) | ((j & 1) << 2) takes old j
+__device__ __forceinline__ void ff_rotate(FFC (&v)[8]) {
+    const FFC t1 = v[1], t2 = v[2], t3 = v[3], t4 = v[4], t5 = v[5], t6 = v[6];
+    // old j -> new j': 1->4, 2->1, 3->5, 4->2, 5->6, 6->3 (0 and 7 stay)
+    v[4] = t1;
+    v[1] = t2;
+    v[5] = t3;
+    v[2] = t4;
+    v[6] = t5;
+    v[3] = t6;
+}
+
+// S + E += a * b for float-float reals (the ffa_term of qs_ff.cuh)
+__device__ __forceinline__ void ffv_term(float& S, float& E, float ah, float al, float bh, float bl) {
+    ffa_term(S, E, ah, al, bh, bl);
+}
+
+// One-qubit op on register bit 0: the gradient Im <l|P|p> over the thread's
+// 4 pairs (generator gen: 1 X, 2 Y, 3 Z), then (p0, p1) <- M (p0, p1) and the
+// same for lambda, M = the 4 entries m (real: imaginary parts zero).
+template <bool REAL>
+__device__ __forceinline__ FFV ff_g1_bit0(FFC (&ps)[8], FFC (&ls)[8], const FFC* m, int gen) {
+    float S = 0.f, E = 0.f;
+    const FFC m0 = m[0], m1 = m[1], m2 = m[2], m3 = m[3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        FFC& p0 = ps[2 * k];
+        FFC& p1 = ps[2 * k + 1];
+        FFC& l0 = ls[2 * k];
+        FFC& l1 = ls[2 * k + 1];
+        if (gen == 2) {  // Re(conj(l1) p0) - Re(conj(l0) p1)
+            ffv_term(S, E, l1.h.x, l1.l.x, p0.h.x, p0.l.x);
+            ffv_term(S, E, l1.h.y, l1.l.y, p0.h.y, p0.l.y);
+            ffv_term(S, E, -l0.h.x, -l0.l.x, p1.h.x, p1.l.x);
+            ffv_term(S, E, -l0.h.y, -l0.l.y, p1.h.y, p1.l.y);
+        } else if (gen == 1) {  // Im(conj(l0) p1) + Im(conj(l1) p0)
+            ffv_term(S, E, l0.h.x, l0.l.x, p1.h.y, p1.l.y);
+            ffv_term(S, E, -l0.h.y, -l0.l.y, p1.h.x, p1.l.x);
+            ffv_term(S, E, l1.h.x, l1.l.x, p0.h.y, p0.l.y);
+            ffv_term(S, E, -l1.h.y, -l1.l.y, p0.h.x, p0.l.x);
+        } else if (gen == 3) {  // Im(conj(l0) p0) - Im(conj(l1) p1)
+            ffv_term(S, E, l0.h.x, l0.l.x, p0.h.y, p0.l.y);
+            ffv_term(S, E, -l0.h.y, -l0.l.y, p0.h.x, p0.l.x);
+            ffv_term(S, E, -l1.h.x, -l1.l.x, p1.h.y, p1.l.y);
+            ffv_term(S, E, l1.h.y, l1.l.y, p1.h.x, p1.l.x);
+        }
+        if (REAL) {  // real entries: each output component a two-term sum
+            auto rmac = [](const FFC& ma, const FFC& a, const FFC& mb, const FFC& b) {
+                const float2 re = ff_dot2(ma.h.x, ma.l.x, a.h.x, a.l.x, mb.h.x, mb.l.x, b.h.x, b.l.x);
+                const float2 im = ff_dot2(ma.h.x, ma.l.x, a.h.y, a.l.y, mb.h.x, mb.l.x, b.h.y, b.l.y);
+                FFC r;
+                r.h = make_float2(re.x, im.x);
+                r.l = make_float2(re.y, im.y);
+                return r;
+            };
+            const FFC q0 = rmac(m0, p0, m1, p1), q1 = rmac(m2, p0, m3, p1);
+            const FFC k0 = rmac(m0, l0, m1, l1), k1 = rmac(m2, l0, m3, l1);
+            p0 = q0;
+            p1 = q1;
+            l0 = k0;
+            l1 = k1;
+        } else {
+            const FFC q0 = ff_cmac2(m0, p0, m1, p1), q1 = ff_cmac2(m2, p0, m3, p1);
+            const FFC k0 = ff_cmac2(m0, l0, m1, l1), k1 = ff_cmac2(m2, l0, m3, l1);
+            p0 = q0;
+            p1 = q1;
+            l0 = k0;
+            l1 = k1;
+        }
+    }
+    FFV g;
+    g.h = S + E;
+    g.l = E - (g.h - S);
+    return g;
+}
+
+__device__ __forceinline__ FFV ff_g1_any(FFC (&ps)[8], FFC (&ls)[8], const FFC* m, int form, int gen) {
+    return form == G1_FF_REAL ? ff_g1_bit0<true>(ps, ls, m, gen) : ff_g1_bit0<false>(ps, ls, m, gen);
+}
+
+// psi and lambda of the tile through shared memory (one 16-byte slot per
+// element and state, swizzled as the FP64 form); one barrier, as there
+__device__ __forceinline__ void ff_transpose(float4* buf, FFC (&ps)[8], FFC (&ls)[8], int af, int at) {
+    constexpr int L = kSweepTileC128, SW = 3;
+    const uint32_t s0 = swz<SW>(layout_base<3>(threadIdx.x, af)), s1 = swz<SW>(layout_base<3>(threadIdx.x, at));
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t s = s0 ^ swz<SW>((uint32_t)j << af);
+        buf[s] = make_float4(ps[j].h.x, ps[j].h.y, ps[j].l.x, ps[j].l.y);
+        buf[(1u << L) + s] = make_float4(ls[j].h.x, ls[j].h.y, ls[j].l.x, ls[j].l.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t s = s1 ^ swz<SW>((uint32_t)j << at);
+        const float4 a = buf[s], b = buf[(1u << L) + s];
+        ps[j].h = make_float2(a.x, a.y);
+        ps[j].l = make_float2(a.z, a.w);
+        ls[j].h = make_float2(b.x, b.y);
+        ls[j].l = make_float2(b.z, b.w);
+    }
+}
+
+// ph times the diagonal entries of `count` gates at index x (float-float tables)
+template <typename X>
+__device__ __forceinline__ FFC ff_cross_phase(const X* cg, int count, const FFC* tab, uint64_t x, FFC ph) {
+    for (int c = 0; c < count; ++c) {
+        uint32_t li = 0;
+        for (int i = 0; i < cg[c].k; ++i) li = (li << 1) | (uint32_t)((x >> cg[c].q[i]) & 1);
+        ph = ff_cmul(ph, tab[cg[c].tab + li]);
+    }
+    return ph;
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restrict__ psi, double2* __restrict__ lam,
+                                                              const double2* __restrict__ mats,
+                                                              const double2* __restrict__ tabs,
+                                                              const __grid_constant__ SweepArgs a,
+                                                              double* __restrict__ partials) {
+    constexpr int L = kSweepTileC128, RB = 3, PER = 8;
+    constexpr int kRows = 8, TPR = kThreads / kRows;  // staged rows of (hi, lo) gradients, threads per row
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float4* buf = reinterpret_cast<float4*>(smem_raw);                          // 2 x 2^L (psi, lambda)
+    FFC* tab = reinterpret_cast<FFC*>(buf + 2 * (1u << L));                     // a.tab_elems
+    FFC* cm = tab + a.tab_elems;                                                // 4 x a.nmat
+    float* gsh = reinterpret_cast<float*>(cm + 4 * a.nmat);                     // 2 banks x kRows x kThreads
+    float* gsl = gsh + 2 * kRows * kThreads;
+    float* dred = gsl + 2 * kRows * kThreads;                                   // 8 warps x (6 + RB) x (sum, error)
+    double* red = reinterpret_cast<double*>(dred + 2 * (kThreads / 32) * (6 + RB));   // a.ngrad
+    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // PER: byte offset of j
+    const uint32_t tid = threadIdx.x;
+    for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = ff_from(tabs[i]);
+    for (int i = tid; i < 4 * a.nmat; i += kThreads) cm[i] = ff_from(mats[i]);
+    for (int i = tid; i < a.ngrad; i += kThreads) red[i] = 0.0;
+    if (tid < PER) {  // natural layout: register bit k is tile bit L - RB + k
+        uint64_t o = 0;
+        for (int k = 0; k < RB; ++k)
+            if ((tid >> k) & 1) o |= 1ull << a.pos[L - RB + k];
+        xo[tid] = o * sizeof(double2);
+    }
+    auto global_of = [&](uint32_t e) {
+        uint64_t x = 0;
+        for (int i = 0; i < L; ++i) x |= (uint64_t)((e >> i) & 1u) << a.pos[i];
+        return x;
+    };
+    auto tile_base = [&](uint64_t t) {
+        for (int i = 0; i < L; ++i) t = insert_zero(t, a.pos[i]);
+        return t;
+    };
+    auto lay_a = [](int l) { return SweepShape<double>::lay(l); };   // register ranges 8, 5, 2, 0
+    const uint64_t xg0 = global_of(layout_base<RB>(tid, lay_a(0)));
+    const uint64_t xl0 = global_of(layout_base<RB>(tid, 0));
+    __syncthreads();
+
+    int gdone = 0, srow = 0, bank = 0;
+    // staged (hi, lo) rows summed with TwoSum steps, FP64 per row (double-
+    // buffered banks: no barrier at the end, as in the FP32/FP64 form)
+    auto flush = [&]() {
+        __syncthreads();
+        const int row = tid / TPR, part = tid % TPR;
+        const float* bh = gsh + bank * kRows * kThreads;
+        const float* bl = gsl + bank * kRows * kThreads;
+        F2Acc v;
+#pragma unroll
+        for (int k = 0; k < kThreads / TPR; ++k) {
+            v.add(bh[row * kThreads + part + TPR * k]);
+            v.add(bl[row * kThreads + part + TPR * k]);
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) {
+            const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR), l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
+            v.add(h);
+            v.lo += l;
+        }
+        if (part == 0 && row < srow) red[gdone + row] += (double)v.hi + (double)v.lo;
+        gdone += srow;
+        srow = 0;
+        bank ^= 1;
+    };
+    auto stage = [&](FFV v) {
+        gsh[(bank * kRows + srow) * kThreads + tid] = v.h;
+        gsl[(bank * kRows + srow) * kThreads + tid] = v.l;
+        if (++srow == kRows) flush();
+    };
+
+    uint64_t base = tile_base(blockIdx.x);
+    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        FFC ps[PER], ls[PER];
+        {
+            const char* pp = reinterpret_cast<const char*>(psi) + (base | xg0) * sizeof(double2);
+            const char* pl = reinterpret_cast<const char*>(lam) + (base | xg0) * sizeof(double2);
+            double2 dp[PER], dl[PER];
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                dp[j] = *reinterpret_cast<const double2*>(pp + xo[j]);
+                dl[j] = *reinterpret_cast<const double2*>(pl + xo[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                ps[j] = ff_from(dp[j]);
+                ls[j] = ff_from(dl[j]);
+            }
+        }
+        uint64_t nb = 0;
+        if (tile + gridDim.x < a.ntiles) {  // the next tile on its way into L2
+            nb = tile_base(tile + gridDim.x);
+            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(double2);
+            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(double2);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xo[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xo[j]));
+            }
+        }
+        int lay = 0;
+        gdone = 0;
+        for (int o = 0; o < a.nops; ++o) {
+            const SweepOpRec op = a.ops[o];
+            if (op.type == SWEEP_LAYOUT) {
+                ff_transpose(buf, ps, ls, lay_a(lay), lay_a(op.arg));
+                lay = op.arg;
+            } else if (op.type == SWEEP_G1 || op.type == SWEEP_G1ALL) {
+                // one call site for every register bit: rotate the gate's bit to 0
+                const int pre = op.type == SWEEP_G1 ? op.arg : 0, count = op.type == SWEEP_G1 ? 1 : RB;
+                for (int t = 0; t < pre; ++t) {
+                    ff_rotate(ps);
+                    ff_rotate(ls);
+                }
+#pragma unroll 1
+                for (int i = 0; i < count; ++i) {
+                    const FFV g = ff_g1_any(ps, ls, cm + 4 * (op.idx + i), op.form, op.gen);
+                    if (op.gen) stage(g);
+                    ff_rotate(ps);
+                    ff_rotate(ls);
+                }
+                for (int t = (pre + count) % RB; t != 0 && t < RB; ++t) {
+                    ff_rotate(ps);
+                    ff_rotate(ls);
+                }
+            } else {  // DIAG, in the low layout: register index j = bits 0 .. RB-1 of the index
+                const SweepDiagRec d = a.diag[op.idx];
+                const FFC* dtab = tab + d.tab;
+                const uint64_t xt = base | xl0;
+                FFC pc;  // chunks 1.. and the cross gates without a register qubit
+                pc.h = make_float2(1.f, 0.f);
+                pc.l = make_float2(0.f, 0.f);
+                for (int c = 1; c < d.nchunks; ++c) pc = ff_cmul(pc, dtab[256 * c + ((xt >> (8 * c)) & 255)]);
+                pc = ff_cross_phase(a.cross + d.cross0 + d.nct, d.ncross - d.nct, tab, xt, pc);
+                // Im(conj(l) p) per element as float-float, and the sums over
+                // the thread's elements (all, and those with register bit i set)
+                auto im_lp = [&](int j) {  // Im(conj(l_j) p_j)
+                    const float2 v = ff_dot2(ls[j].h.x, ls[j].l.x, ps[j].h.y, ps[j].l.y, -ls[j].h.y, -ls[j].l.y,
+                                             ps[j].h.x, ps[j].l.x);
+                    return FFV{v.x, v.y};
+                };
+                float ts = 0.f, te = 0.f, us[RB], ue[RB];
+#pragma unroll
+                for (int i = 0; i < RB; ++i) us[i] = ue[i] = 0.f;
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    const FFV t = im_lp(j);
+                    float s2, e2;
+                    two_sum(ts, t.h, s2, e2);
+                    ts = s2;
+                    te += e2 + t.l;
+#pragma unroll
+                    for (int i = 0; i < RB; ++i)
+                        if ((j >> i) & 1) {
+                            two_sum(us[i], t.h, s2, e2);
+                            us[i] = s2;
+                            ue[i] += e2 + t.l;
+                        }
+                }
+                for (int g = 0; g < d.nstaged; ++g) {
+                    const SweepZGen z = a.gens[d.gen0 + g];
+                    float S = ts, E = te;  // kind 0: the sum
+                    if (z.kind >= 1 && z.kind <= RB) {  // sum - 2 (sum over register bit set)
+                        const int i = z.kind - 1;
+                        const float uh = i == 0 ? us[0] : i == 1 ? us[1] : us[2];
+                        const float ul = i == 0 ? ue[0] : i == 1 ? ue[1] : ue[2];
+                        float s2, e2;
+                        two_sum(S, -2.f * uh, s2, e2);
+                        S = s2;
+                        E += e2 - 2.f * ul;
+                    } else if (z.kind > RB) {
+                        S = 0.f;
+                        E = 0.f;
+#pragma unroll
+                        for (int j = 0; j < PER; ++j) {
+                            const float sg = ((z.jmask >> j) & 1) ? -1.f : 1.f;
+                            const FFV t = im_lp(j);
+                            float s2, e2;
+                            two_sum(S, sg * t.h, s2, e2);
+                            S = s2;
+                            E += e2 + sg * t.l;
+                        }
+                    }
+                    FFV v;
+                    v.h = S + E;
+                    v.l = E - (v.h - S);
+                    if (__popcll(xt & z.mthr) & 1) {
+                        v.h = -v.h;
+                        v.l = -v.l;
+                    }
+                    stage(v);
+                }
+                if (d.ngen > d.nstaged) {  // block generators: warp sums of S, W_b (lane bits), U_k
+                    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+                    for (int i = 0; i < 6 + RB; ++i) {
+                        const bool on = i == 0 || i >= 6 || ((lane >> (i - 1)) & 1);
+                        F2Acc w;
+                        w.hi = !on ? 0.f : i < 6 ? ts : us[i - 6];
+                        w.lo = !on ? 0.f : i < 6 ? te : ue[i - 6];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) {
+                            const float h = __shfl_xor_sync(0xffffffffu, w.hi, o), l = __shfl_xor_sync(0xffffffffu, w.lo, o);
+                            w.add(h);
+                            w.lo += l;
+                        }
+                        if (lane == 0) {
+                            dred[2 * (warp * (6 + RB) + i)] = w.hi;
+                            dred[2 * (warp * (6 + RB) + i) + 1] = w.lo;
+                        }
+                    }
+                    __syncthreads();
+                    for (int g = d.nstaged + tid; g < d.ngen; g += kThreads) {
+                        const SweepZGen z = a.gens[d.gen0 + g];
+                        double S = 0, X = 0;
+                        for (int q = 0; q < kThreads / 32; ++q) {  // fixed order
+                            const float* wq = dred + 2 * q * (6 + RB);
+                            auto at = [&](int i) { return (double)wq[2 * i] + (double)wq[2 * i + 1]; };
+                            S += at(0);
+                            if (z.src >= 1 && z.src <= RB) X += at(5 + z.src);
+                            else if (z.src > RB && z.src <= RB + 5) X += at(z.src - RB);
+                            else if (z.src > RB + 5 && ((q >> (z.src - RB - 6)) & 1)) X += at(0);
+                        }
+                        const double v = S - 2 * X;
+                        red[z.local] += (__popcll(base & z.mthr) & 1) ? -v : v;
+                    }
+                    __syncthreads();  // dred is reused by the next diagonal op
+                }
+                const FFC* t0 = dtab + (xt & 255);  // chunk 0: the thread's bits, plus j
+#pragma unroll
+                for (int j = 0; j < PER; ++j) {
+                    FFC ph = ff_cmul(pc, t0[j]);
+                    if (d.nct) ph = ff_cross_phase(a.cross + d.cross0, d.nct, tab, xt | (uint64_t)j, ph);
+                    ps[j] = ff_cmul(ph, ps[j]);
+                    ls[j] = ff_cmul(ph, ls[j]);
+                }
+            }
+        }
+        if (lay != 0) ff_transpose(buf, ps, ls, lay_a(lay), lay_a(0));
+        {
+            char* pp = reinterpret_cast<char*>(psi) + (base | xg0) * sizeof(double2);
+            char* pl = reinterpret_cast<char*>(lam) + (base | xg0) * sizeof(double2);
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                *reinterpret_cast<double2*>(pp + xo[j]) = ff_to(ps[j]);
+                *reinterpret_cast<double2*>(pl + xo[j]) = ff_to(ls[j]);
+            }
+        }
+        if (srow) flush();
+        base = nb;
+    }
+    __syncthreads();
+    for (int s = tid; s < a.ngrad; s += kThreads) {
+        const size_t at = ((size_t)a.slot[s] * a.nb + blockIdx.x) * 2;
+        partials[at] = 0.0;
+        partials[at + 1] = red[s];
+    }
+}
+
+size_t sweep_smem_ff(const SweepArgs& a) {
+    constexpr int L = kSweepTileC128, RB = 3;
+    return 16 * (2 * ((size_t)1 << L) + a.tab_elems + 4 * (size_t)a.nmat) + sizeof(float) * 2 * 2 * 8 * kThreads +
+           sizeof(float) * 2 * (kThreads / 32) * (6 + RB) + sizeof(double) * (size_t)a.ngrad +
+           sizeof(uint64_t) * ((size_t)1 << RB);
+}
+
 template <typename R>
 size_t sweep_smem(const SweepArgs& a) {
     constexpr int L = SweepShape<R>::L;
     const size_t esz = sizeof(typename C2<R>::T);
-    return esz * (2 * ((size_t)1 << L) + a.tab_elems) + sizeof(R) * SweepShape<R>::ROWS * kThreads +
+    return esz * (2 * ((size_t)1 << L) + a.tab_elems) + sizeof(R) * 2 * SweepShape<R>::ROWS * kThreads +
            sizeof(double) * ((a.ngrad + 1) & ~1) + sizeof(uint64_t) * ((size_t)1 << (L - 8)) +
-           sizeof(R) * (kThreads / 32) * (6 + (L - 8)) + sizeof(typename C2<R>::T) * 4 * a.nmat;
+           sizeof(R) * 2 * (kThreads / 32) * (6 + (L - 8)) + sizeof(typename C2<R>::T) * 4 * a.nmat;
 }
 
 }  // namespace
@@ -475,8 +983,15 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
             if (op.arg >= nlay) return cudaErrorInvalidValue;
             cur = op.arg;
         } else if (op.type == SWEEP_G1) {
-            if (op.arg >= RB || op.idx >= nmat || op.gen > 3 || op.form >= G1_FORMS) return cudaErrorInvalidValue;
+            const bool ff = op.form == G1_FF_REAL || op.form == G1_FF_CPLX;
+            if (op.arg >= RB || op.idx >= nmat || op.gen > 3 || op.form >= G1_FORMS || ff != (dt == QS_C128))
+                return cudaErrorInvalidValue;
             grads += op.gen != 0;
+        } else if (op.type == SWEEP_G1ALL) {
+            const bool ok = dt == QS_C128 ? (op.form == G1_FF_REAL || op.form == G1_FF_CPLX)
+                                          : (op.form == G1_RSHEAR || op.form == G1_RSHEAR_Y || op.form == G1_CSHEAR_X);
+            if ((uint64_t)op.idx + RB > nmat || op.gen > 3 || !ok) return cudaErrorInvalidValue;
+            grads += op.gen != 0 ? RB : 0;
         } else if (op.type == SWEEP_DIAG) {
             if (op.idx >= p.diags.size() || cur != nlay - 1) return cudaErrorInvalidValue;  // the low layout
             const SweepDiagRec& d = p.diags[op.idx];
@@ -516,11 +1031,11 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
         if (e != cudaSuccess) return e;
         k_sweep_pass<float><<<grid, kThreads, sweep_smem<float>(a), st>>>(
             (float2*)psi, (float2*)lam, (const float2*)dmats, (const float2*)dtabs, a, partials);
-    } else {
-        cudaError_t e = allow_max_dynamic_smem(k_sweep_pass<double>);
+    } else {  // complex128: the float-float form
+        cudaError_t e = allow_max_dynamic_smem(k_sweep_pass_ff);
         if (e != cudaSuccess) return e;
-        k_sweep_pass<double><<<grid, kThreads, sweep_smem<double>(a), st>>>(
-            (double2*)psi, (double2*)lam, (const double2*)dmats, (const double2*)dtabs, a, partials);
+        k_sweep_pass_ff<<<grid, kThreads, sweep_smem_ff(a), st>>>((double2*)psi, (double2*)lam, (const double2*)dmats,
+                                                                  (const double2*)dtabs, a, partials);
     }
     return cudaGetLastError();
 }
