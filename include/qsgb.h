@@ -210,7 +210,8 @@ qs_status qs_fuse(const qs_circuit* in, int k_max, qs_circuit** out);
  * optional fusion, grouping into passes (shared-memory tile passes, strided
  * dense passes, diagonal / monomial passes, tensor-core passes), matrices
  * converted to the state's precision and uploaded to the device.  Uses the
- * current device; `opt` may be NULL for defaults. */
+ * current device; `opt` may be NULL for defaults (qs_options_default, with
+ * k_max 3 for complex128: blocks its float-float register tile applies). */
 qs_status qs_plan_create(const qs_circuit* c, qs_dtype dt, const qs_options* opt, qs_plan** out);
 qs_status qs_plan_destroy(qs_plan* p);
 
@@ -240,8 +241,10 @@ qs_status qs_plan_pass(const qs_plan* p, int i, int* kind, int* width, int* num_
  * A tensor-core mode on a complex64 state (n >= 12): 6-qubit blocks, fused
  * and run together -- a host thread runs the block search while this call
  * launches each block's pass (its own pass: no tile grouping) as soon as the
- * block is found, so the search overlaps the device passes; the call returns
- * after the last launch.  Otherwise: plan (k_max 4), execute, free the plan.
+ * block is found, so the search overlaps the device passes (passes wait in
+ * a window of up to 3 so that qubit 0 can be kept out of their targets); the
+ * call returns after the last launch.  Otherwise: plan (k_max 4 for
+ * complex64, 3 for complex128), execute, free the plan.
  * Asynchronous like qs_plan_execute: matrices are allocated and freed in the
  * state's stream order. */
 qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec);

@@ -947,6 +947,8 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     if (psi->dt == QS_C64 && gemm_supported(psi->n, 6)) {
         fast.k_max = 6;
         fast.precision = QS_PREC_3XTF32;
+    } else if (psi->dt == QS_C128) {
+        fast.k_max = 3;  // blocks the float-float register tile applies (up to its 3 register bits)
     }
     // the forward cannot start before its plan: the quicker block search
     fast.fusion_effort = 0;

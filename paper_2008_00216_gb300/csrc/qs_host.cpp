@@ -450,8 +450,12 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     *out = nullptr;
     if (dt != QS_C64 && dt != QS_C128) return fail(QS_ERR_ARG, "bad dtype");
     qs_options opt;
-    if (opt_in) opt = *opt_in;
-    else qs_options_default(&opt);
+    if (opt_in) {
+        opt = *opt_in;
+    } else {
+        qs_options_default(&opt);
+        if (dt == QS_C128) opt.k_max = 3;  // blocks the float-float register tile applies
+    }
     if (opt.k_max < 1 || opt.k_max > kMaxK) return fail(QS_ERR_ARG, "k_max outside 1..6");
     if (opt.fusion_effort < 0 || opt.fusion_effort > 1) return fail(QS_ERR_ARG, "fusion_effort must be 0 or 1");
     const int maxL = dt == QS_C64 ? 13 : 12;
@@ -723,6 +727,7 @@ qs_status qs_apply_circuit(qs_state* s, const qs_circuit* c, qs_precision prec) 
     qs_options_default(&opt);
     opt.precision = prec;
     if (prec != QS_PREC_FP32 && s->dt == QS_C64) opt.k_max = 6;  // 6-qubit blocks on the tensor cores
+    if (s->dt == QS_C128) opt.k_max = 3;  // blocks the float-float register tile applies
     if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XFP16) return fail(QS_ERR_ARG, "bad precision");
     if (s->dt == QS_C64 && prec != QS_PREC_FP32 && gemm_supported(s->n, 6)) {
         qs_status st = check_state(s);

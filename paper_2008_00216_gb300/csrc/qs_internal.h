@@ -149,7 +149,7 @@ constexpr uint8_t kTileMulfree = 8;
 // says which tile bit each lane, register and warp bit holds; ops run in
 // the current layout and LAYOUT ops move the tile between layouts through a
 // swizzled shared-memory transpose.
-constexpr int kRTMaxLayouts = 12, kRTMaxOps = 160;
+constexpr int kRTMaxLayouts = 48, kRTMaxOps = 160;
 enum RTOpType : uint8_t {
     RT_GATE = 0,    // k-qubit gate on register bits 0..k-1 (local bit i = register bit i)
     RT_GATE1 = 1,   // one-qubit gate on register bit `arg`
