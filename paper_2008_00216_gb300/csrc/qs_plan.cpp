@@ -738,19 +738,22 @@ static void sort_qubits_descending(Pass& p) {
     int order[kMaxK];  // new position i takes old position order[i]
     for (int i = 0; i < k; ++i) order[i] = i;
     std::sort(order, order + k, [&](int x, int y) { return p.qubits[x] > p.qubits[y]; });
-    auto old_index = [&](int ln) {
+    int old_index[1 << kMaxK];  // new local index -> old
+    for (int ln = 0; ln < d; ++ln) {
         int lo = 0;
         for (int i = 0; i < k; ++i)
             if ((ln >> (k - 1 - i)) & 1) lo |= 1 << (k - 1 - order[i]);
-        return lo;
-    };
+        old_index[ln] = lo;
+    }
     std::vector<double> m(p.mats.size());
-    for (int r = 0; r < d; ++r)
+    for (int r = 0; r < d; ++r) {
+        const double* src = p.mats.data() + 2 * (size_t)old_index[r] * d;
+        double* dst = m.data() + 2 * (size_t)r * d;
         for (int c = 0; c < d; ++c) {
-            const int ro = old_index(r), co = old_index(c);
-            m[2 * (r * d + c)] = p.mats[2 * (ro * d + co)];
-            m[2 * (r * d + c) + 1] = p.mats[2 * (ro * d + co) + 1];
+            dst[2 * c] = src[2 * old_index[c]];
+            dst[2 * c + 1] = src[2 * old_index[c] + 1];
         }
+    }
     int q[kMaxK];
     for (int i = 0; i < k; ++i) q[i] = p.qubits[order[i]];
     for (int i = 0; i < k; ++i) p.qubits[i] = q[i];

@@ -369,6 +369,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         if (++srow == kRows) flush();
     };
 
+    // the next tile's base: adding the deposited grid stride with the tile
+    // bits set to 1 carries straight through them
+    uint64_t tmask = 0;
+    for (int i = 0; i < L; ++i) tmask |= 1ull << a.pos[i];
+    const uint64_t gstep = tile_base(gridDim.x);
     uint64_t base = tile_base(blockIdx.x);
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         T ps[PER], ls[PER];
@@ -385,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         // the next tile of psi and lambda on its way into L2 while this one is processed
         uint64_t nb = 0;
         if (tile + gridDim.x < a.ntiles) {
-            nb = tile_base(tile + gridDim.x);
+            nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
             const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(T);
             const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(T);
 #pragma unroll
@@ -726,6 +731,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
         if (++srow == kRows) flush();
     };
 
+    // the next tile's base: adding the deposited grid stride with the tile
+    // bits set to 1 carries straight through them
+    uint64_t tmask = 0;
+    for (int i = 0; i < L; ++i) tmask |= 1ull << a.pos[i];
+    const uint64_t gstep = tile_base(gridDim.x);
     uint64_t base = tile_base(blockIdx.x);
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         FFC ps[PER], ls[PER];
@@ -746,7 +756,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
         }
         uint64_t nb = 0;
         if (tile + gridDim.x < a.ntiles) {  // the next tile on its way into L2
-            nb = tile_base(tile + gridDim.x);
+            nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
             const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(double2);
             const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(double2);
 #pragma unroll
