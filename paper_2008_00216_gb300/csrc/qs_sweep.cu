@@ -456,50 +456,55 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                     }
                     stage((__popcll(xt & z.mthr) & 1) ? -v : v);
                 }
-                if (d.ngen > d.nstaged) {  // block generators: warp sums of S, W_b (lane bits), U_k
-                    const int lane = tid & 31, warp = tid >> 5;
-                    // warp sums as (sum, rounding errors) pairs for complex64
-                    // (TwoSum steps), then FP64 across the warps
+                if (d.ngen > d.nstaged) {
+                    // block generators: the tile's sums S (all), W_b (thread bit b set)
+                    // and U_k (register bit k set) as staged rows of the current bank,
+                    // reduced like the gradient rows (TwoSum steps), FP64 per tile
+                    constexpr int NB = 1 + 8 + RB;
+                    static_assert(NB <= kRows, "basis rows fit a bank");
+                    if (srow) flush();  // the current bank is then empty
+                    R* rows = gs + bank * kRows * kThreads;
 #pragma unroll
-                    for (int i = 0; i < 6 + RB; ++i) {
-                        const R w0 = i == 0 ? tsum : i < 6 ? (((lane >> (i - 1)) & 1) ? tsum : (R)0) : u[i < 6 ? 0 : i - 6];
-                        R hi = w0, lo = 0;
-                        if constexpr (sizeof(R) == 4) {
-                            F2Acc w;
-                            w.hi = w0;
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) {
-                                const float h = __shfl_xor_sync(0xffffffffu, w.hi, o), l = __shfl_xor_sync(0xffffffffu, w.lo, o);
-                                w.add(h);
-                                w.lo += l;
-                            }
-                            hi = w.hi;
-                            lo = w.lo;
-                        } else {
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) hi += __shfl_xor_sync(0xffffffffu, hi, o);
-                        }
-                        if (lane == 0) {
-                            dred[2 * (warp * (6 + RB) + i)] = hi;
-                            dred[2 * (warp * (6 + RB) + i) + 1] = lo;
-                        }
+                    for (int b = 0; b < NB; ++b) {
+                        const R v = b == 0 ? tsum : b <= 8 ? (((tid >> (b - 1)) & 1) ? tsum : (R)0) : u[b < 9 ? 0 : b - 9];
+                        rows[b * kThreads + tid] = v;
                     }
                     __syncthreads();
+                    double* tileB = reinterpret_cast<double*>(dred);  // NB totals
+                    {  // every thread takes part (rows NB.. hold stale values and are dropped)
+                        const int row = tid / TPR, part = tid % TPR;
+                        double tot;
+                        if constexpr (sizeof(R) == 4) {
+                            F2Acc v;
+#pragma unroll
+                            for (int k = 0; k < kThreads / TPR; ++k) v.add(rows[row * kThreads + part + TPR * k]);
+#pragma unroll
+                            for (int o = TPR / 2; o > 0; o >>= 1) {
+                                const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR);
+                                const float l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
+                                v.add(h);
+                                v.lo += l;
+                            }
+                            tot = (double)v.hi + (double)v.lo;
+                        } else {
+                            R v = 0;
+#pragma unroll
+                            for (int k = 0; k < kThreads / TPR; ++k) v += rows[row * kThreads + part + TPR * k];
+#pragma unroll
+                            for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
+                            tot = (double)v;
+                        }
+                        if (part == 0 && row < NB) tileB[row] = tot;
+                    }
+                    __syncthreads();  // the totals are visible, and the bank's rows are free again
                     for (int g = d.nstaged + tid; g < d.ngen; g += kThreads) {
                         const SweepZGen z = a.gens[d.gen0 + g];
-                        double S = 0, X = 0;
-                        for (int q = 0; q < kThreads / 32; ++q) {  // fixed order
-                            const R* wq = dred + 2 * q * (6 + RB);
-                            auto at = [&](int i) { return (double)wq[2 * i] + (double)wq[2 * i + 1]; };
-                            S += at(0);
-                            if (z.src >= 1 && z.src <= RB) X += at(5 + z.src);
-                            else if (z.src > RB && z.src <= RB + 5) X += at(z.src - RB);
-                            else if (z.src > RB + 5 && ((q >> (z.src - RB - 6)) & 1)) X += at(0);
-                        }
-                        const double v = S - 2 * X;
+                        double X = 0;
+                        if (z.src >= 1 && z.src <= RB) X = tileB[9 + z.src - 1];
+                        else if (z.src > RB && z.src <= RB + 8) X = tileB[1 + z.src - RB - 1];
+                        const double v = tileB[0] - 2 * X;
                         red[z.local] += (__popcll(base & z.mthr) & 1) ? -v : v;
                     }
-                    __syncthreads();  // dred is reused by the next diagonal op
                 }
                 const T* t0 = dtab + (xt & 255);  // chunk 0: the thread's bits, plus j
 #pragma unroll
