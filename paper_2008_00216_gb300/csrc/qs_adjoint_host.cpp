@@ -600,7 +600,20 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
         // qubits 0 .. RB-1; each step's gates are grouped by layout, the
         // current one first and the one the next step starts in last
         const int low = nlay - 1;
+        // the tile is loaded and stored in layout 0 or 1 (both coalesced): start
+        // in 1 when the first step's gates all sit there, store in the layout
+        // the pass ends in when that is 0 or 1
         int cur = 0;
+        if (!pp.steps.empty() && !pp.steps[0].diag) {
+            bool has0 = false, has1 = false;
+            for (int gi : pp.steps[0].gates) {
+                const int l = layout_of(local_of[c.gates[gi].qubits[0]]);
+                has0 = has0 || l == 0;
+                has1 = has1 || l == 1;
+            }
+            if (has1 && !has0) cur = 1;
+        }
+        p.load_lay = cur;
         std::vector<int> block_slots;
         for (size_t k = 0; k < pp.steps.size(); ++k) {
             const Step& st = pp.steps[k];
@@ -613,11 +626,18 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
                 for (int b = 0; b < RB; ++b) rq[b] = p.pos[lay_a[low] + b];
                 compile_fused_diag(c, run[st.stage].diag, n, rq, RB, p, block_slots);
             }
-            const int last = k + 1 < pp.steps.size() && pp.steps[k + 1].diag ? low : 0;
             std::vector<int> order{cur};
-            for (int l = 0; l < nlay; ++l)
-                if (l != cur && l != last) order.push_back(l);
-            if (last != cur) order.push_back(last);
+            if (k + 1 < pp.steps.size()) {
+                const int last = pp.steps[k + 1].diag ? low : 0;
+                for (int l = 0; l < nlay; ++l)
+                    if (l != cur && l != last) order.push_back(l);
+                if (last != cur) order.push_back(last);
+            } else {  // the final step: end in a layout the tile can be stored from
+                for (int l = nlay - 1; l >= 2; --l)
+                    if (l != cur) order.push_back(l);
+                for (int l = 0; l < 2; ++l)
+                    if (l != cur) order.push_back(l);
+            }
             struct G1Op {
                 SweepOpRec op;
                 double c8[8];
@@ -679,6 +699,7 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
                 }
             }
         }
+        p.store_lay = cur <= 1 ? cur : 0;
         for (const SweepDiagRec& d : p.diags)  // block generators' slots follow the staged ones
             for (int g = d.nstaged; g < d.ngen; ++g) p.gens[d.gen0 + g].local += (uint16_t)p.slots.size();
         p.slots.insert(p.slots.end(), block_slots.begin(), block_slots.end());

@@ -439,6 +439,7 @@ struct SweepPassDesc {
     int pos[16] = {0};
     int nlay = 0;
     int lay_a[kSweepMaxLayouts] = {0};
+    int load_lay = 0, store_lay = 0;  // the tile's load and store layouts: 0 or 1 (both coalesced)
     std::vector<SweepOpRec> ops;
     std::vector<SweepDiagRec> diags;
     std::vector<DiagCross> cross;      // tab: element offset in the pass's table block

@@ -52,6 +52,7 @@ template <> struct SweepShape<double> {
 
 struct SweepArgs {
     int n, nops, ngrad, nb, nmat;
+    int load_lay, store_lay;   // layouts (0 or 1, both coalesced) the tile is loaded and stored in
     uint32_t tab_elems;
     uint64_t ntiles;
     int pos[16];
@@ -302,17 +303,18 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     T* tab = buf + 2 * (1u << L);                                               // a.tab_elems
     R* gs = reinterpret_cast<R*>(tab + a.tab_elems);                            // 2 banks x kRows x kThreads
     double* red = reinterpret_cast<double*>(gs + 2 * kRows * kThreads);         // a.ngrad (even count: 16-byte alignment below)
-    uint64_t* xo = reinterpret_cast<uint64_t*>(red + ((a.ngrad + 1) & ~1));    // PER: byte offset of j
-    R* dred = reinterpret_cast<R*>(xo + PER);                                   // 8 warps x (6 + RB) x (sum, error)
+    uint64_t* xo = reinterpret_cast<uint64_t*>(red + ((a.ngrad + 1) & ~1));    // 2 x PER: byte offset of j, layouts 0, 1
+    R* dred = reinterpret_cast<R*>(xo + 2 * PER);                               // 8 warps x (6 + RB) x (sum, error)
     T* cm = reinterpret_cast<T*>(dred + 2 * (kThreads / 32) * (6 + RB));        // 4 x a.nmat coefficients
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = tabs[i];
     for (int i = tid; i < 4 * a.nmat; i += kThreads) cm[i] = mats[i];
     for (int i = tid; i < a.ngrad; i += kThreads) red[i] = 0.0;
-    if (tid < PER) {  // natural layout: register bit k is tile bit L - RB + k
+    if (tid < 2 * PER) {  // layout l: register bit k is tile bit lay(l) + k
+        const int l = tid / PER, j = tid % PER;
         uint64_t o = 0;
         for (int k = 0; k < RB; ++k)
-            if ((tid >> k) & 1) o |= 1ull << a.pos[L - RB + k];
+            if ((j >> k) & 1) o |= 1ull << a.pos[S::lay(l) + k];
         xo[tid] = o * sizeof(T);
     }
     auto global_of = [&](uint32_t e) {  // tile index -> global offset within the tile
@@ -320,7 +322,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         for (int i = 0; i < L; ++i) x |= (uint64_t)((e >> i) & 1u) << a.pos[i];
         return x;
     };
-    const uint64_t xg0 = global_of(layout_base<RB>(tid, S::lay(0)));  // the thread's bits, natural layout
+    // the thread's bits in the load and store layouts
+    const uint64_t xgl = global_of(layout_base<RB>(tid, S::lay(a.load_lay)));
+    const uint64_t xgs = global_of(layout_base<RB>(tid, S::lay(a.store_lay)));
+    const uint64_t* xol = xo + PER * a.load_lay;
+    const uint64_t* xos = xo + PER * a.store_lay;
     const uint64_t xl0 = global_of(layout_base<RB>(tid, 0));          // the thread's bits, low layout
     auto tile_base = [&](uint64_t t) {
         for (int i = 0; i < L; ++i) t = insert_zero(t, a.pos[i]);
@@ -378,11 +384,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         T ps[PER], ls[PER];
         {
-            const char* pp = reinterpret_cast<const char*>(psi) + (base | xg0) * sizeof(T);
-            const char* pl = reinterpret_cast<const char*>(lam) + (base | xg0) * sizeof(T);
+            const char* pp = reinterpret_cast<const char*>(psi) + (base | xgl) * sizeof(T);
+            const char* pl = reinterpret_cast<const char*>(lam) + (base | xgl) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                const uint64_t o = xo[j];
+                const uint64_t o = xol[j];
                 ps[j] = *reinterpret_cast<const T*>(pp + o);
                 ls[j] = *reinterpret_cast<const T*>(pl + o);
             }
@@ -391,15 +397,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
         uint64_t nb = 0;
         if (tile + gridDim.x < a.ntiles) {
             nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
-            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(T);
-            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(T);
+            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xgl) * sizeof(T);
+            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xgl) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xo[j]));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xo[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
             }
         }
-        int lay = 0;
+        int lay = a.load_lay;
         gdone = 0;
         for (int o = 0; o < a.nops; ++o) {
             const SweepOpRec op = a.ops[o];
@@ -516,13 +522,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 }
             }
         }
-        if (lay != 0) transpose_any<R>(buf, ps, ls, lay, 0);
+        if (lay != a.store_lay) transpose_any<R>(buf, ps, ls, lay, a.store_lay);
         {
-            char* pp = reinterpret_cast<char*>(psi) + (base | xg0) * sizeof(T);
-            char* pl = reinterpret_cast<char*>(lam) + (base | xg0) * sizeof(T);
+            char* pp = reinterpret_cast<char*>(psi) + (base | xgs) * sizeof(T);
+            char* pl = reinterpret_cast<char*>(lam) + (base | xgs) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                const uint64_t o = xo[j];
+                const uint64_t o = xos[j];
                 *reinterpret_cast<T*>(pp + o) = ps[j];
                 *reinterpret_cast<T*>(pl + o) = ls[j];
             }
@@ -680,15 +686,16 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
     float* gsl = gsh + 2 * kRows * kThreads;
     float* dred = gsl + 2 * kRows * kThreads;                                   // 8 warps x (6 + RB) x (sum, error)
     double* red = reinterpret_cast<double*>(dred + 2 * (kThreads / 32) * (6 + RB));   // a.ngrad
-    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // PER: byte offset of j
+    uint64_t* xo = reinterpret_cast<uint64_t*>(red + a.ngrad);                  // 2 x PER: byte offset of j, layouts 0, 1
     const uint32_t tid = threadIdx.x;
     for (uint32_t i = tid; i < a.tab_elems; i += kThreads) tab[i] = ff_from(tabs[i]);
     for (int i = tid; i < 4 * a.nmat; i += kThreads) cm[i] = ff_from(mats[i]);
     for (int i = tid; i < a.ngrad; i += kThreads) red[i] = 0.0;
-    if (tid < PER) {  // natural layout: register bit k is tile bit L - RB + k
+    if (tid < 2 * PER) {  // layout l: register bit k is tile bit lay(l) + k
+        const int l = tid / PER, j = tid % PER;
         uint64_t o = 0;
         for (int k = 0; k < RB; ++k)
-            if ((tid >> k) & 1) o |= 1ull << a.pos[L - RB + k];
+            if ((j >> k) & 1) o |= 1ull << a.pos[SweepShape<double>::lay(l) + k];
         xo[tid] = o * sizeof(double2);
     }
     auto global_of = [&](uint32_t e) {
@@ -701,7 +708,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
         return t;
     };
     auto lay_a = [](int l) { return SweepShape<double>::lay(l); };   // register ranges 8, 5, 2, 0
-    const uint64_t xg0 = global_of(layout_base<RB>(tid, lay_a(0)));
+    const uint64_t xgl = global_of(layout_base<RB>(tid, lay_a(a.load_lay)));
+    const uint64_t xgs = global_of(layout_base<RB>(tid, lay_a(a.store_lay)));
+    const uint64_t* xol = xo + PER * a.load_lay;
+    const uint64_t* xos = xo + PER * a.store_lay;
     const uint64_t xl0 = global_of(layout_base<RB>(tid, 0));
     __syncthreads();
 
@@ -745,13 +755,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
     for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
         FFC ps[PER], ls[PER];
         {
-            const char* pp = reinterpret_cast<const char*>(psi) + (base | xg0) * sizeof(double2);
-            const char* pl = reinterpret_cast<const char*>(lam) + (base | xg0) * sizeof(double2);
+            const char* pp = reinterpret_cast<const char*>(psi) + (base | xgl) * sizeof(double2);
+            const char* pl = reinterpret_cast<const char*>(lam) + (base | xgl) * sizeof(double2);
             double2 dp[PER], dl[PER];
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                dp[j] = *reinterpret_cast<const double2*>(pp + xo[j]);
-                dl[j] = *reinterpret_cast<const double2*>(pl + xo[j]);
+                dp[j] = *reinterpret_cast<const double2*>(pp + xol[j]);
+                dl[j] = *reinterpret_cast<const double2*>(pl + xol[j]);
             }
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
@@ -762,15 +772,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
         uint64_t nb = 0;
         if (tile + gridDim.x < a.ntiles) {  // the next tile on its way into L2
             nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
-            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xg0) * sizeof(double2);
-            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xg0) * sizeof(double2);
+            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xgl) * sizeof(double2);
+            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xgl) * sizeof(double2);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xo[j]));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xo[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
             }
         }
-        int lay = 0;
+        int lay = a.load_lay;
         gdone = 0;
         for (int o = 0; o < a.nops; ++o) {
             const SweepOpRec op = a.ops[o];
@@ -908,14 +918,14 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
                 }
             }
         }
-        if (lay != 0) ff_transpose(buf, ps, ls, lay_a(lay), lay_a(0));
+        if (lay != a.store_lay) ff_transpose(buf, ps, ls, lay_a(lay), lay_a(a.store_lay));
         {
-            char* pp = reinterpret_cast<char*>(psi) + (base | xg0) * sizeof(double2);
-            char* pl = reinterpret_cast<char*>(lam) + (base | xg0) * sizeof(double2);
+            char* pp = reinterpret_cast<char*>(psi) + (base | xgs) * sizeof(double2);
+            char* pl = reinterpret_cast<char*>(lam) + (base | xgs) * sizeof(double2);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                *reinterpret_cast<double2*>(pp + xo[j]) = ff_to(ps[j]);
-                *reinterpret_cast<double2*>(pl + xo[j]) = ff_to(ls[j]);
+                *reinterpret_cast<double2*>(pp + xos[j]) = ff_to(ps[j]);
+                *reinterpret_cast<double2*>(pl + xos[j]) = ff_to(ls[j]);
             }
         }
         if (srow) flush();
@@ -933,7 +943,7 @@ size_t sweep_smem_ff(const SweepArgs& a) {
     constexpr int L = kSweepTileC128, RB = 3;
     return 16 * (2 * ((size_t)1 << L) + a.tab_elems + 4 * (size_t)a.nmat) + sizeof(float) * 2 * 2 * 8 * kThreads +
            sizeof(float) * 2 * (kThreads / 32) * (6 + RB) + sizeof(double) * (size_t)a.ngrad +
-           sizeof(uint64_t) * ((size_t)1 << RB);
+           sizeof(uint64_t) * 2 * ((size_t)1 << RB);
 }
 
 template <typename R>
@@ -941,7 +951,7 @@ size_t sweep_smem(const SweepArgs& a) {
     constexpr int L = SweepShape<R>::L;
     const size_t esz = sizeof(typename C2<R>::T);
     return esz * (2 * ((size_t)1 << L) + a.tab_elems) + sizeof(R) * 2 * SweepShape<R>::ROWS * kThreads +
-           sizeof(double) * ((a.ngrad + 1) & ~1) + sizeof(uint64_t) * ((size_t)1 << (L - 8)) +
+           sizeof(double) * ((a.ngrad + 1) & ~1) + sizeof(uint64_t) * 2 * ((size_t)1 << (L - 8)) +
            sizeof(R) * 2 * (kThreads / 32) * (6 + (L - 8)) + sizeof(typename C2<R>::T) * 4 * a.nmat;
 }
 
@@ -991,7 +1001,10 @@ cudaError_t launch_sweep_pass(void* psi, void* lam, int n, qs_dtype dt, const Sw
     const uint32_t nmat = (uint32_t)(p.mats.size() / 8);
     if (nmat > kSweepMaxOps) return cudaErrorInvalidValue;
     a.nmat = (int)nmat;
-    int grads = 0, cur = 0;  // cur: the layout the kernel is in at this op
+    if (p.load_lay < 0 || p.load_lay > 1 || p.store_lay < 0 || p.store_lay > 1) return cudaErrorInvalidValue;
+    a.load_lay = p.load_lay;
+    a.store_lay = p.store_lay;
+    int grads = 0, cur = p.load_lay;  // cur: the layout the kernel is in at this op
     for (int o = 0; o < a.nops; ++o) {
         const SweepOpRec& op = p.ops[o];
         if (op.type == SWEEP_LAYOUT) {
