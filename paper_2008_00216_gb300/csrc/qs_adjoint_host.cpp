@@ -971,8 +971,9 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     } else if (psi->dt == QS_C128) {
         fast.k_max = 3;  // blocks the float-float register tile applies (up to its 3 register bits)
     }
-    // the forward cannot start before its plan: the quicker block search
-    fast.fusion_effort = 0;
+    // the full block search (fewer blocks); its grouping is cached on the
+    // circuit, so repeated gradients (new angles, same gates) skip it
+    fast.fusion_effort = 1;
     // forward and lambda are enqueued first; the reverse sweep is planned on
     // the host while the GPU runs them (plan memory is stream-ordered, so
     // nothing here synchronises)

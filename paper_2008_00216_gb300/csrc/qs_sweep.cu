@@ -399,10 +399,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
             nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
             const char* pp = reinterpret_cast<const char*>(psi) + (nb | xgl) * sizeof(T);
             const char* pl = reinterpret_cast<const char*>(lam) + (nb | xgl) * sizeof(T);
+            if ((tid & ((128 / sizeof(T)) - 1)) == 0) {  // one thread per 128-byte row of the tile
 #pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
+                for (int j = 0; j < PER; ++j) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
+                }
             }
         }
         int lay = a.load_lay;
@@ -774,10 +776,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
             nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
             const char* pp = reinterpret_cast<const char*>(psi) + (nb | xgl) * sizeof(double2);
             const char* pl = reinterpret_cast<const char*>(lam) + (nb | xgl) * sizeof(double2);
+            if ((tid & 7) == 0) {  // one thread per 128-byte row of the tile
 #pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
-                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
+                for (int j = 0; j < PER; ++j) {
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
+                }
             }
         }
         int lay = a.load_lay;
