@@ -381,32 +381,38 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     for (int i = 0; i < L; ++i) tmask |= 1ull << a.pos[i];
     const uint64_t gstep = tile_base(gridDim.x);
     uint64_t base = tile_base(blockIdx.x);
-    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-        T ps[PER], ls[PER];
-        {
-            const char* pp = reinterpret_cast<const char*>(psi) + (base | xgl) * sizeof(T);
-            const char* pl = reinterpret_cast<const char*>(lam) + (base | xgl) * sizeof(T);
+    T ps[PER], ls[PER];
+    auto load_tile = [&](uint64_t b) {
+        const char* pp = reinterpret_cast<const char*>(psi) + (b | xgl) * sizeof(T);
+        const char* pl = reinterpret_cast<const char*>(lam) + (b | xgl) * sizeof(T);
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const uint64_t o = xol[j];
+            ps[j] = *reinterpret_cast<const T*>(pp + o);
+            ls[j] = *reinterpret_cast<const T*>(pl + o);
+        }
+    };
+    auto prefetch_tile = [&](uint64_t b) {  // into L2, one thread per 128-byte row of the tile
+        if ((tid & ((128 / sizeof(T)) - 1)) == 0) {
+            const char* pp = reinterpret_cast<const char*>(psi) + (b | xgl) * sizeof(T);
+            const char* pl = reinterpret_cast<const char*>(lam) + (b | xgl) * sizeof(T);
 #pragma unroll
             for (int j = 0; j < PER; ++j) {
-                const uint64_t o = xol[j];
-                ps[j] = *reinterpret_cast<const T*>(pp + o);
-                ls[j] = *reinterpret_cast<const T*>(pl + o);
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
             }
         }
-        // the next tile of psi and lambda on its way into L2 while this one is processed
-        uint64_t nb = 0;
-        if (tile + gridDim.x < a.ntiles) {
-            nb = ((base | tmask) + gstep) & ~tmask;  // tile + gridDim.x, deposited
-            const char* pp = reinterpret_cast<const char*>(psi) + (nb | xgl) * sizeof(T);
-            const char* pl = reinterpret_cast<const char*>(lam) + (nb | xgl) * sizeof(T);
-            if ((tid & ((128 / sizeof(T)) - 1)) == 0) {  // one thread per 128-byte row of the tile
-#pragma unroll
-                for (int j = 0; j < PER; ++j) {
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pp + xol[j]));
-                    asm volatile("prefetch.global.L2 [%0];" ::"l"(pl + xol[j]));
-                }
-            }
-        }
+    };
+    auto next_base = [&](uint64_t b) { return ((b | tmask) + gstep) & ~tmask; };  // tile + gridDim.x, deposited
+    // a tile's loads are issued as soon as the previous tile is stored (their
+    // latency overlaps that tile's gradient reduction), and the tile after
+    // it is prefetched into L2 meanwhile
+    if (blockIdx.x < a.ntiles) {
+        load_tile(base);
+        if (blockIdx.x + gridDim.x < a.ntiles) prefetch_tile(next_base(base));
+    }
+    for (uint64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+        const uint64_t nb = tile + gridDim.x < a.ntiles ? next_base(base) : 0;
         int lay = a.load_lay;
         gdone = 0;
         for (int o = 0; o < a.nops; ++o) {
@@ -534,6 +540,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 *reinterpret_cast<T*>(pp + o) = ps[j];
                 *reinterpret_cast<T*>(pl + o) = ls[j];
             }
+        }
+        if (tile + gridDim.x < a.ntiles) {
+            load_tile(nb);
+            if (tile + 2 * (uint64_t)gridDim.x < a.ntiles) prefetch_tile(next_base(nb));
         }
         if (srow) flush();
         base = nb;
