@@ -36,17 +36,18 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// L: tile qubits; 2^SW elements per 128-byte row; ROWS: staged gradients
-// (one row of kThreads values each, in the state's precision); LAY: the
-// register layouts (start of the register range), 0 natural, the last one
-// "low" (registers hold qubits 0 .. L-9, where diagonal ops run).
+// L: tile qubits; ROWS: staged gradient rows per bank (one row of kThreads
+// values each); lay(l): the register layouts (start of the register range),
+// 0 natural, the last one "low" (registers hold qubits 0 .. L-9, where
+// diagonal ops run).  float: complex64; double: the complex128 tile of the
+// float-float form.
 template <typename R> struct SweepShape;
 template <> struct SweepShape<float> {
-    static constexpr int L = kSweepTileC64, SW = 4, ROWS = 16, NLAY = 3;
+    static constexpr int L = kSweepTileC64, ROWS = 16, NLAY = 3;
     __host__ __device__ static constexpr int lay(int l) { return l == 0 ? 8 : l == 1 ? 4 : 0; }
 };
 template <> struct SweepShape<double> {
-    static constexpr int L = kSweepTileC128, SW = 3, ROWS = 8, NLAY = 4;
+    static constexpr int L = kSweepTileC128, ROWS = 8, NLAY = 4;
     __host__ __device__ static constexpr int lay(int l) { return l == 0 ? 8 : l == 1 ? 5 : l == 2 ? 2 : 0; }
 };
 
@@ -80,30 +81,6 @@ __host__ __device__ constexpr uint32_t swz(uint32_t e) {
     return e ^ ((e >> SW) & ((1u << SW) - 1u));
 }
 
-// A transpose needs one barrier, between its writes and its reads.  A slot
-// belongs to one tile element, so the slots a thread writes (its elements
-// in the current layout) are exactly the slots it alone read in the
-// previous transpose, which brought it into this layout (tiles start and
-// end in layout 0): no other thread can still be reading them.
-template <typename T, int L, int SW, int AF, int AT>
-__device__ __forceinline__ void transpose_ct(T* buf, T (&ps)[1 << (L - 8)], T (&ls)[1 << (L - 8)]) {
-    constexpr int RB = L - 8, PER = 1 << RB;
-    const uint32_t s0 = swz<SW>(layout_base<RB>(threadIdx.x, AF)), s1 = swz<SW>(layout_base<RB>(threadIdx.x, AT));
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint32_t s = s0 ^ swz<SW>((uint32_t)j << AF);
-        buf[s] = ps[j];
-        buf[(1u << L) + s] = ls[j];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const uint32_t s = s1 ^ swz<SW>((uint32_t)j << AT);
-        ps[j] = buf[s];
-        ls[j] = buf[(1u << L) + s];
-    }
-}
-
 // Complex64: psi and lambda of one tile element share a 16-byte slot, so a
 // transpose moves both with one 128-bit store and one 128-bit load per
 // element.  A 128-bit access is served in four phases of 8 lanes; the slot's
@@ -114,6 +91,11 @@ __device__ __forceinline__ void transpose_ct(T* buf, T (&ps)[1 << (L - 8)], T (&
 // slot XOR a constant.
 __host__ __device__ constexpr uint32_t swz16(uint32_t e) { return e ^ ((e >> 4) & 7u); }
 
+// A transpose needs one barrier, between its writes and its reads.  A slot
+// belongs to one tile element, so the slots a thread writes (its elements
+// in the current layout) are exactly the slots it alone read in the
+// previous transpose, which brought it into this layout (tiles start and
+// end in layout 0): no other thread can still be reading them.
 template <int L, int AF, int AT>
 __device__ __forceinline__ void transpose_pl(float4* buf, float2 (&ps)[1 << (L - 8)], float2 (&ls)[1 << (L - 8)]) {
     constexpr int RB = L - 8, PER = 1 << RB;
@@ -134,8 +116,7 @@ template <typename R, int AF, int AT>
 __device__ __forceinline__ void transpose_to(typename C2<R>::T* buf, typename C2<R>::T (&ps)[1 << (SweepShape<R>::L - 8)],
                                              typename C2<R>::T (&ls)[1 << (SweepShape<R>::L - 8)]) {
     using S = SweepShape<R>;
-    if constexpr (sizeof(R) == 4) transpose_pl<S::L, AF, AT>(reinterpret_cast<float4*>(buf), ps, ls);
-    else transpose_ct<typename C2<R>::T, S::L, S::SW, AF, AT>(buf, ps, ls);
+    transpose_pl<S::L, AF, AT>(reinterpret_cast<float4*>(buf), ps, ls);
 }
 
 template <typename R, int F>
@@ -286,6 +267,24 @@ __device__ __forceinline__ void g1_all(T (&ps)[1 << RB], T (&ls)[1 << RB], const
     }
 }
 
+// The sum of row `row` of a bank of staged values (kThreads floats): this
+// thread's TPR-strided share with TwoSum steps into a (sum, error) pair, then
+// across the row's TPR lanes the same way; the pair enters FP64.
+template <int TPR>
+__device__ __forceinline__ double row_total(const float* rows, int row, int part) {
+    F2Acc v;
+#pragma unroll
+    for (int k = 0; k < kThreads / TPR; ++k) v.add(rows[row * kThreads + part + TPR * k]);
+#pragma unroll
+    for (int o = TPR / 2; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR), l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
+        v.add(h);
+        v.lo += l;
+    }
+    return (double)v.hi + (double)v.lo;
+}
+
+// complex64 (R = float); complex128 runs k_sweep_pass_ff below
 template <typename R>
 __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* __restrict__ psi,
                                                             typename C2<R>::T* __restrict__ lam,
@@ -294,6 +293,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                                                             const __grid_constant__ SweepArgs a,
                                                             double* __restrict__ partials) {
     using T = typename C2<R>::T;
+    static_assert(sizeof(R) == 4, "complex64 only: complex128 runs the float-float form");
     using S = SweepShape<R>;
     constexpr int L = S::L, RB = L - 8, PER = 1 << RB, LOW = S::NLAY - 1;
     constexpr int kRows = S::ROWS, TPR = kThreads / kRows;  // threads per staged row
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     // block-uniform: add the staged rows to red.  Complex64: each row's 256
     // values are summed with error-free TwoSum steps into a float pair (sum,
     // rounding errors), so the tile's sum reaches FP64 as if it had been
-    // accumulated there; complex128 sums in FP64 throughout.
+    // accumulated there.
     // The rows are double-buffered: staging goes on in the other bank while
     // slower threads still read this one, so the flush needs no barrier at
     // its end (the next flush's barrier orders this bank's reuse).
@@ -346,26 +346,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
     auto flush = [&]() {
         __syncthreads();
         const int row = tid / TPR, part = tid % TPR;
-        const R* gb = gs + bank * kRows * kThreads;
-        if constexpr (sizeof(R) == 4) {
-            F2Acc v;
-#pragma unroll
-            for (int k = 0; k < kThreads / TPR; ++k) v.add(gb[row * kThreads + part + TPR * k]);
-#pragma unroll
-            for (int o = TPR / 2; o > 0; o >>= 1) {
-                const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR), l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
-                v.add(h);
-                v.lo += l;
-            }
-            if (part == 0 && row < srow) red[gdone + row] += (double)v.hi + (double)v.lo;
-        } else {
-            R v = 0;
-#pragma unroll
-            for (int k = 0; k < kThreads / TPR; ++k) v += gb[row * kThreads + part + TPR * k];
-#pragma unroll
-            for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
-            if (part == 0 && row < srow) red[gdone + row] += (double)v;
-        }
+        const double tot = row_total<TPR>(gs + bank * kRows * kThreads, row, part);
+        if (part == 0 && row < srow) red[gdone + row] += tot;
         gdone += srow;
         srow = 0;
         bank ^= 1;
@@ -487,27 +469,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                     double* tileB = reinterpret_cast<double*>(dred);  // NB totals
                     {  // every thread takes part (rows NB.. hold stale values and are dropped)
                         const int row = tid / TPR, part = tid % TPR;
-                        double tot;
-                        if constexpr (sizeof(R) == 4) {
-                            F2Acc v;
-#pragma unroll
-                            for (int k = 0; k < kThreads / TPR; ++k) v.add(rows[row * kThreads + part + TPR * k]);
-#pragma unroll
-                            for (int o = TPR / 2; o > 0; o >>= 1) {
-                                const float h = __shfl_xor_sync(0xffffffffu, v.hi, o, TPR);
-                                const float l = __shfl_xor_sync(0xffffffffu, v.lo, o, TPR);
-                                v.add(h);
-                                v.lo += l;
-                            }
-                            tot = (double)v.hi + (double)v.lo;
-                        } else {
-                            R v = 0;
-#pragma unroll
-                            for (int k = 0; k < kThreads / TPR; ++k) v += rows[row * kThreads + part + TPR * k];
-#pragma unroll
-                            for (int o = TPR / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, TPR);
-                            tot = (double)v;
-                        }
+                        const double tot = row_total<TPR>(rows, row, part);
                         if (part == 0 && row < NB) tileB[row] = tot;
                     }
                     __syncthreads();  // the totals are visible, and the bank's rows are free again
