@@ -191,7 +191,7 @@ struct F2Acc {
     }
     // add x*x with its product rounding error (one FMA recovers it)
     __device__ __forceinline__ void add_sq(float x) {
-        const float p = x * x;
+        const float p = __fmul_rn(x, x);  // never contracted into the sum below
         const float q = fmaf(x, x, -p);
         float s, e;
         two_sum(hi, p, s, e);

@@ -88,7 +88,7 @@ struct FFAcc {
 __device__ __forceinline__ FFAcc ffa_zero() { return FFAcc{0.f, 0.f, 0.f, 0.f}; }
 // S + E += (ah + al)(bh + bl), dropping al * bl (2^-48 relative)
 __device__ __forceinline__ void ffa_term(float& S, float& E, float ah, float al, float bh, float bl) {
-    const float p = ah * bh;
+    const float p = __fmul_rn(ah, bh);  // never contracted into the sums below
     float e = fmaf(ah, bh, -p);
     e = fmaf(ah, bl, e);
     e = fmaf(al, bh, e);
@@ -130,7 +130,7 @@ __device__ __forceinline__ FFC ff_rot(const FFC& v, int code) {   // i^code v
 // high products exactly (FMA-based TwoProd) and summed with TwoSum, every
 // other part gathered in lo (al * bl and cl * dl dropped, 2^-48 relative)
 __device__ __forceinline__ float2 ff_dot2(float ah, float al, float bh, float bl, float ch, float cl, float dh, float dl) {
-    const float p = ah * bh, q = ch * dh;
+    const float p = __fmul_rn(ah, bh), q = __fmul_rn(ch, dh);  // never contracted into the sums below
     float e = fmaf(ah, bh, -p);
     e = fmaf(ah, bl, e);
     e = fmaf(al, bh, e);
@@ -158,7 +158,7 @@ __device__ __forceinline__ float2 ff_dot4(const float (&ah)[4], const float (&al
     float p[4], e = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        p[k] = ah[k] * bh[k];
+        p[k] = __fmul_rn(ah[k], bh[k]);  // never contracted into the sums below
         float ek = fmaf(ah[k], bh[k], -p[k]);
         ek = fmaf(ah[k], bl[k], ek);
         ek = fmaf(al[k], bh[k], ek);
