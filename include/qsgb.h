@@ -179,6 +179,12 @@ qs_status qs_circuit_destroy(qs_circuit* c);
 /* Append a fixed gate (copied). */
 qs_status qs_circuit_add(qs_circuit* c, const int* qubits, int k, const double* m);
 
+/* Append `count` fixed gates at once (copied), in order: gate i has ks[i]
+ * qubits, the next ks[i] entries of `qubits`, and the next 2 * 4^ks[i]
+ * doubles of `mats` (its matrix as for qs_circuit_add).  Every gate is
+ * checked first; on an error nothing is appended (QS_ERR_ARG). */
+qs_status qs_circuit_add_gates(qs_circuit* c, int count, const int* ks, const int* qubits, const double* mats);
+
 /* Append a parametrised gate exp(-i theta P / 2) with P the Pauli string
  * `paulis` ("X", "ZZ", "XY", ... ; paulis[i] acts on qubits[i]), parameter
  * index `param` >= 0 and current value `theta`. */

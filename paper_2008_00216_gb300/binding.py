@@ -57,6 +57,8 @@ _SIGS = {
     "qs_circuit_create": (ct.c_int, [ct.c_int, ct.POINTER(_P)]),
     "qs_circuit_destroy": (ct.c_int, [_P]),
     "qs_circuit_add": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.c_int, ct.POINTER(ct.c_double)]),
+    "qs_circuit_add_gates": (ct.c_int, [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                        ct.POINTER(ct.c_double)]),
     "qs_circuit_add_rotation": (ct.c_int, [_P, ct.POINTER(ct.c_int), ct.c_int, ct.c_char_p, ct.c_int,
                                            ct.c_double]),
     "qs_circuit_set_params": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int]),
@@ -286,8 +288,31 @@ class Circuit:
             _call("qs_circuit_create", self.n, ct.byref(h))
             handle = h
         self.handle = handle
+        fixed = []  # runs of fixed gates go to the library in one call
         for g in gates:
-            self.add(g)
+            param = getattr(g, "param", -1)
+            if param is not None and param >= 0:
+                self.add_many(fixed)
+                fixed = []
+                self.add(g)
+            else:
+                fixed.append(g)
+        self.add_many(fixed)
+
+    def add_many(self, gates):
+        """Append fixed gates with one library call (qs_circuit_add_gates)."""
+        if not gates:
+            return
+        ks, qubits, mats = [], [], []
+        for g in gates:
+            qs = g.qubits if hasattr(g, "qubits") else g[0]
+            m = np.asarray(g.matrix if hasattr(g, "matrix") else g[1], dtype=np.complex128)
+            ks.append(len(qs))
+            qubits.extend(int(x) for x in qs)
+            mats.append(m.ravel())
+        flat = np.concatenate(mats)
+        _call("qs_circuit_add_gates", self.handle, len(ks), _ints(ks), _ints(qubits),
+              _dbl(np.stack([flat.real, flat.imag], axis=-1)))
 
     def add(self, g):
         qs = g.qubits if hasattr(g, "qubits") else g[0]

@@ -370,6 +370,39 @@ qs_status qs_circuit_add(qs_circuit* c, const int* qubits, int k, const double* 
     return QS_OK;
 }
 
+qs_status qs_circuit_add_gates(qs_circuit* c, int count, const int* ks, const int* qubits, const double* mats) {
+    if (!c) return fail(QS_ERR_ARG, "null circuit");
+    if (count < 0) return fail(QS_ERR_ARG, "negative gate count");
+    if (count > 0 && (!ks || !qubits || !mats)) return fail(QS_ERR_ARG, "null argument");
+    size_t qo = 0, mo = 0;
+    for (int i = 0; i < count; ++i) {  // every gate checked before any is appended
+        const int k = ks[i];
+        if (k < 1 || k > kMaxK) return fail(QS_ERR_ARG, "gate %d: bad size %d", i, k);
+        qs_status st = check_gate_args(c->n, qubits + qo, k, mats + mo);
+        if (st != QS_OK) {
+            const std::string why = qs_last_error();
+            return fail(st, "gate %d: %s", i, why.c_str());
+        }
+        qo += (size_t)k;
+        mo += 2 * ((size_t)1 << (2 * k));
+    }
+    c->gates.reserve(c->gates.size() + (size_t)count);
+    qo = mo = 0;
+    for (int i = 0; i < count; ++i) {
+        const int k = ks[i];
+        const size_t len = 2 * ((size_t)1 << (2 * k));
+        GateRec g;
+        g.k = k;
+        for (int j = 0; j < k; ++j) g.qubits[j] = qubits[qo + j];
+        g.m.assign(mats + mo, mats + mo + len);
+        g.kind = classify_matrix(k, g.m.data());
+        c->gates.push_back(std::move(g));
+        qo += (size_t)k;
+        mo += len;
+    }
+    return QS_OK;
+}
+
 qs_status qs_circuit_add_rotation(qs_circuit* c, const int* qubits, int k, const char* paulis,
                                   int param, double theta) {
     if (!c || !qubits || !paulis) return fail(QS_ERR_ARG, "null argument");

@@ -52,6 +52,41 @@ def test_circuit_add_rejects_bad_gates(qubits, k):
     assert e.value.status == 1
 
 
+def test_circuit_add_gates_matches_single_adds():
+    """qs_circuit_add_gates appends the same gates (qubits, matrix, kind) as
+    one qs_circuit_add per gate, rotations in between included."""
+    circ = C.scale_grid_circuit(14, 4, seed=3)
+    batched = B.circuit_from(circ)
+    single = B.Circuit(14)
+    for g in circ.gates:
+        single.add(g)
+    a, b = batched.gates(), single.gates()
+    assert len(a) == len(b) == len(circ.gates)
+    for x, y in zip(a, b):
+        assert x[0] == y[0] and x[2] == y[2]
+        assert np.array_equal(x[1], y[1])
+    theta = C.ansatz_theta(6, 2, seed=1)
+    spec = C.ansatz_circuit(6, 2, theta)
+    spec.theta = theta
+    mixed = B.circuit_from(spec)
+    assert mixed.size() == (6, len(spec.gates), theta.size)
+
+
+def test_circuit_add_gates_is_all_or_nothing():
+    c = B.Circuit(12)
+    ks = [1, 2, 1]
+    qubits = [0, 3, 4, 12]            # the third gate's qubit is out of range
+    mats = np.concatenate([np.eye(2).ravel(), np.eye(4).ravel(), np.eye(2).ravel()]).astype(complex)
+    with pytest.raises(B.QsError) as e:
+        B._call("qs_circuit_add_gates", c.handle, 3, B._ints(ks), B._ints(qubits),
+                B._dbl(np.stack([mats.real, mats.imag], axis=-1)))
+    assert e.value.status == 1
+    assert c.size()[1] == 0
+    with pytest.raises(B.QsError):
+        B._call("qs_circuit_add_gates", c.handle, 1, B._ints([7]), B._ints([0]), B._dbl(np.zeros(2)))
+    assert c.size()[1] == 0
+
+
 def test_fuse_rejects_bad_kmax():
     c = B.circuit_from(C.small_grid_circuit())
     for k in (0, 7):
