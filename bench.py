@@ -38,8 +38,8 @@ FALLBACK_HBM_GBS = 6800.0
 # in proportion to the amplitudes, so a launch at n qubits moves
 # bytes_per_amp * 2^n).  Must be cleared when the kernel changes.
 NCU_TRAFFIC_PER_AMP_C64 = {
-    "tensor": None,
-    "tile": None,
+    "tensor": (536.983296e6 + 474.812160e6) / (1 << 26),   # k_gemm6, profiles/k_gemm6_grid26_3xtf32.md
+    "tile": (536.981504e6 + 475.719936e6) / (1 << 26),     # k_rtile, profiles/k_rtile_grid26_k3_fp32.md
     "dense": None,
 }
 
