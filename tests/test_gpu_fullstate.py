@@ -29,13 +29,16 @@ pytestmark = pytest.mark.gpu
 CONFIGS = {
     "c64-3xtf32": ("c64", dict(k_max=6, precision="3xtf32"), 2e-5),
     "c64-fp32-tile": ("c64", dict(k_max=3, precision="fp32"), 2e-5),
-    "c128": ("c128", dict(k_max=4), 1e-12),
+    "c128": ("c128", dict(k_max=4), 1e-12),                # 4-qubit blocks: the FP64 shared-memory tile
+    "c128-ff": ("c128", dict(k_max=3), 1e-12),             # the float-float register tile (the default)
     "c64-tf32": ("c64", dict(k_max=6, precision="tf32"), 4e-3),
     "c64-3xbf16": ("c64", dict(k_max=6, precision="3xbf16"), 6e-5),
     "c64-3xfp16": ("c64", dict(k_max=6, precision="3xfp16"), 2e-5),
     "c64-3xfp16-tiles": ("c64", dict(k_max=6, precision="3xfp16", tensor_tiles=True), 2e-5),
 }
-CASES = [(26, name) for name in CONFIGS] + [(28, "c64-3xtf32"), (28, "c64-3xfp16-tiles"), (28, "c128")]
+CASES = [(26, name) for name in CONFIGS] + [(28, name) for name in
+                                            ("c64-3xtf32", "c64-tf32", "c64-3xbf16", "c64-3xfp16-tiles", "c128",
+                                             "c128-ff")]
 
 _ORACLE = {}
 
