@@ -868,8 +868,11 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
     std::atomic<size_t> next(0);
     int dev = 0;
     cudaGetDevice(&dev);
+    const unsigned cap = set_host_thread_cap(0);
+    set_host_thread_cap(cap);
     auto worker = [&]() {
         cudaSetDevice(dev);
+        set_host_thread_cap(cap);
         for (size_t i = next++; i < invs.size(); i = next++) {
             sts[i] = plan_create_on(&invs[i], dt, &fast, stream, &sw.plans[i]);
             if (sts[i] != QS_OK) msgs[i] = qs_last_error();
@@ -977,27 +980,55 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     // forward and lambda are enqueued first; the reverse sweep is planned on
     // the host while the GPU runs them (plan memory is stream-ordered, so
     // nothing here synchronises)
-    qs_plan* fwd = nullptr;
-    st = plan_create_on(c, psi->dt, &fast, sm, &fwd);
-    if (st != QS_OK) return st;
-    cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
-    if (le != cudaSuccess) {
-        qs_plan_destroy(fwd);
-        return cuda_fail(le, "init");
+    // The reverse sweep is planned on a host thread of its own while this
+    // thread enqueues the forward and lambda (it reads only the gate list).
+    AdjointSweep sw;
+    struct Releaser {  // on every return, after the planner thread has joined
+        AdjointSweep& s;
+        ~Releaser() { s.release(); }
+    } releaser{sw};
+    qs_status sweep_st = QS_OK;
+    std::string sweep_msg;
+    struct Joiner {
+        std::thread t;
+        ~Joiner() {
+            if (t.joinable()) t.join();
+        }
+    } planner;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned cap = set_host_thread_cap(0);
+    set_host_thread_cap(cap);
+    planner.t = std::thread([&, dev, cap]() {
+        cudaSetDevice(dev);  // the caller's device and thread cap hold on this thread too
+        set_host_thread_cap(cap);
+        sweep_st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sm, sw);
+        if (sweep_st != QS_OK) sweep_msg = qs_last_error();
+    });
+    if (fast.k_max == 6) {  // on the tensor cores: fused and run together (the GPU starts at once)
+        cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
+        if (le != cudaSuccess) return cuda_fail(le, "init");
+        st = apply_streamed(psi, c, fast);
+        if (st != QS_OK) return st;
+    } else {
+        qs_plan* fwd = nullptr;
+        st = plan_create_on(c, psi->dt, &fast, sm, &fwd);
+        if (st != QS_OK) return st;
+        cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
+        if (le != cudaSuccess) {
+            qs_plan_destroy(fwd);
+            return cuda_fail(le, "init");
+        }
+        st = qs_plan_execute(psi, fwd);
+        qs_plan_destroy(fwd);  // freed in stream order, after the forward passes
+        if (st != QS_OK) return st;
     }
-    st = qs_plan_execute(psi, fwd);
-    qs_plan_destroy(fwd);  // freed in stream order, after the forward passes
-    if (st != QS_OK) return st;
     // lambda = H psi; E = <psi|lambda>
     QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
     double* res = result_area(psi);
     QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
-    AdjointSweep sw;
-    st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sm, sw);
-    if (st != QS_OK) {
-        sw.release();
-        return st;
-    }
+    planner.t.join();
+    if (sweep_st != QS_OK) return fail(sweep_st, "%s", sweep_msg.c_str());
     const int nb = reduce_blocks();
     const int rows = std::max(num_params, 1);
     st = run_reverse_sweep(sw, psi, lam, nb, rows, sm);

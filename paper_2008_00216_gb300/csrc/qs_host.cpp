@@ -614,53 +614,146 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
     return cudaErrorInvalidValue;
 }
 
-// Fuse and run together (qs_apply_circuit on the tensor cores): a host thread
-// runs the block search and hands over each group as soon as it is found;
-// this thread forms the group's block and pass (each block its own pass),
-// uploads the pass's matrix and launches it in stream order, so the GPU runs
-// pass i while the search looks for block i + 1.  Passes wait in a short
-// look-ahead window so that the bit-0 placement of the planned path
-// (bit0_plan) can keep qubit 0 out of the 6-qubit passes' targets here too:
-// the window's leading run of 6-qubit passes is planned from the current
-// exchange state, the first pass is committed and launched.
-static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
-    constexpr size_t kWindow = 3;  // passes formed ahead of the one launched
+// Pinned host staging for the streamed path's matrix uploads (a copy from
+// pageable memory may wait for the stream's earlier work before it is
+// staged).  One buffer per host thread, reused once the stream has consumed
+// the previous call's copies.
+namespace {
+struct PinnedStage {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;  // recorded after the last copy out of the buffer
+    int dev = -1;
+    ~PinnedStage() {
+        if (done) cudaEventSynchronize(done);
+        if (p) cudaFreeHost(p);
+        if (done) cudaEventDestroy(done);
+    }
+    cudaError_t reserve(size_t bytes, int device) {
+        if (done) {
+            cudaError_t e = cudaEventSynchronize(done);
+            if (e != cudaSuccess) return e;
+        }
+        if (dev != device && done) {
+            cudaEventDestroy(done);
+            done = nullptr;
+        }
+        if (!done) {
+            cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            dev = device;
+        }
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+};
+thread_local PinnedStage t_stage;
+}  // namespace
+
+// Fuse and run together (qs_apply_circuit and the adjoint gradient's forward
+// on the tensor cores): a host thread runs the block search and hands over
+// each group as soon as it is found (all at once when the circuit's grouping
+// is cached); worker threads form the groups' blocks (FP64 products) and
+// passes in parallel; this thread uploads each pass's matrix through pinned
+// staging and launches the passes in order, so the GPU runs pass i while
+// later blocks are being found and multiplied.  Passes wait in a look-ahead
+// window so that the bit-0 placement of the planned path (bit0_plan) can
+// keep qubit 0 out of the 6-qubit passes' targets here too: the window's
+// leading run of 6-qubit passes is planned from the current exchange state,
+// the first pass is committed and launched.  The window grows with the
+// passes already queued (so the GPU starts at once) and spans up to 8 passes
+// once the search is done.
+qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
+    constexpr size_t kWindow = 3, kWindowDone = 8;
+    const int n = c->n;
+    const size_t esz = s->amp_bytes();
     std::mutex mu;
     std::condition_variable cv;
-    std::deque<std::vector<int>> queue;
-    bool done = false;
+    std::vector<std::vector<int>> groups;           // in search order
+    std::vector<std::unique_ptr<Pass>> formed;      // formed[i]: the pass of group i, once ready
+    size_t next_group = 0;                          // the next group a worker takes
+    bool done = false, stop = false;
     qs_status fst = QS_OK;
     std::string fmsg;
     std::thread search([&]() {
-        const qs_status st = fuse_each(c->n, c->gates, opt.k_max, opt.fusion_effort, c->fuse_cache.get(),
+        const qs_status st = fuse_each(n, c->gates, opt.k_max, opt.fusion_effort, c->fuse_cache.get(),
                                        [&](std::vector<int>&& g) {
                                            std::lock_guard<std::mutex> lk(mu);
-                                           queue.push_back(std::move(g));
-                                           cv.notify_one();
+                                           groups.push_back(std::move(g));
+                                           formed.emplace_back();
+                                           cv.notify_all();
                                        });
         std::lock_guard<std::mutex> lk(mu);
         fst = st;
         if (st != QS_OK) fmsg = qs_last_error();
         done = true;
-        cv.notify_one();
+        cv.notify_all();
     });
+    auto worker = [&]() {
+        for (;;) {
+            std::vector<int> g;
+            size_t i;
+            {
+                std::unique_lock<std::mutex> lk(mu);
+                cv.wait(lk, [&]() { return stop || next_group < groups.size() || done; });
+                if (stop || next_group >= groups.size()) {
+                    if (stop || done) return;
+                    continue;
+                }
+                i = next_group++;
+                g = groups[i];
+            }
+            GateRec b;
+            block_product(n, c->gates, g, b);
+            std::unique_ptr<Pass> p(new Pass);
+            single_block_pass(n, s->dt, opt, b, *p);
+            factor_tile_scalars(*p);
+            std::lock_guard<std::mutex> lk(mu);
+            formed[i] = std::move(p);
+            cv.notify_all();
+        }
+    };
+    std::vector<std::thread> workers;
+    const unsigned nw = std::max(1u, std::min(4u, host_threads(4)));
+    for (unsigned w = 0; w < nw; ++w) workers.emplace_back(worker);
+
     qs_status st = QS_OK;
-    const int n = c->n;
-    const size_t esz = s->amp_bytes();
-    std::vector<char> host;
+    int dev = 0;
+    cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaSuccess) ge = t_stage.reserve(2u << 20, dev);  // 64 complex64 6-qubit matrices
+    if (ge != cudaSuccess) st = cuda_fail(ge, "pinned staging");
+    size_t stage_at = 0;  // bytes of the staging buffer used by this call
     auto launch_one = [&](Pass& p) {
         void* dm = nullptr;
         const size_t elems = p.mats.size() / 2;
         cudaError_t e = cudaSuccess;
         if (elems && p.kind != PASS_DENSE && p.kind != PASS_DIAG && p.kind != PASS_MONO) {
-            host.resize(elems * esz);
-            for (size_t i = 0; i < p.mats.size(); ++i) {
-                if (s->dt == QS_C64) ((float*)host.data())[i] = (float)p.mats[i];
-                else ((double*)host.data())[i] = p.mats[i];
+            const size_t bytes = elems * esz;
+            const void* src;
+            std::vector<char> host;
+            if (stage_at + bytes <= t_stage.cap) {  // pinned: the copy is fully asynchronous
+                char* dst = t_stage.p + stage_at;
+                for (size_t i = 0; i < p.mats.size(); ++i) {
+                    if (s->dt == QS_C64) ((float*)dst)[i] = (float)p.mats[i];
+                    else ((double*)dst)[i] = p.mats[i];
+                }
+                src = dst;
+                stage_at += (bytes + 255) & ~(size_t)255;
+            } else {  // beyond the staging buffer: a pageable source, staged by the driver
+                host.resize(bytes);
+                for (size_t i = 0; i < p.mats.size(); ++i) {
+                    if (s->dt == QS_C64) ((float*)host.data())[i] = (float)p.mats[i];
+                    else ((double*)host.data())[i] = p.mats[i];
+                }
+                src = host.data();
             }
-            // stream-ordered; a pageable source is staged before the call returns
-            e = cudaMallocAsync(&dm, elems * esz, s->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dm, host.data(), elems * esz, cudaMemcpyHostToDevice, s->stream);
+            e = cudaMallocAsync(&dm, bytes, s->stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(dm, src, bytes, cudaMemcpyHostToDevice, s->stream);
         }
         if (e == cudaSuccess) e = launch_pass(s, p, dm, opt.precision);
         if (dm) cudaFreeAsync(dm, s->stream);
@@ -682,9 +775,10 @@ static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_optio
         xs = -1;
     };
     std::deque<Pass> pending;
-    size_t launched = 0;  // the window grows with the passes already queued, so the GPU starts at once
-    auto drain = [&](bool final) {
-        while (st == QS_OK && !pending.empty() && (final || pending.size() > std::min(kWindow, launched))) {
+    size_t launched = 0;
+    auto drain = [&](bool final, bool search_done) {
+        const size_t win = search_done ? kWindowDone : std::min(kWindow, launched);
+        while (st == QS_OK && !pending.empty() && (final || pending.size() > win)) {
             Pass& p0 = pending.front();
             if (p0.kind == PASS_GEMM) {
                 std::vector<const Pass*> run;
@@ -708,27 +802,30 @@ static qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_optio
         }
         if (final && st == QS_OK && xs >= 0) restore();
     };
-    for (;;) {
-        std::vector<int> g;
+    for (size_t i = 0;; ++i) {
+        std::unique_ptr<Pass> p;
+        bool search_done;
         {
             std::unique_lock<std::mutex> lk(mu);
-            cv.wait(lk, [&]() { return !queue.empty() || done; });
-            if (queue.empty()) break;
-            g = std::move(queue.front());
-            queue.pop_front();
+            cv.wait(lk, [&]() { return (i < formed.size() && formed[i]) || (done && i >= groups.size()); });
+            if (i >= groups.size()) break;
+            p = std::move(formed[i]);
+            search_done = done;
         }
-        if (st != QS_OK) continue;  // drain the search after a failure
-        GateRec b;
-        block_product(n, c->gates, g, b);
-        Pass p;
-        single_block_pass(n, s->dt, opt, b, p);
-        factor_tile_scalars(p);
-        pending.push_back(std::move(p));
-        drain(false);
+        if (st != QS_OK) continue;  // drain the search and workers after a failure
+        pending.push_back(std::move(*p));
+        drain(false, search_done);
     }
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        stop = true;
+        cv.notify_all();
+    }
+    for (auto& w : workers) w.join();
     search.join();
     if (fst != QS_OK) return fail(fst, "%s", fmsg.c_str());
-    drain(true);
+    drain(true, true);
+    if (t_stage.done) cudaEventRecord(t_stage.done, s->stream);  // the staging buffer is free once this passes
     return st;
 }
 

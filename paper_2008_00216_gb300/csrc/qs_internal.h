@@ -252,6 +252,9 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
                        const qs_options& opt, std::vector<Pass>& passes);
 // The pass of one fused block on its own (no tile grouping).
 void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec& g, Pass& p);
+// Fuse and run together on the tensor cores: each block's pass is launched
+// as soon as it is found and multiplied (qs_host.cpp)
+qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt);
 // bit-0 placement over 6-qubit passes (qs_plan.cpp)
 int bit0_plan(int n, const std::vector<const Pass*>& run, int s0, bool end_free, std::vector<int>& choice);
 int bit0_apply(Pass& p, int s, int bc);
