@@ -119,6 +119,36 @@ static void conj_transpose(const GateRec& g, GateRec& u) {
     u.kind = classify_matrix(g.k, u.m.data());
 }
 
+// t[j] (j = 0 .. 255, the bits of the 8-qubit chunk c0) times the diagonal
+// entry of u that j's bits select; u's qubits all lie in the chunk
+static void scale_chunk_table(std::complex<double>* t, const GateRec& u, int c0) {
+    const int k = u.k, d = 1 << k;
+    double er[1 << kMaxK], ei[1 << kMaxK];
+    int sh[kMaxK];
+    for (int l = 0; l < d; ++l) {
+        er[l] = u.m[2 * (l * d + l)];
+        ei[l] = u.m[2 * (l * d + l) + 1];
+    }
+    for (int i = 0; i < k; ++i) sh[i] = u.qubits[i] - 8 * c0;
+    auto scale = [&](auto index) {
+        for (int j = 0; j < 256; ++j) {
+            const int l = index(j);
+            const double ar = t[j].real(), ai = t[j].imag();
+            t[j] = std::complex<double>(ar * er[l] - ai * ei[l], ar * ei[l] + ai * er[l]);
+        }
+    };
+    if (k == 1)
+        scale([&](int j) { return (j >> sh[0]) & 1; });
+    else if (k == 2)
+        scale([&](int j) { return (((j >> sh[0]) & 1) << 1) | ((j >> sh[1]) & 1); });
+    else
+        scale([&](int j) {
+            int l = 0;
+            for (int i = 0; i < k; ++i) l = (l << 1) | ((j >> sh[i]) & 1);
+            return l;
+        });
+}
+
 static bool generator_diagonal(const GateRec& g) {
     for (int i = 0; g.param >= 0 && i < g.k; ++i)
         if (g.paulis[i] == 'X' || g.paulis[i] == 'Y') return false;
@@ -280,11 +310,7 @@ static void add_diag_stage(const std::vector<const GateRec*>& gates, int n, Adjo
         bool one_chunk = true;
         for (int i = 1; i < k; ++i) one_chunk = one_chunk && (u.qubits[i] >> 3) == c0;
         if (one_chunk) {
-            for (int j = 0; j < 256; ++j) {
-                int l = 0;
-                for (int i = 0; i < k; ++i) l = (l << 1) | ((j >> (u.qubits[i] - 8 * c0)) & 1);
-                tab[256 * c0 + j] *= std::complex<double>(u.m[2 * (l * d + l)], u.m[2 * (l * d + l) + 1]);
-            }
+            scale_chunk_table(tab.data() + 256 * c0, u, c0);
         } else {
             DiagCross x{};
             x.k = (uint8_t)k;
@@ -319,10 +345,10 @@ struct DiagCost {
     uint32_t tab = 0;
     int cross = 0, gens = 0;
 };
-static DiagCost fused_diag_cost(const qs_circuit& c, const std::vector<int>& diag, int n) {
+static DiagCost fused_diag_cost(const qs_circuit& c, const std::vector<int>& diag, int n, int RB) {
     DiagCost dc;
     if (diag.empty()) return dc;
-    dc.tab = 256u * (uint32_t)((n + 7) / 8);
+    dc.tab = 256u * (uint32_t)((n + 7) / 8) + (256u >> RB);  // chunk 0 padded (see compile_fused_diag)
     for (int gi : diag) {
         const GateRec& g = c.gates[gi];
         bool one_chunk = true;
@@ -362,11 +388,7 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
             touched = touched || ((rmask >> u.qubits[i]) & 1);
         }
         if (one_chunk) {
-            for (int j = 0; j < 256; ++j) {
-                int l = 0;
-                for (int i = 0; i < k; ++i) l = (l << 1) | ((j >> (u.qubits[i] - 8 * c0)) & 1);
-                tab[256 * c0 + j] *= std::complex<double>(u.m[2 * (l * dd + l)], u.m[2 * (l * dd + l) + 1]);
-            }
+            scale_chunk_table(tab.data() + 256 * c0, u, c0);
         } else {
             Cross x{};
             x.x.k = (uint8_t)k;
@@ -375,6 +397,21 @@ static void compile_fused_diag(const qs_circuit& c, const std::vector<int>& diag
             x.touched = touched;
             cross.push_back(std::move(x));
         }
+    }
+    // Chunk 0 is read with the register bits (qubits 0 .. RB-1) as its low
+    // index bits and thread bits above them: each row of 2^RB entries is
+    // padded by one, so the lanes of a warp, which read different rows at
+    // the same column, fall in different shared-memory banks.
+    {
+        const int per = 1 << RB;
+        std::vector<std::complex<double>> padded;
+        padded.reserve(tab.size() + (256 >> RB));
+        for (int r = 0; r < (256 >> RB); ++r) {
+            padded.insert(padded.end(), tab.begin() + r * per, tab.begin() + (r + 1) * per);
+            padded.push_back(1.0);
+        }
+        padded.insert(padded.end(), tab.begin() + 256, tab.end());
+        tab.swap(padded);
     }
     // the gates that hold a register qubit first: the kernel looks those up per amplitude
     std::stable_partition(cross.begin(), cross.end(), [](const Cross& x) { return x.touched; });
@@ -536,7 +573,7 @@ static qs_status add_fused_run(const qs_circuit& c, const std::vector<FusedStage
         for (;;) {
             Step st{(int)si, false, {}};
             if (!diag_done) {
-                const DiagCost dc = fused_diag_cost(c, run[si].diag, n);
+                const DiagCost dc = fused_diag_cost(c, run[si].diag, n, RB);
                 if (ndiag + 1 > kSweepMaxDiags || tabs + dc.tab > budget || ncross + dc.cross > kSweepMaxCross ||
                     ngens + dc.gens > kSweepMaxGens || ngrad + dc.gens > kSweepMaxGrads ||
                     nops + 1 + nlay > kSweepMaxOps)
@@ -819,7 +856,7 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
             else fused_ok = false;
         }
         if (fused_ok) {
-            const DiagCost dc = fused_diag_cost(c, fs.diag, n);
+            const DiagCost dc = fused_diag_cost(c, fs.diag, n, fused_L - 8);
             fused_ok = dc.tab <= sweep_tab_budget(dt) && dc.cross <= kSweepDiagCross && dc.gens <= kSweepDiagGens;
         }
         if (fused_ok) {
@@ -953,11 +990,14 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     if (psi->data == lam->data) return fail(QS_ERR_ARG, "psi and lambda must be distinct");
     if (num_params != c->num_params)
         return fail(QS_ERR_ARG, "circuit has %d parameters, %d given", c->num_params, num_params);
-    for (const GateRec& g : c->gates)
-        if (g.param >= 0)
-            for (const GateRec& g2 : c->gates)
-                if (&g2 != &g && g2.param == g.param)
-                    return fail(QS_ERR_UNSUPPORTED, "parameter %d is shared by several gates", g.param);
+    {
+        std::vector<char> seen(c->num_params, 0);
+        for (const GateRec& g : c->gates)
+            if (g.param >= 0) {
+                if (seen[g.param]) return fail(QS_ERR_UNSUPPORTED, "parameter %d is shared by several gates", g.param);
+                seen[g.param] = 1;
+            }
+    }
     if (num_params) {
         st = qs_circuit_set_params(c, theta, num_params);
         if (st != QS_OK) return st;
@@ -977,11 +1017,9 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     // the full block search (fewer blocks); its grouping is cached on the
     // circuit, so repeated gradients (new angles, same gates) skip it
     fast.fusion_effort = 1;
-    // forward and lambda are enqueued first; the reverse sweep is planned on
-    // the host while the GPU runs them (plan memory is stream-ordered, so
-    // nothing here synchronises)
-    // The reverse sweep is planned on a host thread of its own while this
-    // thread enqueues the forward and lambda (it reads only the gate list).
+    // The forward and lambda are enqueued first while the reverse sweep is
+    // planned on a host thread of its own (it reads only the gate list; plan
+    // memory is stream-ordered, so nothing here synchronises).
     AdjointSweep sw;
     struct Releaser {  // on every return, after the planner thread has joined
         AdjointSweep& s;
@@ -995,16 +1033,24 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
             if (t.joinable()) t.join();
         }
     } planner;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned cap = set_host_thread_cap(0);
-    set_host_thread_cap(cap);
-    planner.t = std::thread([&, dev, cap]() {
-        cudaSetDevice(dev);  // the caller's device and thread cap hold on this thread too
-        set_host_thread_cap(cap);
+    auto plan_sweep = [&]() {
         sweep_st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sm, sw);
         if (sweep_st != QS_OK) sweep_msg = qs_last_error();
-    });
+    };
+    // (with the host threads capped at one, as inside a batch of gradients
+    // that run in parallel, it is planned here after the forward is enqueued)
+    const bool own_thread = host_threads(2) >= 2;
+    if (own_thread) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        const unsigned cap = set_host_thread_cap(0);
+        set_host_thread_cap(cap);
+        planner.t = std::thread([&, dev, cap]() {
+            cudaSetDevice(dev);  // the caller's device and thread cap hold on this thread too
+            set_host_thread_cap(cap);
+            plan_sweep();
+        });
+    }
     if (fast.k_max == 6) {  // on the tensor cores: fused and run together (the GPU starts at once)
         cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
         if (le != cudaSuccess) return cuda_fail(le, "init");
@@ -1027,7 +1073,8 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     QS_CUDA(launch_apply_pauli_sum(psi->data, lam->data, psi->n, psi->dt, *h, sm));
     double* res = result_area(psi);
     QS_CUDA(launch_inner(psi->data, lam->data, psi->n, psi->dt, psi->scratch, res, sm));
-    planner.t.join();
+    if (own_thread) planner.t.join();
+    else plan_sweep();
     if (sweep_st != QS_OK) return fail(sweep_st, "%s", sweep_msg.c_str());
     const int nb = reduce_blocks();
     const int rows = std::max(num_params, 1);

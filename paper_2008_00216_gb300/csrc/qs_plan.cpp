@@ -103,12 +103,13 @@ static inline uint64_t qmask(const GateRec& g) {
     return m;
 }
 
-// Multiply gate g (on its qubits) into the block matrix `acc` whose local
-// bit b corresponds to qubit bq[K-1-b] (bq listed most significant first):
-// acc <- E(g) acc.  For each row set r (the gate's bits zero) the 2^k rows
-// r | l mix as (g.m) x (those rows), for all D columns at once; complex
-// products are written out in real arithmetic.
-static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector<cd>& acc) {
+// Multiply gate g (on its qubits) into the block matrix acc = R + i I
+// (real and imaginary parts apart, row-major D x D, so the column loops
+// vectorise) whose local bit b corresponds to qubit bq[K-1-b] (bq listed
+// most significant first): acc <- E(g) acc.  For each row set r (the gate's
+// bits zero) the 2^k rows r | l mix as (g.m) x (those rows), for all D
+// columns at once; complex products are written out in real arithmetic.
+static void apply_into_block(const GateRec& g, int K, const int* bq, double* R, double* I) {
     const int D = 1 << K, d = 1 << g.k;
     int lpos[kMaxK];  // local bit of each gate qubit
     for (int i = 0; i < g.k; ++i) {
@@ -126,40 +127,67 @@ static void apply_into_block(const GateRec& g, int K, const int* bq, std::vector
         rowof[l] = idx;
     }
     const double* m = g.m.data();
-    double* A = reinterpret_cast<double*>(acc.data());  // interleaved, row-major D x D
     if (g.kind == QS_GATE_DIAGONAL) {  // scale each row by its diagonal entry
         for (int r = 0; r < D; ++r) {
             int l = 0;
             for (int i = 0; i < g.k; ++i) l = (l << 1) | ((r >> lpos[i]) & 1);
             const double mr = m[2 * (l * d + l)], mi = m[2 * (l * d + l) + 1];
             if (mr == 1.0 && mi == 0.0) continue;
-            double* row = A + 2 * (size_t)r * D;
+            double* xr = R + (size_t)r * D;
+            double* xi = I + (size_t)r * D;
             for (int c = 0; c < D; ++c) {
-                const double xr = row[2 * c], xi = row[2 * c + 1];
-                row[2 * c] = mr * xr - mi * xi;
-                row[2 * c + 1] = mr * xi + mi * xr;
+                const double a = xr[c], b = xi[c];
+                xr[c] = mr * a - mi * b;
+                xi[c] = mr * b + mi * a;
             }
         }
         return;
     }
-    std::vector<double> in(2 * (size_t)d * D);
+    if (g.k == 1) {  // in place: each row pair (r, r | bit) mixes as a 2 x 2
+        const double m00r = m[0], m00i = m[1], m01r = m[2], m01i = m[3];
+        const double m10r = m[4], m10i = m[5], m11r = m[6], m11i = m[7];
+        const int bit = 1 << lpos[0];
+        for (int r = 0; r < D; ++r) {
+            if (r & bit) continue;
+            double* __restrict__ r0 = R + (size_t)r * D;
+            double* __restrict__ i0 = I + (size_t)r * D;
+            double* __restrict__ r1 = R + (size_t)(r | bit) * D;
+            double* __restrict__ i1 = I + (size_t)(r | bit) * D;
+            for (int c = 0; c < D; ++c) {
+                const double ar = r0[c], ai = i0[c], br = r1[c], bi = i1[c];
+                r0[c] = (m00r * ar - m00i * ai) + (m01r * br - m01i * bi);
+                i0[c] = (m00r * ai + m00i * ar) + (m01r * bi + m01i * br);
+                r1[c] = (m10r * ar - m10i * ai) + (m11r * br - m11i * bi);
+                i1[c] = (m10r * ai + m10i * ar) + (m11r * bi + m11i * br);
+            }
+        }
+        return;
+    }
+    thread_local std::vector<double> inr, ini;
+    inr.resize((size_t)d * D);
+    ini.resize((size_t)d * D);
     for (int r = 0; r < D; ++r) {
         if (r & gmask) continue;
-        for (int l = 0; l < d; ++l)
-            std::copy(A + 2 * (size_t)(r | rowof[l]) * D, A + 2 * (size_t)((r | rowof[l]) + 1) * D,
-                      in.begin() + 2 * (size_t)l * D);
+        for (int l = 0; l < d; ++l) {
+            const size_t row = (size_t)(r | rowof[l]) * D;
+            std::copy(R + row, R + row + D, inr.begin() + (size_t)l * D);
+            std::copy(I + row, I + row + D, ini.begin() + (size_t)l * D);
+        }
         for (int lo = 0; lo < d; ++lo) {
-            double* out = A + 2 * (size_t)(r | rowof[lo]) * D;
+            double* __restrict__ outr = R + (size_t)(r | rowof[lo]) * D;
+            double* __restrict__ outi = I + (size_t)(r | rowof[lo]) * D;
             for (int c = 0; c < D; ++c) {
-                double sr = 0.0, si = 0.0;
-                for (int li = 0; li < d; ++li) {
-                    const double mr = m[2 * (lo * d + li)], mi = m[2 * (lo * d + li) + 1];
-                    const double xr = in[2 * ((size_t)li * D + c)], xi = in[2 * ((size_t)li * D + c) + 1];
-                    sr += mr * xr - mi * xi;
-                    si += mr * xi + mi * xr;
+                outr[c] = 0.0;
+                outi[c] = 0.0;
+            }
+            for (int li = 0; li < d; ++li) {
+                const double mr = m[2 * (lo * d + li)], mi = m[2 * (lo * d + li) + 1];
+                const double* __restrict__ xr = inr.data() + (size_t)li * D;
+                const double* __restrict__ xi = ini.data() + (size_t)li * D;
+                for (int c = 0; c < D; ++c) {
+                    outr[c] += mr * xr[c] - mi * xi[c];
+                    outi[c] += mr * xi[c] + mi * xr[c];
                 }
-                out[2 * c] = sr;
-                out[2 * c + 1] = si;
             }
         }
     }
@@ -498,13 +526,50 @@ void block_product(int n, const std::vector<GateRec>& in, const std::vector<int>
         if ((support >> q) & 1) bq[j++] = q;  // descending: qubits[0] most significant
     for (int i = 0; i < b.k; ++i) b.qubits[i] = bq[i];
     const int D = 1 << b.k;
-    std::vector<cd> acc(D * D, 0.0);
-    for (int i = 0; i < D; ++i) acc[i * D + i] = 1.0;
-    for (int t : taken) apply_into_block(in[t], b.k, bq, acc);
+    std::vector<double> accr((size_t)D * D, 0.0), acci((size_t)D * D, 0.0);
+    for (int i = 0; i < D; ++i) accr[(size_t)i * D + i] = 1.0;
+    // one-qubit gates that follow each other on a qubit (no member in between
+    // touches it) are multiplied as 2 x 2 matrices first, then applied once
+    GateRec one;  // the pending one-qubit product
+    bool have = false;
+    auto flush_one = [&]() {
+        if (have) apply_into_block(one, b.k, bq, accr.data(), acci.data());
+        have = false;
+    };
+    for (int t : taken) {
+        const GateRec& g = in[t];
+        if (g.k == 1 && have && g.qubits[0] == one.qubits[0]) {  // one <- g * one
+            const double* x = g.m.data();
+            double y[8];
+            for (int r = 0; r < 2; ++r)
+                for (int c2 = 0; c2 < 2; ++c2) {
+                    const double ar = x[2 * (2 * r)], ai = x[2 * (2 * r) + 1], br = x[2 * (2 * r + 1)],
+                                 bi = x[2 * (2 * r + 1) + 1];
+                    const double pr = one.m[2 * c2], pi = one.m[2 * c2 + 1], qr = one.m[2 * (2 + c2)],
+                                 qi = one.m[2 * (2 + c2) + 1];
+                    y[2 * (2 * r + c2)] = (ar * pr - ai * pi) + (br * qr - bi * qi);
+                    y[2 * (2 * r + c2) + 1] = (ar * pi + ai * pr) + (br * qi + bi * qr);
+                }
+            std::copy(y, y + 8, one.m.begin());
+            one.kind = QS_GATE_DENSE;
+            continue;
+        }
+        flush_one();
+        if (g.k == 1) {
+            one.k = 1;
+            one.qubits[0] = g.qubits[0];
+            one.m.assign(g.m.begin(), g.m.begin() + 8);
+            one.kind = g.kind;
+            have = true;
+            continue;
+        }
+        apply_into_block(g, b.k, bq, accr.data(), acci.data());
+    }
+    flush_one();
     b.m.resize(2 * D * D);
     for (int i = 0; i < D * D; ++i) {
-        b.m[2 * i] = acc[i].real();
-        b.m[2 * i + 1] = acc[i].imag();
+        b.m[2 * i] = accr[i];
+        b.m[2 * i + 1] = acci[i];
     }
     b.kind = classify_matrix(b.k, b.m.data());
 }

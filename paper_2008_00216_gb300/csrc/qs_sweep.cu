@@ -418,7 +418,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                 T pc;  // chunks 1.. and the cross gates without a register qubit
                 pc.x = 1;
                 pc.y = 0;
-                for (int c = 1; c < d.nchunks; ++c) pc = cmul(pc, dtab[256 * c + ((xt >> (8 * c)) & 255)]);
+                for (int c = 1; c < d.nchunks; ++c) pc = cmul(pc, dtab[256 * c + (256 >> RB) + ((xt >> (8 * c)) & 255)]);
                 pc = cross_phase(a.cross + d.cross0 + d.nct, d.ncross - d.nct, tab, xt, pc);
                 R tsum = 0, u[RB];
 #pragma unroll
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass(typename C2<R>::T* _
                         red[z.local] += (__popcll(base & z.mthr) & 1) ? -v : v;
                     }
                 }
-                const T* t0 = dtab + (xt & 255);  // chunk 0: the thread's bits, plus j
+                const T* t0 = dtab + ((xt & 255) >> RB) * (PER + 1);  // chunk 0 (padded rows): the thread's row, plus j
 #pragma unroll
                 for (int j = 0; j < PER; ++j) {
                     T ph = cmul(pc, t0[j]);
@@ -788,7 +788,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
                 FFC pc;  // chunks 1.. and the cross gates without a register qubit
                 pc.h = make_float2(1.f, 0.f);
                 pc.l = make_float2(0.f, 0.f);
-                for (int c = 1; c < d.nchunks; ++c) pc = ff_cmul(pc, dtab[256 * c + ((xt >> (8 * c)) & 255)]);
+                for (int c = 1; c < d.nchunks; ++c) pc = ff_cmul(pc, dtab[256 * c + (256 >> RB) + ((xt >> (8 * c)) & 255)]);
                 pc = ff_cross_phase(a.cross + d.cross0 + d.nct, d.ncross - d.nct, tab, xt, pc);
                 // Im(conj(l) p) per element as float-float, and the sums over
                 // the thread's elements (all, and those with register bit i set)
@@ -884,7 +884,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_sweep_pass_ff(double2* __restri
                     }
                     __syncthreads();  // dred is reused by the next diagonal op
                 }
-                const FFC* t0 = dtab + (xt & 255);  // chunk 0: the thread's bits, plus j
+                const FFC* t0 = dtab + ((xt & 255) >> RB) * (PER + 1);  // chunk 0 (padded rows): the thread's row, plus j
 #pragma unroll
                 for (int j = 0; j < PER; ++j) {
                     FFC ph = ff_cmul(pc, t0[j]);
