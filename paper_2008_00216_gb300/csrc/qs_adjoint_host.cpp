@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <complex>
 #include <string>
@@ -925,6 +926,164 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
     return QS_OK;
 }
 
+// ------------------------------------------------------------ block sweep
+// Complex64 gradients on the tensor cores (qs_gram.cu).  The sweep undoes
+// the forward's fused blocks one at a time, B^dagger on psi and on lambda as
+// tensor-core passes, and every gradient inside a block comes from its Gram
+// matrix M = sum_s psi_s lambda_s^dagger over the block's six qubits, taken
+// just before: <lambda_l|P_l|psi_l> = tr(P_l M_l) with M_l = W^dagger M W, W
+// the block's gates after gate l (Section 4.5's sweep, one block per step).
+struct BlockSweep {
+    std::vector<GateRec> blocks;              // the forward blocks B, last first
+    std::vector<Pass> passes;                 // their B^dagger passes, in the same order
+    qs_plan* inv = nullptr;                   // those passes, uploaded
+    std::vector<int> slot;                    // per pass: Gram slot, or -1 (no generator in the block)
+    std::vector<std::array<int, 6>> targets;  // per slot: the Gram's six qubits, descending
+    std::vector<BlockGradGate> gates;         // per slot: the block's gates, last to first
+    std::vector<int> gate0;                   // slot ranges (slots + 1)
+    std::vector<float> gmats;                 // complex64 gate matrices
+    void release() {
+        if (inv) qs_plan_destroy(inv);
+        inv = nullptr;
+    }
+};
+
+// Plan the block sweep; QS_ERR_UNSUPPORTED when a group is not one block of
+// at most six qubits (wide diagonal clusters), so the stage sweep is used.
+static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options& fast, BlockSweep& bs) {
+    std::vector<std::vector<int>> groups;
+    qs_status st = fuse_each(n, c.gates, 6, fast.fusion_effort, c.fuse_cache.get(),
+                             [&](std::vector<int>&& g) { groups.push_back(std::move(g)); });
+    if (st != QS_OK) return st;
+    const size_t G = groups.size();
+    std::vector<GateRec> blocks(G);
+    std::vector<Pass> fwd_inv(G);
+    std::vector<char> bad(G, 0);
+    std::atomic<size_t> next(0);
+    auto work = [&]() {
+        for (size_t i = next++; i < G; i = next++) {
+            block_product(n, c.gates, groups[i], blocks[i]);
+            if (blocks[i].k == 0) {
+                bad[i] = 1;
+                continue;
+            }
+            GateRec binv;
+            conj_transpose(blocks[i], binv);
+            single_block_pass(n, QS_C64, fast, binv, fwd_inv[i]);
+            factor_tile_scalars(fwd_inv[i]);
+        }
+    };
+    {
+        const size_t nt = std::min<size_t>(host_threads(4), G);
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < nt; ++t) pool.emplace_back(work);
+        work();
+        for (auto& th : pool) th.join();
+    }
+    for (size_t i = 0; i < G; ++i)
+        if (bad[i]) return QS_ERR_UNSUPPORTED;
+    bs.passes.reserve(G);
+    bs.gate0.assign(1, 0);
+    for (size_t r = 0; r < G; ++r) {
+        const size_t i = G - 1 - r;  // the sweep runs the blocks last to first
+        const std::vector<int>& g = groups[i];
+        std::vector<int> members;
+        if (g[0] < 0) members.push_back(-1 - g[0]);
+        else members = g;
+        bool has_param = false;
+        for (int gi : members) has_param = has_param || c.gates[gi].param >= 0;
+        bs.passes.push_back(std::move(fwd_inv[i]));
+        if (!has_param) {
+            bs.slot.push_back(-1);
+            continue;
+        }
+        // Gram qubits: the block's, then the highest others (low qubits stay
+        // set bits, so a set's neighbours are adjacent amplitudes)
+        uint64_t used = 0;
+        for (int t = 0; t < blocks[i].k; ++t) used |= 1ull << blocks[i].qubits[t];
+        for (int q = n - 1; q >= 0 && __builtin_popcountll(used) < 6; --q) used |= 1ull << q;
+        std::array<int, 6> T{};
+        int cnt = 0;
+        for (int q = n - 1; q >= 0; --q)
+            if ((used >> q) & 1) T[cnt++] = q;
+        bs.slot.push_back((int)bs.targets.size());
+        bs.targets.push_back(T);
+        for (size_t m = members.size(); m-- > 0;) {
+            const GateRec& gr = c.gates[members[m]];
+            BlockGradGate bg{};
+            bg.k = gr.k;
+            for (int t = 0; t < gr.k; ++t) {
+                int pos = 0;
+                while (T[pos] != gr.qubits[t]) ++pos;
+                bg.lb[t] = 5 - pos;
+            }
+            bg.param = gr.param;
+            if (gr.param >= 0)
+                for (int t = 0; t < gr.k; ++t) {
+                    const char pc = gr.paulis[t];
+                    if (pc == 'X' || pc == 'Y') bg.xmask |= 1 << bg.lb[t];
+                    if (pc == 'Y' || pc == 'Z') bg.zmask |= 1 << bg.lb[t];
+                    bg.ny += pc == 'Y';
+                }
+            bg.diag = gr.kind == QS_GATE_DIAGONAL;
+            bg.moff = (uint32_t)(bs.gmats.size() / 2);
+            for (double v : gr.m) bs.gmats.push_back((float)v);
+            bs.gates.push_back(bg);
+        }
+        bs.gate0.push_back((int)bs.gates.size());
+    }
+    for (size_t r = 0; r < G; ++r) bs.blocks.push_back(std::move(blocks[G - 1 - r]));
+    return QS_OK;
+}
+
+// Device phase: per block, its Gram matrix (when it has generators), then
+// B^dagger on both states; finally every block's gradients into sums.
+static qs_status run_block_sweep(BlockSweep& bs, const qs_options& fast, qs_state* psi, qs_state* lam, double* sums,
+                                 cudaStream_t sm) {
+    const int nslots = (int)bs.targets.size();
+    const int npass = (int)bs.passes.size();
+    qs_status pst = plan_from_passes(psi->n, QS_C64, fast, std::move(bs.passes), sm, &bs.inv);
+    if (pst != QS_OK) return pst;
+    double* ws = nullptr;
+    double* Mall = nullptr;
+    BlockGradGate* dgates = nullptr;
+    int* dgate0 = nullptr;
+    float* dgmats = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto step = [&](cudaError_t r) {
+        if (e == cudaSuccess) e = r;
+    };
+    if (nslots) {
+        step(cudaMallocAsync(&ws, sizeof(double) * gram_workspace_elems(), sm));
+        step(cudaMallocAsync(&Mall, sizeof(double) * 8192 * (size_t)nslots, sm));
+        step(cudaMallocAsync(&dgates, sizeof(BlockGradGate) * bs.gates.size(), sm));
+        step(cudaMallocAsync(&dgate0, sizeof(int) * bs.gate0.size(), sm));
+        step(cudaMallocAsync(&dgmats, sizeof(float) * std::max<size_t>(bs.gmats.size(), 2), sm));
+        // pageable sources: staged before the calls return
+        step(cudaMemcpyAsync(dgates, bs.gates.data(), sizeof(BlockGradGate) * bs.gates.size(), cudaMemcpyHostToDevice, sm));
+        step(cudaMemcpyAsync(dgate0, bs.gate0.data(), sizeof(int) * bs.gate0.size(), cudaMemcpyHostToDevice, sm));
+        if (!bs.gmats.empty())
+            step(cudaMemcpyAsync(dgmats, bs.gmats.data(), sizeof(float) * bs.gmats.size(), cudaMemcpyHostToDevice, sm));
+    }
+    qs_status st = QS_OK;
+    for (int i = 0; i < npass && e == cudaSuccess && st == QS_OK; ++i) {
+        const int sl = bs.slot[i];
+        if (sl >= 0)
+            step(launch_gram(psi->data, lam->data, psi->n, bs.targets[sl].data(), ws, Mall + 8192 * (size_t)sl,
+                             psi->errflag, sm));
+        if (e != cudaSuccess) break;
+        st = qs_plan_execute_range(psi, bs.inv, i, 1);
+        if (st == QS_OK) st = qs_plan_execute_range(lam, bs.inv, i, 1);
+    }
+    if (e == cudaSuccess && st == QS_OK && nslots)
+        step(launch_block_grads(Mall, nslots, dgates, dgate0, dgmats, sums, sm));
+    for (void* ptr : {(void*)ws, (void*)Mall, (void*)dgates, (void*)dgate0, (void*)dgmats})
+        if (ptr) cudaFreeAsync(ptr, sm);
+    if (st != QS_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "block sweep");
+    return QS_OK;
+}
+
 // Device phase: one upload of the tile-sweep matrices and the phase tables,
 // then every launch in order on the states' stream.
 static qs_status run_reverse_sweep(AdjointSweep& sw, qs_state* psi, qs_state* lam, int nb, int rows, cudaStream_t sm) {
@@ -1033,7 +1192,28 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
             if (t.joinable()) t.join();
         }
     } planner;
+    // complex64 with tensor-core blocks: the block sweep (gradients from Gram
+    // matrices); otherwise, or when a group is not a block of at most six
+    // qubits, the stage sweep
+    BlockSweep bsw;
+    struct BlockReleaser {
+        BlockSweep& s;
+        ~BlockReleaser() { s.release(); }
+    } block_releaser{bsw};
+    bool use_blocks = false;
     auto plan_sweep = [&]() {
+        if (psi->dt == QS_C64 && fast.k_max == 6 && gram_supported(psi->n)) {
+            sweep_st = build_block_sweep(*c, psi->n, fast, bsw);
+            if (sweep_st == QS_OK) {
+                use_blocks = true;
+                return;
+            }
+            bsw = BlockSweep();
+            if (sweep_st != QS_ERR_UNSUPPORTED) {
+                sweep_msg = qs_last_error();
+                return;
+            }
+        }
         sweep_st = build_reverse_sweep(*c, psi->n, psi->dt, fast, sm, sw);
         if (sweep_st != QS_OK) sweep_msg = qs_last_error();
     };
@@ -1076,21 +1256,36 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     if (own_thread) planner.t.join();
     else plan_sweep();
     if (sweep_st != QS_OK) return fail(sweep_st, "%s", sweep_msg.c_str());
-    const int nb = reduce_blocks();
     const int rows = std::max(num_params, 1);
-    st = run_reverse_sweep(sw, psi, lam, nb, rows, sm);
-    if (st != QS_OK) {
-        sw.release();
-        return st;
+    double* sums = nullptr;  // (Re, Im) <lambda|P|psi> per parameter
+    cudaError_t e = cudaSuccess;
+    if (use_blocks) {
+        QS_CUDA(cudaMallocAsync(&sums, sizeof(double) * 2 * rows, sm));
+        e = cudaMemsetAsync(sums, 0, sizeof(double) * 2 * rows, sm);
+        st = e == cudaSuccess ? run_block_sweep(bsw, fast, psi, lam, sums, sm) : cuda_fail(e, "block sweep");
+        if (st != QS_OK) {
+            cudaFreeAsync(sums, sm);
+            return st;
+        }
+    } else {
+        const int nb = reduce_blocks();
+        st = run_reverse_sweep(sw, psi, lam, nb, rows, sm);
+        if (st != QS_OK) {
+            sw.release();
+            return st;
+        }
+        e = launch_sum_partials(sw.partials, rows, nb, sw.sums, sm);
+        sums = sw.sums;
     }
     std::vector<double> host(2 * rows + 2);
-    cudaError_t e = launch_sum_partials(sw.partials, rows, nb, sw.sums, sm);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(host.data(), sw.sums, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, sm);
+        e = cudaMemcpyAsync(host.data(), sums, sizeof(double) * 2 * rows, cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(host.data() + 2 * rows, res, sizeof(double) * 2, cudaMemcpyDeviceToHost, sm);
     if (e == cudaSuccess) e = cudaStreamSynchronize(sm);
+    if (use_blocks) cudaFreeAsync(sums, sm);
     sw.release();
+    bsw.release();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint sweep");
     st = check_device_flag(psi);
     if (st != QS_OK) return st;

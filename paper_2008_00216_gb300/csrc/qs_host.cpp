@@ -496,12 +496,6 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
         return fail(QS_ERR_ARG, "tile_qubits outside 6..%d", maxL);
     if (opt.precision < QS_PREC_FP32 || opt.precision > QS_PREC_3XFP16)
         return fail(QS_ERR_ARG, "bad precision");
-    std::unique_ptr<qs_plan> p(new (std::nothrow) qs_plan);
-    if (!p) return fail(QS_ERR_OOM, "host allocation failed");
-    p->n = c->n;
-    p->dt = dt;
-    p->opt = opt;
-    QS_CUDA(cudaGetDevice(&p->device));
     std::vector<GateRec> blocks;
     qs_status st;
     if (opt.fuse) {
@@ -512,12 +506,28 @@ qs_status qsgb::plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_option
     } else {
         blocks = c->gates;
     }
-    st = build_passes(c->n, dt, blocks, opt, p->passes);
+    std::vector<Pass> passes;
+    st = build_passes(c->n, dt, blocks, opt, passes);
     if (st != QS_OK) return st;
-    for (Pass& ps : p->passes) {
+    for (Pass& ps : passes) {
         factor_tile_scalars(ps);
         if (ps.kind == PASS_TILE && !build_rtile_program(dt, ps, ps.rt)) ps.rt.nops = 0;
     }
+    return plan_from_passes(c->n, dt, opt, std::move(passes), stream, out);
+}
+
+// A plan of ready passes: their matrices are uploaded, converted to the
+// state's precision (in `stream` order when one is given).
+qs_status qsgb::plan_from_passes(int n, qs_dtype dt, const qs_options& opt, std::vector<Pass>&& passes,
+                                 cudaStream_t stream, qs_plan** out) {
+    *out = nullptr;
+    std::unique_ptr<qs_plan> p(new (std::nothrow) qs_plan);
+    if (!p) return fail(QS_ERR_OOM, "host allocation failed");
+    p->n = n;
+    p->dt = dt;
+    p->opt = opt;
+    QS_CUDA(cudaGetDevice(&p->device));
+    p->passes = std::move(passes);
     // upload every pass's matrices, converted to the state's precision
     size_t total = 0;
     for (Pass& ps : p->passes) {

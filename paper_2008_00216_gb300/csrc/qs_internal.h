@@ -239,6 +239,9 @@ namespace qsgb {
 // qs_plan_create with the matrices uploaded and (at destruction) freed in the
 // order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
 qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
+// A plan of ready passes (matrices uploaded and converted, in `stream` order when given).
+qs_status plan_from_passes(int n, qs_dtype dt, const qs_options& opt, std::vector<Pass>&& passes, cudaStream_t stream,
+                           qs_plan** out);
 // effort 1: each candidate block scored with a one-level lookahead; 0: greedy
 qs_status fuse_gates(int n, const std::vector<GateRec>& in, int k_max, std::vector<GateRec>& out, int effort = 1,
                      FuseCache* cache = nullptr);
@@ -294,6 +297,28 @@ cudaError_t launch_diag_wide(void* psi, int n, qs_dtype dt, const WideDiag& w, c
 // Tensor-core pass for a dense 6-qubit gate on a complex64 state (n >= 11);
 // `err` (device int) is set to 1 if a bounded device wait timed out.
 bool gemm_supported(int n, int k);
+// Gram matrices of the block adjoint sweep (qs_gram.cu).  A gate of a fused
+// block in the block's local coordinates (its six Gram targets, local bit b
+// = the b-th lowest target), for the gradient recursion.
+struct BlockGradGate {
+    int k;                   // gate qubits
+    int lb[6];               // local bit of the gate's qubit t (t = 0: most significant in its matrix)
+    int param;               // parameter index, or -1
+    int xmask, zmask, ny;    // generator in local bits: X or Y bits, Y or Z bits, number of Y
+    int diag;                // the matrix is diagonal
+    uint32_t moff;           // offset of its 2^k x 2^k complex64 matrix in the gate-matrix array
+};
+bool gram_supported(int n);
+size_t gram_workspace_elems();   // doubles of the per-CTA parts
+// M (2 x 64 x 64 FP64: Re rows, then Im rows) = sum over the sets of
+// psi_s lambda_s^dagger over the six `targets` (descending); ws holds
+// gram_workspace_elems() doubles.
+cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, double* M,
+                        int* err, cudaStream_t st);
+// One CTA per block: gates[gate0[b] .. gate0[b+1]) from the block's last
+// gate to its first; gradient of parameter p into sums[2p + 1].
+cudaError_t launch_block_grads(const double* Mall, int nslots, const BlockGradGate* gates, const int* gate0,
+                               const void* mats, double* sums, cudaStream_t st);
 // A tensor tile pass on a complex64 state (3xFP16): dmat holds d.nb 64 x 64
 // float2 matrices, each in the one-block pass's local-index order.
 cudaError_t launch_ttile(void* psi, int n, const TTileDesc& d, const void* dmat, int* err, cudaStream_t st);
