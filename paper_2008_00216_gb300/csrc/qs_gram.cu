@@ -23,9 +23,9 @@
 //   Re M[l][l'] = D[2l][2l'] + D[2l+1][2l'+1],  Im M[l][l'] = D[2l+1][2l'] - D[2l][2l'+1].
 // One persistent CTA per SM, warp-specialised:
 //   warps 0-3   epilogue: warp q owns tensor-memory lanes 32q..32q+31
-//   warps 4-11  producers: warp w loads 16 local indices of psi (w < 8) or
-//               lambda, one set per lane, a stage ahead in registers
-//   warp 12     one thread issues the MMAs
+//   warps 4-19  producers: warp w loads 8 local indices of psi (w < 12) or
+//               lambda, three stages deep in registers
+//   warp 20     one thread issues the MMAs
 // Two accumulators alternate every kFlush stages; the epilogue adds each
 // finished one into the CTA's FP64 part of M, so no FP32 sum runs over more
 // than 2048 sets.  Every mbarrier wait is bounded (about two seconds of
@@ -46,7 +46,7 @@ using namespace tc;
 
 constexpr int kKSets = 32;                    // sets per stage
 constexpr int kStages = 3;
-constexpr int kEpiWarps = 4, kProdWarps = 8;
+constexpr int kEpiWarps = 4, kProdWarps = 16;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kPart = 128 * 128;              // bytes of one operand part: 128 rows x 128 bytes
@@ -55,7 +55,7 @@ constexpr int kBar = kStages * kStage;
 constexpr int kSmem = kBar + 256;
 constexpr int kTmemCols = 256;                // two accumulators of 128 columns
 constexpr int kFlush = 64;                    // stages per accumulator period
-constexpr int kPrefetch = 4;                  // stages fetched into L2 ahead of the register loads
+constexpr int kPrefetch = 6;                  // stages fetched into L2 ahead of the register loads
 constexpr int kMElems = 2 * 64 * 64;          // one M in FP64: Re rows, then Im rows
 
 struct Args {
@@ -77,12 +77,18 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     tmem_ld16(taddr + 16, v + 16);
 }
 
-__device__ __forceinline__ float2 ld_stream(const float2* p) {
-    float2 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+__device__ __forceinline__ float4 ld_stream4(const float2* p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
     return v;
 }
 
+// PAIR (qubit 0 not a target, so sets 2j and 2j + 1 are adjacent amplitudes):
+// a lane loads both with one 16-byte load, half-warp h taking row 2i + h;
+// otherwise a lane loads one set, the warp one row per load
+template <bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gram6(const float2* __restrict__ psi, const float2* __restrict__ lam, const __grid_constant__ Args a,
             double* __restrict__ ws, int* err) {
@@ -124,61 +130,99 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t nper = (my + kFlush - 1) / kFlush;
 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
-        // ================= producers: 16 local indices of one state, one set per lane
+        // ================= producers: 8 local indices of one state, one set per lane
         const int pw = warp - kEpiWarps;
-        const float2* src = pw < 4 ? psi : lam;
-        const int l0 = (pw & 3) * 16;
-        const uint32_t part = pw < 4 ? 0u : 2u * kPart;
-        auto load = [&](float2 (&v)[16], uint64_t it) {
-            const uint64_t t = blockIdx.x + it * gridDim.x;
-            const float2* p = src + set_base(t * kKSets + (uint64_t)lane, a.sorted);
-#pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = ld_stream(p + a.off[l0 + i]);
-        };
-        // the rows of stage it + kPrefetch are fetched into L2 meanwhile (lane:
-        // row lane / 2, sets 16 (lane & 1) ... of the stage, one 128-byte line
-        // when the low set bits are the low qubits), so the register loads,
-        // two stages deep, mostly wait for L2 rather than DRAM
-        auto prefetch = [&](uint64_t it) {
+        const float2* src = pw < 8 ? psi : lam;
+        const int l0 = (pw & 7) * 8;
+        const uint32_t part = pw < 8 ? 0u : 2u * kPart;
+        const int h = lane >> 4, j = lane & 15;
+        auto load = [&](float4 (&v)[4], uint64_t it) {
             if (it >= my) return;
+            const uint64_t t = blockIdx.x + it * gridDim.x;
+            if constexpr (PAIR) {
+                const float2* p = src + set_base(t * kKSets + (uint64_t)(2 * j), a.sorted);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) v[i] = ld_stream4(p + a.off[l0 + 2 * i + h]);
+            } else {
+                const float2* p = src + set_base(t * kKSets + (uint64_t)lane, a.sorted);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 x = __ldg(p + a.off[l0 + 2 * i]), y = __ldg(p + a.off[l0 + 2 * i + 1]);
+                    v[i] = make_float4(x.x, x.y, y.x, y.y);
+                }
+            }
+        };
+        // the rows of stage it + kPrefetch are fetched into L2 meanwhile (lane
+        // < 16: row lane / 2, sets 16 (lane & 1) ... of the stage, one 128-byte
+        // line when the low set bits are the low qubits), so the register
+        // loads, three stages deep, mostly wait for L2 rather than DRAM
+        auto prefetch = [&](uint64_t it) {
+            if (it >= my || lane >= 16) return;
             const uint64_t t = blockIdx.x + it * gridDim.x;
             const int row = lane >> 1, half = lane & 1;
             const float2* p = src + set_base(t * kKSets + (uint64_t)(16 * half), a.sorted) + a.off[l0 + row];
             asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
         };
-        auto put = [&](const float2 (&v)[16], uint64_t it) {
+        auto put = [&](const float4 (&v)[4], uint64_t it) {
             const int st = (int)(it % kStages);
             const uint64_t u = it / kStages;
             if (u > 0 && !mbar_wait(&empty[st], (uint32_t)((u - 1) & 1), err, abort_flag)) return false;
             unsigned char* hi = sm + st * kStage + part;
             unsigned char* lo = hi + kPart;
-            const uint32_t col = 4u * (uint32_t)(lane & 3);
+            auto split = [](float x, float& xh, float& xl) {
+                xh = tf32_round(x);
+                xl = tf32_round(x - xh);
+            };
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int r = 2 * (l0 + i);
-                const uint32_t o0 = swz(r, lane >> 2) + col, o1 = swz(r + 1, lane >> 2) + col;
-                const float rh = tf32_round(v[i].x), ih = tf32_round(v[i].y);
-                *reinterpret_cast<float*>(hi + o0) = rh;
-                *reinterpret_cast<float*>(lo + o0) = tf32_round(v[i].x - rh);
-                *reinterpret_cast<float*>(hi + o1) = ih;
-                *reinterpret_cast<float*>(lo + o1) = tf32_round(v[i].y - ih);
+            for (int i = 0; i < 4; ++i) {
+                if constexpr (PAIR) {  // row l0 + 2i + h, sets 2j, 2j + 1
+                    const int r = 2 * (l0 + 2 * i + h);
+                    const uint32_t o0 = swz(r, j >> 1) + 8u * (uint32_t)(j & 1);
+                    const uint32_t o1 = swz(r + 1, j >> 1) + 8u * (uint32_t)(j & 1);
+                    float2 rh, rl, ih, il;
+                    split(v[i].x, rh.x, rl.x);
+                    split(v[i].z, rh.y, rl.y);
+                    split(v[i].y, ih.x, il.x);
+                    split(v[i].w, ih.y, il.y);
+                    *reinterpret_cast<float2*>(hi + o0) = rh;
+                    *reinterpret_cast<float2*>(lo + o0) = rl;
+                    *reinterpret_cast<float2*>(hi + o1) = ih;
+                    *reinterpret_cast<float2*>(lo + o1) = il;
+                } else {  // rows l0 + 2i and l0 + 2i + 1, set `lane`
+                    const uint32_t col = 4u * (uint32_t)(lane & 3);
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int r = 2 * (l0 + 2 * i + e);
+                        const uint32_t o0 = swz(r, lane >> 2) + col, o1 = swz(r + 1, lane >> 2) + col;
+                        float xh, xl;
+                        split(e ? v[i].z : v[i].x, xh, xl);
+                        *reinterpret_cast<float*>(hi + o0) = xh;
+                        *reinterpret_cast<float*>(lo + o0) = xl;
+                        split(e ? v[i].w : v[i].y, xh, xl);
+                        *reinterpret_cast<float*>(hi + o1) = xh;
+                        *reinterpret_cast<float*>(lo + o1) = xl;
+                    }
+                }
             }
             fence_async_smem();
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[st]);
             return true;
         };
-        float2 v[16], w[16];
+        float4 b0[4], b1[4], b2[4];
         for (uint64_t it = 0; it < (uint64_t)kPrefetch; ++it) prefetch(it);
-        if (my > 0) load(v, 0);
-        for (uint64_t it = 0; it < my; it += 2) {
+        load(b0, 0);
+        load(b1, 1);
+        for (uint64_t it = 0; it < my; it += 3) {
             prefetch(it + kPrefetch);
-            if (it + 1 < my) load(w, it + 1);
-            if (!put(v, it)) break;
-            if (it + 1 >= my) break;
+            load(b2, it + 2);
+            if (!put(b0, it) || it + 1 >= my) break;
             prefetch(it + 1 + kPrefetch);
-            if (it + 2 < my) load(v, it + 2);
-            if (!put(w, it + 1)) break;
+            load(b0, it + 3);
+            if (!put(b1, it + 1) || it + 2 >= my) break;
+            prefetch(it + 2 + kPrefetch);
+            load(b1, it + 4);
+            if (!put(b2, it + 2)) break;
         }
     } else if (warp == kMmaWarp) {
         // ================= MMA issuer
@@ -466,10 +510,15 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     std::sort(a.sorted, a.sorted + 6);
     a.ntiles = (1ull << (n - 6)) / gram::kKSets;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
-    cudaError_t e = allow_max_dynamic_smem(gram::k_gram6);
+    const bool pair = a.sorted[0] != 0;
+    cudaError_t e = pair ? allow_max_dynamic_smem(gram::k_gram6<true>) : allow_max_dynamic_smem(gram::k_gram6<false>);
     if (e != cudaSuccess) return e;
-    gram::k_gram6<<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam, a, ws,
-                                                                     err);
+    if (pair)
+        gram::k_gram6<true><<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam,
+                                                                               a, ws, err);
+    else
+        gram::k_gram6<false><<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam,
+                                                                                a, ws, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     gram::k_gram_reduce<<<gram::kMElems / 32, 32 * gram::kRedParts, 0, st>>>(ws, grid, M);
