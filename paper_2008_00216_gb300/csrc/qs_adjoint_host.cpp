@@ -1072,6 +1072,7 @@ static qs_status run_block_sweep(BlockSweep& bs, const qs_options& fast, qs_stat
             step(launch_gram(psi->data, lam->data, psi->n, bs.targets[sl].data(), ws, Mall + 8192 * (size_t)sl,
                              psi->errflag, sm));
         if (e != cudaSuccess) break;
+        if (i + 1 == npass) break;  // the first block's inverse: nothing reads the states after it
         st = qs_plan_execute_range(psi, bs.inv, i, 1);
         if (st == QS_OK) st = qs_plan_execute_range(lam, bs.inv, i, 1);
     }

@@ -23,8 +23,9 @@
 //   Re M[l][l'] = D[2l][2l'] + D[2l+1][2l'+1],  Im M[l][l'] = D[2l+1][2l'] - D[2l][2l'+1].
 // One persistent CTA per SM, warp-specialised:
 //   warps 0-3   epilogue: warp q owns tensor-memory lanes 32q..32q+31
-//   warps 4-19  producers: warp w loads 8 local indices of psi (w < 12) or
-//               lambda, three stages deep in registers
+//   warps 4-19  producers: warp w copies 8 local indices of psi (w < 12) or
+//               lambda (rows of 32 sets) with cp.async into a raw ring kRaw
+//               stages ahead, then splits its own rows into the operands
 //   warp 20     one thread issues the MMAs
 // Two accumulators alternate every kFlush stages; the epilogue adds each
 // finished one into the CTA's FP64 part of M, so no FP32 sum runs over more
@@ -45,17 +46,19 @@ namespace gram {
 using namespace tc;
 
 constexpr int kKSets = 32;                    // sets per stage
-constexpr int kStages = 3;
+constexpr int kStages = 2;                    // operand stages (split, swizzled)
+constexpr int kRaw = 3;                       // raw stages in flight (cp.async)
 constexpr int kEpiWarps = 4, kProdWarps = 16;
 constexpr int kMmaWarp = kEpiWarps + kProdWarps;
 constexpr int kThreads = 32 * (kMmaWarp + 1);
 constexpr int kPart = 128 * 128;              // bytes of one operand part: 128 rows x 128 bytes
 constexpr int kStage = 4 * kPart;             // psi hi, psi lo, lambda hi, lambda lo
-constexpr int kBar = kStages * kStage;
+constexpr int kRawStage = 128 * 256;          // 128 rows of 32 sets (complex64), 8 rows per producer warp
+constexpr int kRawOff = kStages * kStage;
+constexpr int kBar = kRawOff + kRaw * kRawStage;
 constexpr int kSmem = kBar + 256;
 constexpr int kTmemCols = 256;                // two accumulators of 128 columns
 constexpr int kFlush = 64;                    // stages per accumulator period
-constexpr int kPrefetch = 6;                  // stages fetched into L2 ahead of the register loads
 constexpr int kMElems = 2 * 64 * 64;          // one M in FP64: Re rows, then Im rows
 
 struct Args {
@@ -77,18 +80,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     tmem_ld16(taddr + 16, v + 16);
 }
 
-__device__ __forceinline__ float4 ld_stream4(const float2* p) {
-    float4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
-    return v;
-}
-
-// PAIR (qubit 0 not a target, so sets 2j and 2j + 1 are adjacent amplitudes):
-// a lane loads both with one 16-byte load, half-warp h taking row 2i + h;
-// otherwise a lane loads one set, the warp one row per load
-template <bool PAIR>
+// W = 2^w: the w lowest qubits are not targets, so W consecutive sets are
+// adjacent amplitudes; a lane copies W of them at once (32 / W lanes per
+// row, W rows per warp instruction)
+template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gram6(const float2* __restrict__ psi, const float2* __restrict__ lam, const __grid_constant__ Args a,
             double* __restrict__ ws, int* err) {
@@ -130,100 +125,97 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint64_t nper = (my + kFlush - 1) / kFlush;
 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
-        // ================= producers: 8 local indices of one state, one set per lane
+        // ================= producers: 8 local indices of one state
         const int pw = warp - kEpiWarps;
         const float2* src = pw < 8 ? psi : lam;
         const int l0 = (pw & 7) * 8;
         const uint32_t part = pw < 8 ? 0u : 2u * kPart;
-        const int h = lane >> 4, j = lane & 15;
-        auto load = [&](float4 (&v)[4], uint64_t it) {
-            if (it >= my) return;
-            const uint64_t t = blockIdx.x + it * gridDim.x;
-            if constexpr (PAIR) {
-                const float2* p = src + set_base(t * kKSets + (uint64_t)(2 * j), a.sorted);
+        constexpr int LPR = 32 / W, NLD = 8 / W;  // lanes per row, copies per stage
+        const int rsub = lane / LPR, s0 = (lane % LPR) * W;  // row within a copy, first set
+        // raw layout: [stage][warp][row 0..7][32 sets] complex64 (256-byte rows)
+        auto raw_at = [&](int slot, int row) {
+            return sm + kRawOff + slot * kRawStage + pw * 2048 + row * 256 + s0 * 8;
+        };
+        auto copy = [&](uint64_t it) {  // the warp's rows of stage it, into raw slot it % kRaw
+            if (it < my) {
+                const uint64_t t = blockIdx.x + it * gridDim.x;
+                const float2* p = src + set_base(t * kKSets + (uint64_t)s0, a.sorted);
+                const int slot = (int)(it % kRaw);
 #pragma unroll
-                for (int i = 0; i < 4; ++i) v[i] = ld_stream4(p + a.off[l0 + 2 * i + h]);
-            } else {
-                const float2* p = src + set_base(t * kKSets + (uint64_t)lane, a.sorted);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 x = __ldg(p + a.off[l0 + 2 * i]), y = __ldg(p + a.off[l0 + 2 * i + 1]);
-                    v[i] = make_float4(x.x, x.y, y.x, y.y);
+                for (int i = 0; i < NLD; ++i) {
+                    const int row = W * i + rsub;
+                    const float2* g = p + a.off[l0 + row];
+                    if constexpr (W == 2)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(raw_at(slot, row))), "l"(g)
+                                     : "memory");
+                    else
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(raw_at(slot, row))), "l"(g)
+                                     : "memory");
                 }
             }
+            cp_async_commit();  // one group per stage, empty past the end
         };
-        // the rows of stage it + kPrefetch are fetched into L2 meanwhile (lane
-        // < 16: row lane / 2, sets 16 (lane & 1) ... of the stage, one 128-byte
-        // line when the low set bits are the low qubits), so the register
-        // loads, three stages deep, mostly wait for L2 rather than DRAM
-        auto prefetch = [&](uint64_t it) {
-            if (it >= my || lane >= 16) return;
-            const uint64_t t = blockIdx.x + it * gridDim.x;
-            const int row = lane >> 1, half = lane & 1;
-            const float2* p = src + set_base(t * kKSets + (uint64_t)(16 * half), a.sorted) + a.off[l0 + row];
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-        };
-        auto put = [&](const float4 (&v)[4], uint64_t it) {
+        auto put = [&](uint64_t it) {
             const int st = (int)(it % kStages);
             const uint64_t u = it / kStages;
+            cp_async_wait<kRaw - 1>();  // this lane's copies of stage it are done
+            __syncwarp();               // and the other lanes' (each warp reads only its own rows)
+            float v[NLD][2 * W];
+            const int slot = (int)(it % kRaw);
+#pragma unroll
+            for (int i = 0; i < NLD; ++i) {
+                const unsigned char* q = raw_at(slot, W * i + rsub);
+                if constexpr (W == 2) {
+                    const float4 x = *reinterpret_cast<const float4*>(q);
+                    v[i][0] = x.x;
+                    v[i][1] = x.y;
+                    v[i][2] = x.z;
+                    v[i][3] = x.w;
+                } else {
+                    const float2 x = *reinterpret_cast<const float2*>(q);
+                    v[i][0] = x.x;
+                    v[i][1] = x.y;
+                }
+            }
             if (u > 0 && !mbar_wait(&empty[st], (uint32_t)((u - 1) & 1), err, abort_flag)) return false;
             unsigned char* hi = sm + st * kStage + part;
             unsigned char* lo = hi + kPart;
-            auto split = [](float x, float& xh, float& xl) {
-                xh = tf32_round(x);
-                xl = tf32_round(x - xh);
-            };
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if constexpr (PAIR) {  // row l0 + 2i + h, sets 2j, 2j + 1
-                    const int r = 2 * (l0 + 2 * i + h);
-                    const uint32_t o0 = swz(r, j >> 1) + 8u * (uint32_t)(j & 1);
-                    const uint32_t o1 = swz(r + 1, j >> 1) + 8u * (uint32_t)(j & 1);
-                    float2 rh, rl, ih, il;
-                    split(v[i].x, rh.x, rl.x);
-                    split(v[i].z, rh.y, rl.y);
-                    split(v[i].y, ih.x, il.x);
-                    split(v[i].w, ih.y, il.y);
-                    *reinterpret_cast<float2*>(hi + o0) = rh;
-                    *reinterpret_cast<float2*>(lo + o0) = rl;
-                    *reinterpret_cast<float2*>(hi + o1) = ih;
-                    *reinterpret_cast<float2*>(lo + o1) = il;
-                } else {  // rows l0 + 2i and l0 + 2i + 1, set `lane`
-                    const uint32_t col = 4u * (uint32_t)(lane & 3);
+            for (int i = 0; i < NLD; ++i) {
+                const int r = 2 * (l0 + W * i + rsub);  // the real row; r + 1 the imaginary
+                const uint32_t o = swz(r, s0 >> 2) + 4u * (uint32_t)(s0 & 3);
+                const uint32_t o1 = swz(r + 1, s0 >> 2) + 4u * (uint32_t)(s0 & 3);
+                float rh[W], rl[W], ih[W], il[W];
 #pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const int r = 2 * (l0 + 2 * i + e);
-                        const uint32_t o0 = swz(r, lane >> 2) + col, o1 = swz(r + 1, lane >> 2) + col;
-                        float xh, xl;
-                        split(e ? v[i].z : v[i].x, xh, xl);
-                        *reinterpret_cast<float*>(hi + o0) = xh;
-                        *reinterpret_cast<float*>(lo + o0) = xl;
-                        split(e ? v[i].w : v[i].y, xh, xl);
-                        *reinterpret_cast<float*>(hi + o1) = xh;
-                        *reinterpret_cast<float*>(lo + o1) = xl;
-                    }
+                for (int e = 0; e < W; ++e) {
+                    rh[e] = tf32_round(v[i][2 * e]);
+                    rl[e] = tf32_round(v[i][2 * e] - rh[e]);
+                    ih[e] = tf32_round(v[i][2 * e + 1]);
+                    il[e] = tf32_round(v[i][2 * e + 1] - ih[e]);
+                }
+                if constexpr (W == 1) {
+                    *reinterpret_cast<float*>(hi + o) = rh[0];
+                    *reinterpret_cast<float*>(lo + o) = rl[0];
+                    *reinterpret_cast<float*>(hi + o1) = ih[0];
+                    *reinterpret_cast<float*>(lo + o1) = il[0];
+                } else {
+                    *reinterpret_cast<float2*>(hi + o) = make_float2(rh[0], rh[1]);
+                    *reinterpret_cast<float2*>(lo + o) = make_float2(rl[0], rl[1]);
+                    *reinterpret_cast<float2*>(hi + o1) = make_float2(ih[0], ih[1]);
+                    *reinterpret_cast<float2*>(lo + o1) = make_float2(il[0], il[1]);
                 }
             }
             fence_async_smem();
-            __syncwarp();
+            __syncwarp();  // also: every lane has read raw slot it % kRaw before it is refilled
             if (lane == 0) mbar_arrive(&full[st]);
             return true;
         };
-        float4 b0[4], b1[4], b2[4];
-        for (uint64_t it = 0; it < (uint64_t)kPrefetch; ++it) prefetch(it);
-        load(b0, 0);
-        load(b1, 1);
-        for (uint64_t it = 0; it < my; it += 3) {
-            prefetch(it + kPrefetch);
-            load(b2, it + 2);
-            if (!put(b0, it) || it + 1 >= my) break;
-            prefetch(it + 1 + kPrefetch);
-            load(b0, it + 3);
-            if (!put(b1, it + 1) || it + 2 >= my) break;
-            prefetch(it + 2 + kPrefetch);
-            load(b1, it + 4);
-            if (!put(b2, it + 2)) break;
+        for (int it = 0; it < kRaw - 1; ++it) copy((uint64_t)it);
+        for (uint64_t it = 0; it < my; ++it) {
+            copy(it + kRaw - 1);
+            if (!put(it)) break;
         }
+        cp_async_wait<0>();  // nothing of ours in flight at exit
     } else if (warp == kMmaWarp) {
         // ================= MMA issuer
         if (lane == 0) {
@@ -510,15 +502,18 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     std::sort(a.sorted, a.sorted + 6);
     a.ntiles = (1ull << (n - 6)) / gram::kKSets;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
-    const bool pair = a.sorted[0] != 0;
-    cudaError_t e = pair ? allow_max_dynamic_smem(gram::k_gram6<true>) : allow_max_dynamic_smem(gram::k_gram6<false>);
+    // the lowest target bounds how many consecutive sets are adjacent amplitudes
+    auto run = [&](auto kern) {
+        cudaError_t r = allow_max_dynamic_smem(kern);
+        if (r != cudaSuccess) return r;
+        kern<<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam, a, ws, err);
+        return cudaSuccess;
+    };
+    // (16-byte copies measured faster than 32-byte loads or 256-byte bulk copies here)
+    // 16-byte copies need 16-byte aligned states (a wrapped buffer may be 8-byte aligned only)
+    const bool a16 = (((uintptr_t)psi | (uintptr_t)lam) & 15) == 0;
+    cudaError_t e = a16 && a.sorted[0] >= 1 ? run(gram::k_gram6<2>) : run(gram::k_gram6<1>);
     if (e != cudaSuccess) return e;
-    if (pair)
-        gram::k_gram6<true><<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam,
-                                                                               a, ws, err);
-    else
-        gram::k_gram6<false><<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam,
-                                                                                a, ws, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     gram::k_gram_reduce<<<gram::kMElems / 32, 32 * gram::kRedParts, 0, st>>>(ws, grid, M);
