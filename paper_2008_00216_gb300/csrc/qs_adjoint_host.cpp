@@ -1037,49 +1037,87 @@ static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options&
 }
 
 // Device phase: per block, its Gram matrix (when it has generators), then
-// B^dagger on both states; finally every block's gradients into sums.
+// B^dagger on both states; finally every block's gradients into sums.  All
+// device memory is one allocation from the library's pool and all host data
+// one copy through pinned staging, so the host enqueues the sweep without
+// waiting for the forward still running on the stream.
+namespace {
+thread_local PinnedStage t_sweep_stage;
+}
+
 static qs_status run_block_sweep(BlockSweep& bs, const qs_options& fast, qs_state* psi, qs_state* lam, double* sums,
                                  cudaStream_t sm) {
     const int nslots = (int)bs.targets.size();
     const int npass = (int)bs.passes.size();
-    qs_status pst = plan_from_passes(psi->n, QS_C64, fast, std::move(bs.passes), sm, &bs.inv);
-    if (pst != QS_OK) return pst;
-    double* ws = nullptr;
-    double* Mall = nullptr;
-    BlockGradGate* dgates = nullptr;
-    int* dgate0 = nullptr;
-    float* dgmats = nullptr;
-    cudaError_t e = cudaSuccess;
-    auto step = [&](cudaError_t r) {
-        if (e == cudaSuccess) e = r;
-    };
-    if (nslots) {
-        step(cudaMallocAsync(&ws, sizeof(double) * gram_workspace_elems(), sm));
-        step(cudaMallocAsync(&Mall, sizeof(double) * 8192 * (size_t)nslots, sm));
-        step(cudaMallocAsync(&dgates, sizeof(BlockGradGate) * bs.gates.size(), sm));
-        step(cudaMallocAsync(&dgate0, sizeof(int) * bs.gate0.size(), sm));
-        step(cudaMallocAsync(&dgmats, sizeof(float) * std::max<size_t>(bs.gmats.size(), 2), sm));
-        // pageable sources: staged before the calls return
-        step(cudaMemcpyAsync(dgates, bs.gates.data(), sizeof(BlockGradGate) * bs.gates.size(), cudaMemcpyHostToDevice, sm));
-        step(cudaMemcpyAsync(dgate0, bs.gate0.data(), sizeof(int) * bs.gate0.size(), cudaMemcpyHostToDevice, sm));
-        if (!bs.gmats.empty())
-            step(cudaMemcpyAsync(dgmats, bs.gmats.data(), sizeof(float) * bs.gmats.size(), cudaMemcpyHostToDevice, sm));
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    // layout: [pass matrices | gates | gate0 | gate matrices] (uploaded), [M | Gram parts] (device only)
+    size_t mats_elems = 0;
+    for (Pass& ps : bs.passes) {
+        ps.dev_offset = mats_elems;
+        mats_elems += ps.mats.size() / 2;
     }
+    const size_t o_gates = up(mats_elems * 8), o_gate0 = o_gates + up(sizeof(BlockGradGate) * bs.gates.size());
+    const size_t o_gmats = o_gate0 + up(sizeof(int) * bs.gate0.size());
+    const size_t host_bytes = o_gmats + up(sizeof(float) * bs.gmats.size());
+    const size_t o_M = host_bytes, o_ws = o_M + up(sizeof(double) * 8192 * (size_t)nslots);
+    const size_t total = o_ws + sizeof(double) * gram_workspace_elems() * (size_t)nslots;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = t_sweep_stage.reserve(host_bytes, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "sweep staging");
+    char* hp = t_sweep_stage.p;
+    {
+        float* f = reinterpret_cast<float*>(hp);
+        size_t at = 0;
+        for (const Pass& ps : bs.passes)
+            for (double v : ps.mats) f[at++] = (float)v;
+    }
+    std::copy(bs.gates.begin(), bs.gates.end(), reinterpret_cast<BlockGradGate*>(hp + o_gates));
+    std::copy(bs.gate0.begin(), bs.gate0.end(), reinterpret_cast<int*>(hp + o_gate0));
+    std::copy(bs.gmats.begin(), bs.gmats.end(), reinterpret_cast<float*>(hp + o_gmats));
+    char* base = nullptr;
+    e = lib_malloc_async(reinterpret_cast<void**>(&base), total, sm);
+    if (e != cudaSuccess) return cuda_fail(e, "block sweep memory");
+    e = cudaMemcpyAsync(base, hp, host_bytes, cudaMemcpyHostToDevice, sm);
+    if (e == cudaSuccess) e = cudaEventRecord(t_sweep_stage.done, sm);  // the staging is free once this passes
+    if (e != cudaSuccess) {
+        cudaFreeAsync(base, sm);
+        return cuda_fail(e, "block sweep upload");
+    }
+    // the inverse passes as a plan over the uploaded matrices (not owned by it)
+    bs.inv = new (std::nothrow) qs_plan;
+    if (!bs.inv) {
+        cudaFreeAsync(base, sm);
+        return fail(QS_ERR_OOM, "host allocation failed");
+    }
+    bs.inv->n = psi->n;
+    bs.inv->dt = QS_C64;
+    bs.inv->opt = fast;
+    bs.inv->device = dev;
+    bs.inv->passes = std::move(bs.passes);
+    bs.inv->dev_mats = base;
+    bs.inv->dev_elems = mats_elems;
+    double* Mall = reinterpret_cast<double*>(base + o_M);
+    double* ws = reinterpret_cast<double*>(base + o_ws);
     qs_status st = QS_OK;
     for (int i = 0; i < npass && e == cudaSuccess && st == QS_OK; ++i) {
         const int sl = bs.slot[i];
         if (sl >= 0)
-            step(launch_gram(psi->data, lam->data, psi->n, bs.targets[sl].data(), ws, Mall + 8192 * (size_t)sl,
-                             psi->errflag, sm));
+            e = launch_gram(psi->data, lam->data, psi->n, bs.targets[sl].data(),
+                            ws + gram_workspace_elems() * (size_t)sl, psi->errflag, sm);
         if (e != cudaSuccess) break;
         if (i + 1 == npass) break;  // the first block's inverse: nothing reads the states after it
         st = qs_plan_execute_range(psi, bs.inv, i, 1);
         if (st == QS_OK) st = qs_plan_execute_range(lam, bs.inv, i, 1);
     }
-    if (e == cudaSuccess && st == QS_OK && nslots)
-        step(launch_block_grads(Mall, nslots, dgates, dgate0, dgmats, sums, sm));
-    for (void* ptr : {(void*)ws, (void*)Mall, (void*)dgates, (void*)dgate0, (void*)dgmats})
-        if (ptr) cudaFreeAsync(ptr, sm);
+    if (e == cudaSuccess && st == QS_OK && nslots) {
+        e = launch_gram_reduce(ws, psi->n, nslots, Mall, sm);
+        if (e == cudaSuccess)
+            e = launch_block_grads(Mall, nslots, reinterpret_cast<const BlockGradGate*>(base + o_gates),
+                                   reinterpret_cast<const int*>(base + o_gate0), base + o_gmats, sums, sm);
+    }
+    cudaFreeAsync(base, sm);
+    bs.inv->dev_mats = nullptr;  // freed above, in stream order
     if (st != QS_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "block sweep");
     return QS_OK;

@@ -82,7 +82,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // W = 2^w: the w lowest qubits are not targets, so W consecutive sets are
 // adjacent amplitudes; a lane copies W of them at once (32 / W lanes per
-// row, W rows per warp instruction)
+// row, W rows per warp instruction).  W = 0: qubit 0 is a target (local
+// bit 0), so rows 2i and 2i + 1 of a set are adjacent amplitudes: a lane
+// copies that pair (raw layout [row pair][set][2]) and converts as W = 1.
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gram6(const float2* __restrict__ psi, const float2* __restrict__ lam, const __grid_constant__ Args a,
@@ -130,8 +132,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float2* src = pw < 8 ? psi : lam;
         const int l0 = (pw & 7) * 8;
         const uint32_t part = pw < 8 ? 0u : 2u * kPart;
-        constexpr int LPR = 32 / W, NLD = 8 / W;  // lanes per row, copies per stage
-        const int rsub = lane / LPR, s0 = (lane % LPR) * W;  // row within a copy, first set
+        constexpr int WC = W == 0 ? 1 : W;          // sets per lane in the conversion
+        constexpr int LPR = 32 / WC, NLD = 8 / WC;  // lanes per row, rows per lane
+        const int rsub = lane / LPR, s0 = (lane % LPR) * WC;  // row within a copy, first set
         // raw layout: [stage][warp][row 0..7][32 sets] complex64 (256-byte rows)
         auto raw_at = [&](int slot, int row) {
             return sm + kRawOff + slot * kRawStage + pw * 2048 + row * 256 + s0 * 8;
@@ -142,15 +145,27 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float2* p = src + set_base(t * kKSets + (uint64_t)s0, a.sorted);
                 const int slot = (int)(it % kRaw);
 #pragma unroll
-                for (int i = 0; i < NLD; ++i) {
-                    const int row = W * i + rsub;
-                    const float2* g = p + a.off[l0 + row];
-                    if constexpr (W == 2)
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(raw_at(slot, row))), "l"(g)
+                if constexpr (W == 0) {  // rows 2i, 2i + 1 of set `lane`: 16 adjacent bytes
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(
+                                         sm + kRawOff + slot * kRawStage + pw * 2048 + i * 512 + lane * 16)),
+                                     "l"(p + a.off[l0 + 2 * i])
                                      : "memory");
-                    else
-                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(raw_at(slot, row))), "l"(g)
-                                     : "memory");
+                } else {
+#pragma unroll
+                    for (int i = 0; i < NLD; ++i) {
+                        const int row = W * i + rsub;
+                        const float2* g = p + a.off[l0 + row];
+                        if constexpr (W == 2)
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(raw_at(slot, row))),
+                                         "l"(g)
+                                         : "memory");
+                        else
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(su32(raw_at(slot, row))),
+                                         "l"(g)
+                                         : "memory");
+                    }
                 }
             }
             cp_async_commit();  // one group per stage, empty past the end
@@ -160,11 +175,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t u = it / kStages;
             cp_async_wait<kRaw - 1>();  // this lane's copies of stage it are done
             __syncwarp();               // and the other lanes' (each warp reads only its own rows)
-            float v[NLD][2 * W];
+            float v[NLD][2 * WC];
             const int slot = (int)(it % kRaw);
 #pragma unroll
             for (int i = 0; i < NLD; ++i) {
-                const unsigned char* q = raw_at(slot, W * i + rsub);
+                const unsigned char* q = W == 0 ? sm + kRawOff + slot * kRawStage + pw * 2048 + (i >> 1) * 512 + lane * 16 + (i & 1) * 8
+                                                : raw_at(slot, WC * i + rsub);
                 if constexpr (W == 2) {
                     const float4 x = *reinterpret_cast<const float4*>(q);
                     v[i][0] = x.x;
@@ -182,18 +198,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             unsigned char* lo = hi + kPart;
 #pragma unroll
             for (int i = 0; i < NLD; ++i) {
-                const int r = 2 * (l0 + W * i + rsub);  // the real row; r + 1 the imaginary
+                const int r = 2 * (l0 + WC * i + rsub);  // the real row; r + 1 the imaginary
                 const uint32_t o = swz(r, s0 >> 2) + 4u * (uint32_t)(s0 & 3);
                 const uint32_t o1 = swz(r + 1, s0 >> 2) + 4u * (uint32_t)(s0 & 3);
-                float rh[W], rl[W], ih[W], il[W];
+                float rh[WC], rl[WC], ih[WC], il[WC];
 #pragma unroll
-                for (int e = 0; e < W; ++e) {
+                for (int e = 0; e < WC; ++e) {
                     rh[e] = tf32_round(v[i][2 * e]);
                     rl[e] = tf32_round(v[i][2 * e] - rh[e]);
                     ih[e] = tf32_round(v[i][2 * e + 1]);
                     il[e] = tf32_round(v[i][2 * e + 1] - ih[e]);
                 }
-                if constexpr (W == 1) {
+                if constexpr (WC == 1) {
                     *reinterpret_cast<float*>(hi + o) = rh[0];
                     *reinterpret_cast<float*>(lo + o) = rl[0];
                     *reinterpret_cast<float*>(hi + o1) = ih[0];
@@ -294,12 +310,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // M = the sum of the CTAs' parts, FP64, in a fixed order: a block takes 32
-// entries; its 8 warps sum every 8th part (coalesced rows of 32), then one
-// warp adds the 8 partial sums in order.
+// entries of one Gram matrix (blockIdx.y); its 8 warps sum every 8th part
+// (coalesced rows of 32), then one warp adds the 8 partial sums in order.
 constexpr int kRedParts = 8;
-__global__ void __launch_bounds__(32 * kRedParts) k_gram_reduce(const double* __restrict__ ws, int parts,
-                                                                 double* __restrict__ M) {
+__global__ void __launch_bounds__(32 * kRedParts) k_gram_reduce(const double* __restrict__ ws_all, int parts,
+                                                                 size_t slot_elems, double* __restrict__ M_all) {
     __shared__ double acc[kRedParts][32];
+    const double* ws = ws_all + slot_elems * blockIdx.y;
+    double* M = M_all + (size_t)kMElems * blockIdx.y;
     const int o = blockIdx.x * 32 + (threadIdx.x & 31), g = threadIdx.x >> 5;
     double s0 = 0.0, s1 = 0.0;
     int b = g;
@@ -486,8 +504,10 @@ bool gram_supported(int n) { return n >= 12; }
 
 size_t gram_workspace_elems() { return (size_t)num_sms() * gram::kMElems; }
 
-cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, double* M,
-                        int* err, cudaStream_t st) {
+static int gram_grid(int n) { return (int)std::min<uint64_t>((1ull << (n - 6)) / gram::kKSets, (uint64_t)num_sms()); }
+
+cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, int* err,
+                        cudaStream_t st) {
     if (!gram_supported(n)) return cudaErrorInvalidValue;
     for (int i = 0; i + 1 < 6; ++i)  // descending target list
         if (targets[i] <= targets[i + 1]) return cudaErrorInvalidValue;
@@ -501,7 +521,7 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     for (int i = 0; i < 6; ++i) a.sorted[i] = targets[i];
     std::sort(a.sorted, a.sorted + 6);
     a.ntiles = (1ull << (n - 6)) / gram::kKSets;
-    const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
+    const int grid = gram_grid(n);
     // the lowest target bounds how many consecutive sets are adjacent amplitudes
     auto run = [&](auto kern) {
         cudaError_t r = allow_max_dynamic_smem(kern);
@@ -512,11 +532,17 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     // (16-byte copies measured faster than 32-byte loads or 256-byte bulk copies here)
     // 16-byte copies need 16-byte aligned states (a wrapped buffer may be 8-byte aligned only)
     const bool a16 = (((uintptr_t)psi | (uintptr_t)lam) & 15) == 0;
-    cudaError_t e = a16 && a.sorted[0] >= 1 ? run(gram::k_gram6<2>) : run(gram::k_gram6<1>);
+    cudaError_t e = !a16 ? run(gram::k_gram6<1>) : a.sorted[0] >= 1 ? run(gram::k_gram6<2>) : run(gram::k_gram6<0>);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gram::k_gram_reduce<<<gram::kMElems / 32, 32 * gram::kRedParts, 0, st>>>(ws, grid, M);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_reduce(const double* ws, int n, int nslots, double* Mall, cudaStream_t st) {
+    if (nslots <= 0) return cudaSuccess;
+    const dim3 grid(gram::kMElems / 32, (unsigned)nslots);
+    gram::k_gram_reduce<<<grid, 32 * gram::kRedParts, 0, st>>>(ws, gram_grid(n), gram_workspace_elems(), Mall);
     return cudaGetLastError();
 }
 

@@ -624,46 +624,46 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
     return cudaErrorInvalidValue;
 }
 
-// Pinned host staging for the streamed path's matrix uploads (a copy from
-// pageable memory may wait for the stream's earlier work before it is
-// staged).  One buffer per host thread, reused once the stream has consumed
-// the previous call's copies.
+// one pinned staging buffer per host thread for the streamed path's matrix
+// uploads (PinnedStage: a copy from pageable memory may wait for the
+// stream's earlier work before it is staged)
 namespace {
-struct PinnedStage {
-    char* p = nullptr;
-    size_t cap = 0;
-    cudaEvent_t done = nullptr;  // recorded after the last copy out of the buffer
-    int dev = -1;
-    ~PinnedStage() {
-        if (done) cudaEventSynchronize(done);
-        if (p) cudaFreeHost(p);
-        if (done) cudaEventDestroy(done);
-    }
-    cudaError_t reserve(size_t bytes, int device) {
-        if (done) {
-            cudaError_t e = cudaEventSynchronize(done);
-            if (e != cudaSuccess) return e;
-        }
-        if (dev != device && done) {
-            cudaEventDestroy(done);
-            done = nullptr;
-        }
-        if (!done) {
-            cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
-            if (e != cudaSuccess) return e;
-            dev = device;
-        }
-        if (bytes <= cap) return cudaSuccess;
-        if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
-        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocDefault);
-        if (e == cudaSuccess) cap = bytes;
-        return e;
-    }
-};
 thread_local PinnedStage t_stage;
 }  // namespace
+
+// The library's stream-ordered memory pool on the current device: it keeps
+// what it has reserved between calls (the adjoint sweep's scratch, tens to
+// hundreds of MB, is then not mapped again on every call); the memory is
+// held until the process exits.
+cudaError_t qsgb::lib_malloc_async(void** ptr, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&pools[dev], &props);
+            if (e != cudaSuccess) {
+                pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = ~0ull;
+            e = cudaMemPoolSetAttribute(pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) return e;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+}
+
 
 // Fuse and run together (qs_apply_circuit and the adjoint gradient's forward
 // on the tensor cores): a host thread runs the block search and hands over
@@ -676,8 +676,9 @@ thread_local PinnedStage t_stage;
 // keep qubit 0 out of the 6-qubit passes' targets here too: the window's
 // leading run of 6-qubit passes is planned from the current exchange state,
 // the first pass is committed and launched.  The window grows with the
-// passes already queued (so the GPU starts at once) and spans up to 8 passes
-// once the search is done.
+// passes already queued (so the GPU starts at once, also when the grouping
+// comes from the cache all at once) up to 3 passes while the search runs and
+// 8 once it is done.
 qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
     constexpr size_t kWindow = 3, kWindowDone = 8;
     const int n = c->n;
@@ -787,7 +788,7 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
     std::deque<Pass> pending;
     size_t launched = 0;
     auto drain = [&](bool final, bool search_done) {
-        const size_t win = search_done ? kWindowDone : std::min(kWindow, launched);
+        const size_t win = std::min(search_done ? kWindowDone : kWindow, launched);
         while (st == QS_OK && !pending.empty() && (final || pending.size() > win)) {
             Pass& p0 = pending.front();
             if (p0.kind == PASS_GEMM) {

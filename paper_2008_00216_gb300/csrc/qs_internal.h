@@ -239,6 +239,46 @@ namespace qsgb {
 // qs_plan_create with the matrices uploaded and (at destruction) freed in the
 // order of `stream` (no device-wide synchronisation); nullptr = qs_plan_create.
 qs_status plan_create_on(const qs_circuit* c, qs_dtype dt, const qs_options* opt, cudaStream_t stream, qs_plan** out);
+// Pinned host staging for uploads that must not wait for the stream: a copy
+// from pageable memory may wait for the stream's earlier work before it is
+// staged.  A buffer is reused once the stream has consumed its last copies
+// (`done`, recorded by the user after them).
+struct PinnedStage {
+    char* p = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;  // recorded after the last copy out of the buffer
+    int dev = -1;
+    ~PinnedStage() {
+        if (done) cudaEventSynchronize(done);
+        if (p) cudaFreeHost(p);
+        if (done) cudaEventDestroy(done);
+    }
+    cudaError_t reserve(size_t bytes, int device) {
+        if (done) {
+            cudaError_t e = cudaEventSynchronize(done);
+            if (e != cudaSuccess) return e;
+        }
+        if (dev != device && done) {
+            cudaEventDestroy(done);
+            done = nullptr;
+        }
+        if (!done) {
+            cudaError_t e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+            if (e != cudaSuccess) return e;
+            dev = device;
+        }
+        if (bytes <= cap) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocDefault);
+        if (e == cudaSuccess) cap = bytes;
+        return e;
+    }
+};
+// stream-ordered allocation from the library's memory pool on the current
+// device (keeps its reservations between calls; free with cudaFreeAsync)
+cudaError_t lib_malloc_async(void** ptr, size_t bytes, cudaStream_t st);
 // A plan of ready passes (matrices uploaded and converted, in `stream` order when given).
 qs_status plan_from_passes(int n, qs_dtype dt, const qs_options& opt, std::vector<Pass>&& passes, cudaStream_t stream,
                            qs_plan** out);
@@ -309,12 +349,15 @@ struct BlockGradGate {
     uint32_t moff;           // offset of its 2^k x 2^k complex64 matrix in the gate-matrix array
 };
 bool gram_supported(int n);
-size_t gram_workspace_elems();   // doubles of the per-CTA parts
-// M (2 x 64 x 64 FP64: Re rows, then Im rows) = sum over the sets of
-// psi_s lambda_s^dagger over the six `targets` (descending); ws holds
-// gram_workspace_elems() doubles.
-cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, double* M,
-                        int* err, cudaStream_t st);
+size_t gram_workspace_elems();   // doubles of one Gram matrix's per-CTA parts
+// The per-CTA parts (into ws, gram_workspace_elems() doubles) of
+// M = sum over the sets of psi_s lambda_s^dagger over the six `targets`
+// (descending); M is 2 x 64 x 64 FP64, Re rows then Im rows.
+cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, int* err,
+                        cudaStream_t st);
+// M of nslots Gram matrices (Mall, 8192 doubles each) from their parts
+// (ws, gram_workspace_elems() doubles each), FP64 in a fixed order.
+cudaError_t launch_gram_reduce(const double* ws, int n, int nslots, double* Mall, cudaStream_t st);
 // One CTA per block: gates[gate0[b] .. gate0[b+1]) from the block's last
 // gate to its first; gradient of parameter p into sums[2p + 1].
 cudaError_t launch_block_grads(const double* Mall, int nslots, const BlockGradGate* gates, const int* gate0,
