@@ -629,6 +629,29 @@ static cudaError_t launch_pass(qs_state* s, const Pass& ps, const void* dm, int 
 // stream's earlier work before it is staged)
 namespace {
 thread_local PinnedStage t_stage;
+// a copy stream per host thread (and device) for those uploads, so that a
+// pass's matrix copy does not sit between two kernels of the state's stream
+struct CopyLane {
+    int dev = -1;
+    cudaStream_t cs = nullptr;
+    cudaEvent_t ev = nullptr;
+    ~CopyLane() {
+        if (ev) cudaEventDestroy(ev);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    cudaError_t get(int device) {
+        if (dev == device && cs) return cudaSuccess;
+        if (ev) cudaEventDestroy(ev);
+        if (cs) cudaStreamDestroy(cs);
+        ev = nullptr;
+        cs = nullptr;
+        dev = device;
+        cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        return e;
+    }
+};
+thread_local CopyLane t_copy;
 }  // namespace
 
 // The library's stream-ordered memory pool on the current device: it keeps
@@ -737,36 +760,46 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
     int dev = 0;
     cudaError_t ge = cudaGetDevice(&dev);
     if (ge == cudaSuccess) ge = t_stage.reserve(2u << 20, dev);  // 64 complex64 6-qubit matrices
+    if (ge == cudaSuccess) ge = t_copy.get(dev);
+    // the device copies of the staged matrices: one buffer for the call,
+    // filled on the copy stream once its allocation is ordered there
+    char* dbuf = nullptr;
+    if (ge == cudaSuccess) ge = cudaMallocAsync(reinterpret_cast<void**>(&dbuf), t_stage.cap, s->stream);
+    if (ge == cudaSuccess) ge = cudaEventRecord(t_copy.ev, s->stream);
+    if (ge == cudaSuccess) ge = cudaStreamWaitEvent(t_copy.cs, t_copy.ev, 0);
     if (ge != cudaSuccess) st = cuda_fail(ge, "pinned staging");
     size_t stage_at = 0;  // bytes of the staging buffer used by this call
     auto launch_one = [&](Pass& p) {
-        void* dm = nullptr;
+        void* dm = nullptr;    // a matrix allocated for this pass alone
+        void* mine = nullptr;  // where the pass reads its matrix
         const size_t elems = p.mats.size() / 2;
         cudaError_t e = cudaSuccess;
         if (elems && p.kind != PASS_DENSE && p.kind != PASS_DIAG && p.kind != PASS_MONO) {
             const size_t bytes = elems * esz;
-            const void* src;
             std::vector<char> host;
-            if (stage_at + bytes <= t_stage.cap) {  // pinned: the copy is fully asynchronous
-                char* dst = t_stage.p + stage_at;
+            if (dbuf && stage_at + bytes <= t_stage.cap) {  // pinned, on the copy stream
+                char* src = t_stage.p + stage_at;
                 for (size_t i = 0; i < p.mats.size(); ++i) {
-                    if (s->dt == QS_C64) ((float*)dst)[i] = (float)p.mats[i];
-                    else ((double*)dst)[i] = p.mats[i];
+                    if (s->dt == QS_C64) ((float*)src)[i] = (float)p.mats[i];
+                    else ((double*)src)[i] = p.mats[i];
                 }
-                src = dst;
+                mine = dbuf + stage_at;
                 stage_at += (bytes + 255) & ~(size_t)255;
+                e = cudaMemcpyAsync(mine, src, bytes, cudaMemcpyHostToDevice, t_copy.cs);
+                if (e == cudaSuccess) e = cudaEventRecord(t_copy.ev, t_copy.cs);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(s->stream, t_copy.ev, 0);
             } else {  // beyond the staging buffer: a pageable source, staged by the driver
                 host.resize(bytes);
                 for (size_t i = 0; i < p.mats.size(); ++i) {
                     if (s->dt == QS_C64) ((float*)host.data())[i] = (float)p.mats[i];
                     else ((double*)host.data())[i] = p.mats[i];
                 }
-                src = host.data();
+                e = cudaMallocAsync(&dm, bytes, s->stream);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(dm, host.data(), bytes, cudaMemcpyHostToDevice, s->stream);
+                mine = dm;
             }
-            e = cudaMallocAsync(&dm, bytes, s->stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(dm, src, bytes, cudaMemcpyHostToDevice, s->stream);
         }
-        if (e == cudaSuccess) e = launch_pass(s, p, dm, opt.precision);
+        if (e == cudaSuccess) e = launch_pass(s, p, mine, opt.precision);
         if (dm) cudaFreeAsync(dm, s->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "streamed pass");
     };
@@ -834,8 +867,13 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
     }
     for (auto& w : workers) w.join();
     search.join();
-    if (fst != QS_OK) return fail(fst, "%s", fmsg.c_str());
+    if (fst != QS_OK) {
+        if (dbuf) cudaFreeAsync(dbuf, s->stream);
+        if (t_stage.done) cudaEventRecord(t_stage.done, s->stream);
+        return fail(fst, "%s", fmsg.c_str());
+    }
     drain(true, true);
+    if (dbuf) cudaFreeAsync(dbuf, s->stream);  // after the passes, which waited for every copy
     if (t_stage.done) cudaEventRecord(t_stage.done, s->stream);  // the staging buffer is free once this passes
     return st;
 }
