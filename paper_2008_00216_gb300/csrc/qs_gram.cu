@@ -85,6 +85,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // row, W rows per warp instruction).  W = 0: qubit 0 is a target (local
 // bit 0), so rows 2i and 2i + 1 of a set are adjacent amplitudes: a lane
 // copies that pair (raw layout [row pair][set][2]) and converts as W = 1.
+// W = 3: qubits 0..2 are targets, so a warp's 8 rows of a set are 64
+// adjacent bytes, four lanes' copies (raw layout [set][8 rows], 16-byte
+// chunks swizzled by the set so that a lane per set reads them without
+// conflicts); converts as W = 1.
 template <int W>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gram6(const float2* __restrict__ psi, const float2* __restrict__ lam, const __grid_constant__ Args a,
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float2* src = pw < 8 ? psi : lam;
         const int l0 = (pw & 7) * 8;
         const uint32_t part = pw < 8 ? 0u : 2u * kPart;
-        constexpr int WC = W == 0 ? 1 : W;          // sets per lane in the conversion
+        constexpr int WC = (W == 0 || W == 3) ? 1 : W;  // sets per lane in the conversion
         constexpr int LPR = 32 / WC, NLD = 8 / WC;  // lanes per row, rows per lane
         const int rsub = lane / LPR, s0 = (lane % LPR) * WC;  // row within a copy, first set
         // raw layout: [stage][warp][row 0..7][32 sets] complex64 (256-byte rows)
@@ -144,8 +148,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint64_t t = blockIdx.x + it * gridDim.x;
                 const float2* p = src + set_base(t * kKSets + (uint64_t)s0, a.sorted);
                 const int slot = (int)(it % kRaw);
+                if constexpr (W == 3) {  // per set, the warp's 8 rows are 64 adjacent bytes: 4 lanes, 16 each
 #pragma unroll
-                if constexpr (W == 0) {  // rows 2i, 2i + 1 of set `lane`: 16 adjacent bytes
+                    for (int i = 0; i < 4; ++i) {
+                        const int ss = 8 * i + (lane >> 2), c = lane & 3;
+                        const float2* g = src + set_base(t * kKSets + (uint64_t)ss, a.sorted) + a.off[l0] + 2 * c;
+                        unsigned char* d =
+                            sm + kRawOff + slot * kRawStage + pw * 2048 + ss * 64 + ((c ^ ((ss >> 1) & 3)) << 4);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(d)), "l"(g) : "memory");
+                    }
+                } else if constexpr (W == 0) {  // rows 2i, 2i + 1 of set `lane`: 16 adjacent bytes
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(
@@ -177,20 +189,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();               // and the other lanes' (each warp reads only its own rows)
             float v[NLD][2 * WC];
             const int slot = (int)(it % kRaw);
+            if constexpr (W == 3) {  // lane = set; chunk c holds rows 2c, 2c + 1 (swizzled by set)
 #pragma unroll
-            for (int i = 0; i < NLD; ++i) {
-                const unsigned char* q = W == 0 ? sm + kRawOff + slot * kRawStage + pw * 2048 + (i >> 1) * 512 + lane * 16 + (i & 1) * 8
-                                                : raw_at(slot, WC * i + rsub);
-                if constexpr (W == 2) {
-                    const float4 x = *reinterpret_cast<const float4*>(q);
-                    v[i][0] = x.x;
-                    v[i][1] = x.y;
-                    v[i][2] = x.z;
-                    v[i][3] = x.w;
-                } else {
-                    const float2 x = *reinterpret_cast<const float2*>(q);
-                    v[i][0] = x.x;
-                    v[i][1] = x.y;
+                for (int c = 0; c < 4; ++c) {
+                    const float4 x = *reinterpret_cast<const float4*>(sm + kRawOff + slot * kRawStage + pw * 2048 +
+                                                                      lane * 64 + ((c ^ ((lane >> 1) & 3)) << 4));
+                    v[2 * c][0] = x.x;
+                    v[2 * c][1] = x.y;
+                    v[2 * c + 1][0] = x.z;
+                    v[2 * c + 1][1] = x.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < NLD; ++i) {
+                    const unsigned char* q = W == 0 ? sm + kRawOff + slot * kRawStage + pw * 2048 + (i >> 1) * 512 + lane * 16 + (i & 1) * 8
+                                                    : raw_at(slot, WC * i + rsub);
+                    if constexpr (W == 2) {
+                        const float4 x = *reinterpret_cast<const float4*>(q);
+                        v[i][0] = x.x;
+                        v[i][1] = x.y;
+                        v[i][2] = x.z;
+                        v[i][3] = x.w;
+                    } else {
+                        const float2 x = *reinterpret_cast<const float2*>(q);
+                        v[i][0] = x.x;
+                        v[i][1] = x.y;
+                    }
                 }
             }
             if (u > 0 && !mbar_wait(&empty[st], (uint32_t)((u - 1) & 1), err, abort_flag)) return false;
@@ -532,7 +556,10 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     // (16-byte copies measured faster than 32-byte loads or 256-byte bulk copies here)
     // 16-byte copies need 16-byte aligned states (a wrapped buffer may be 8-byte aligned only)
     const bool a16 = (((uintptr_t)psi | (uintptr_t)lam) & 15) == 0;
-    cudaError_t e = !a16 ? run(gram::k_gram6<1>) : a.sorted[0] >= 1 ? run(gram::k_gram6<2>) : run(gram::k_gram6<0>);
+    cudaError_t e = !a16                ? run(gram::k_gram6<1>)
+                    : a.sorted[0] >= 1  ? run(gram::k_gram6<2>)
+                    : a.sorted[2] == 2  ? run(gram::k_gram6<3>)   // targets 0, 1, 2 (ascending, distinct)
+                                        : run(gram::k_gram6<0>);
     if (e != cudaSuccess) return e;
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
