@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait_then_release();  // the state is the previous pass's output
 
     if (warp >= kEpiWarps && warp < kMmaWarp) {
         // ================= producer: TMEM quadrant q, local indices 32kh..32kh+31
@@ -508,7 +509,8 @@ static cudaError_t run_q(float2* psi, const float2* U, const Args& a, int* err, 
     cudaError_t e = allow_max_dynamic_smem(k_gemm6<SPLITS, KIND, Q0T>);
     if (e != cudaSuccess) return e;
     const int grid = (int)std::min<uint64_t>(a.ntiles, (uint64_t)num_sms());
-    k_gemm6<SPLITS, KIND, Q0T><<<grid, kThreads, smem, st>>>(psi, U, a, err);
+    e = launch_pdl(k_gemm6<SPLITS, KIND, Q0T>, dim3(grid), dim3(kThreads), (size_t)smem, st, psi, U, a, err);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -126,6 +126,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_wait_then_release();  // psi and lambda are the previous passes' outputs
     // this CTA's stages: tiles blockIdx.x + it * gridDim.x, it < my
     const uint64_t my = a.ntiles > blockIdx.x ? (a.ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const uint64_t nper = (my + kFlush - 1) / kFlush;
@@ -550,8 +551,8 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
     auto run = [&](auto kern) {
         cudaError_t r = allow_max_dynamic_smem(kern);
         if (r != cudaSuccess) return r;
-        kern<<<grid, gram::kThreads, gram::kSmem + 1024, st>>>((const float2*)psi, (const float2*)lam, a, ws, err);
-        return cudaSuccess;
+        return tc::launch_pdl(kern, dim3(grid), dim3(gram::kThreads), (size_t)(gram::kSmem + 1024), st, (const float2*)psi,
+                          (const float2*)lam, a, ws, err);
     };
     // (16-byte copies measured faster than 32-byte loads or 256-byte bulk copies here)
     // 16-byte copies need 16-byte aligned states (a wrapped buffer may be 8-byte aligned only)
