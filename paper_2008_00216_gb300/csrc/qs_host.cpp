@@ -728,6 +728,16 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
         done = true;
         cv.notify_all();
     });
+    auto form = [&](size_t i, const std::vector<int>& g) {  // group i's block and pass
+        GateRec b;
+        block_product(n, c->gates, g, b);
+        std::unique_ptr<Pass> p(new Pass);
+        single_block_pass(n, s->dt, opt, b, *p);
+        factor_tile_scalars(*p);
+        std::lock_guard<std::mutex> lk(mu);
+        formed[i] = std::move(p);
+        cv.notify_all();
+    };
     auto worker = [&]() {
         for (;;) {
             std::vector<int> g;
@@ -742,19 +752,17 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
                 i = next_group++;
                 g = groups[i];
             }
-            GateRec b;
-            block_product(n, c->gates, g, b);
-            std::unique_ptr<Pass> p(new Pass);
-            single_block_pass(n, s->dt, opt, b, *p);
-            factor_tile_scalars(*p);
-            std::lock_guard<std::mutex> lk(mu);
-            formed[i] = std::move(p);
-            cv.notify_all();
+            form(i, g);
         }
     };
+    // the workers start once the first pass is launched: the first block is
+    // formed on this thread, so the GPU does not wait for threads to start
     std::vector<std::thread> workers;
     const unsigned nw = std::max(1u, std::min(4u, host_threads(4)));
-    for (unsigned w = 0; w < nw; ++w) workers.emplace_back(worker);
+    auto start_workers = [&]() {
+        if (workers.empty())
+            for (unsigned w = 0; w < nw; ++w) workers.emplace_back(worker);
+    };
 
     qs_status st = QS_OK;
     int dev = 0;
@@ -846,9 +854,22 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
         }
         if (final && st == QS_OK && xs >= 0) restore();
     };
+    {
+        std::vector<int> g0;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            cv.wait(lk, [&]() { return !groups.empty() || done; });
+            if (!groups.empty() && next_group == 0) {
+                next_group = 1;
+                g0 = groups[0];
+            }
+        }
+        if (!g0.empty()) form(0, g0);
+    }
     for (size_t i = 0;; ++i) {
         std::unique_ptr<Pass> p;
         bool search_done;
+        if (i == 1) start_workers();
         {
             std::unique_lock<std::mutex> lk(mu);
             cv.wait(lk, [&]() { return (i < formed.size() && formed[i]) || (done && i >= groups.size()); });
