@@ -1008,8 +1008,11 @@ static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options&
             if ((used >> q) & 1) T[cnt++] = q;
         bs.slot.push_back((int)bs.targets.size());
         bs.targets.push_back(T);
-        for (size_t m = members.size(); m-- > 0;) {
-            const GateRec& gr = c.gates[members[m]];
+        // The block's gates last to first.  A run of diagonal gates with
+        // diagonal generators commutes, and its generators with every update
+        // inside it, so all its gradients come from the M at the run's end,
+        // followed by one elementwise update with the run's product.
+        auto record = [&](const GateRec& gr) {
             BlockGradGate bg{};
             bg.k = gr.k;
             for (int t = 0; t < gr.k; ++t) {
@@ -1026,10 +1029,66 @@ static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options&
                     bg.ny += pc == 'Y';
                 }
             bg.diag = gr.kind == QS_GATE_DIAGONAL;
+            return bg;
+        };
+        auto push_full = [&](BlockGradGate bg, const GateRec& gr) {
             bg.moff = (uint32_t)(bs.gmats.size() / 2);
             for (double v : gr.m) bs.gmats.push_back((float)v);
             bs.gates.push_back(bg);
+        };
+        std::vector<const GateRec*> run;  // the current run, in sweep order
+        // last: the run ends the block, and no update after it is read
+        auto flush_run = [&](bool last) {
+            if (run.empty()) return;
+            if (run.size() == 1 && !last) {
+                push_full(record(*run[0]), *run[0]);
+            } else {
+                std::vector<std::complex<double>> prod(64, 1.0);
+                for (const GateRec* g : run) {
+                    BlockGradGate bg = record(*g);
+                    const int d = 1 << g->k;
+                    for (int j = 0; j < 64; ++j) {
+                        int li = 0;
+                        for (int t = 0; t < g->k; ++t) li = (li << 1) | ((j >> bg.lb[t]) & 1);
+                        const double er = g->m[2 * (li * d + li)], ei = g->m[2 * (li * d + li) + 1];
+                        prod[j] = std::complex<double>(prod[j].real() * er - prod[j].imag() * ei,
+                                                       prod[j].real() * ei + prod[j].imag() * er);
+                    }
+                    if (g->param >= 0) {  // its gradient now; its update with the run's
+                        bg.flags = kGradNoUpdate;
+                        bg.moff = 0;
+                        bs.gates.push_back(bg);
+                    }
+                }
+                if (!last) {
+                    BlockGradGate bg{};
+                    bg.k = 6;
+                    for (int t = 0; t < 6; ++t) bg.lb[t] = 5 - t;  // gate index = local index
+                    bg.param = -1;
+                    bg.diag = 1;
+                    bg.flags = kGradCompactDiag;
+                    bg.moff = (uint32_t)(bs.gmats.size() / 2);
+                    for (const auto& z : prod) {
+                        bs.gmats.push_back((float)z.real());
+                        bs.gmats.push_back((float)z.imag());
+                    }
+                    bs.gates.push_back(bg);
+                }
+            }
+            run.clear();
+        };
+        for (size_t m = members.size(); m-- > 0;) {
+            const GateRec& gr = c.gates[members[m]];
+            BlockGradGate bg = record(gr);
+            if (bg.diag && bg.xmask == 0) {
+                run.push_back(&gr);
+                continue;
+            }
+            flush_run(false);
+            if (m == 0) bg.flags = kGradNoUpdate;  // the block's first gate: nothing reads M after it
+            if (bg.param >= 0 || m != 0) push_full(bg, gr);
         }
+        flush_run(true);
         bs.gate0.push_back((int)bs.gates.size());
     }
     for (size_t r = 0; r < G; ++r) bs.blocks.push_back(std::move(blocks[G - 1 - r]));

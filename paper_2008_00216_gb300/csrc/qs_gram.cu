@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kGradThreads) k_block_grads(const double* __re
     for (int i = tid; i < 4096; i += kGradThreads) Ms[i >> 6][i & 63] = make_float2((float)Mg[i], (float)Mg[4096 + i]);
     __syncthreads();
     for (int gi = gate0[slot]; gi < gate0[slot + 1]; ++gi) {
-        const int k = gates[gi].k, d = 1 << k, param = gates[gi].param, diag = gates[gi].diag;
+        const int k = gates[gi].k, d = 1 << k, param = gates[gi].param, diag = gates[gi].diag, flags = gates[gi].flags;
         const uint32_t moff = gates[gi].moff;
         // tables and U (M is not touched in this phase), and the gradient
         if (tid < 64) {
@@ -451,11 +451,12 @@ __global__ void __launch_bounds__(kGradThreads) k_block_grads(const double* __re
                 }
                 blk_of[tid] = x;
             }
-        } else if (tid < 128) {
+        } else if (tid < 128 && !(flags & kGradNoUpdate)) {
             const int e = tid - 64;
-            if (diag) Us[e] = mats[moff + (size_t)(e < d ? e : 0) * (d + 1)];  // diagonal entries
+            if (diag)  // diagonal entries
+                Us[e] = mats[moff + (size_t)(e < d ? e : 0) * ((flags & kGradCompactDiag) ? 1 : d + 1)];
         }
-        if (!diag)
+        if (!diag && !(flags & kGradNoUpdate))
             for (int e = tid; e < d * d; e += kGradThreads) Us[e] = mats[moff + e];
         if (param >= 0 && tid >= 128 && tid < 160) {
             const int ln = tid - 128;
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(kGradThreads) k_block_grads(const double* __re
             }
         }
         __syncthreads();  // tables and U written; the gradient has read M
+        if (flags & kGradNoUpdate) continue;
         if (diag) {  // M[i][j] <- conj(u_i) M[i][j] u_j
             for (int e = tid; e < 4096; e += kGradThreads) {
                 const int i = e >> 6, j = e & 63;

@@ -346,8 +346,10 @@ struct BlockGradGate {
     int param;               // parameter index, or -1
     int xmask, zmask, ny;    // generator in local bits: X or Y bits, Y or Z bits, number of Y
     int diag;                // the matrix is diagonal
+    int flags;               // kGradNoUpdate: gradient only; kGradCompactDiag: the 2^k diagonal entries alone
     uint32_t moff;           // offset of its 2^k x 2^k complex64 matrix in the gate-matrix array
 };
+constexpr int kGradNoUpdate = 1, kGradCompactDiag = 2;
 bool gram_supported(int n);
 size_t gram_workspace_elems();   // doubles of one Gram matrix's per-CTA parts
 // The per-CTA parts (into ws, gram_workspace_elems() doubles) of
