@@ -932,7 +932,9 @@ static qs_status build_reverse_sweep(const qs_circuit& c, int n, qs_dtype dt, co
 // tensor-core passes, and every gradient inside a block comes from its Gram
 // matrix M = sum_s psi_s lambda_s^dagger over the block's six qubits, taken
 // just before: <lambda_l|P_l|psi_l> = tr(P_l M_l) with M_l = W^dagger M W, W
-// the block's gates after gate l (Section 4.5's sweep, one block per step).
+// the block's gates after gate l (the reverse sweep, one block per step; the
+// blocks are the fusion groups of Sections 4.2-4.5, so their reverse order is
+// a valid reverse order of the circuit).
 struct BlockSweep {
     std::vector<GateRec> blocks;              // the forward blocks B, last first
     std::vector<Pass> passes;                 // their B^dagger passes, in the same order

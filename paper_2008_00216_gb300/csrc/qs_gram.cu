@@ -2,8 +2,9 @@
 //
 // The adjoint gradient of gate l, U_l = exp(-i theta_l P_l / 2), is
 // Im <lambda_l|P_l|psi_l> with psi_l, lambda_l the two states just after the
-// gate (Section 4.5's reverse sweep).  When the sweep undoes a whole fused
-// block B = U_m ... U_1 on six qubits T at once, every gradient inside it
+// gate (the reverse sweep).  When the sweep undoes a whole fused block
+// B = U_m ... U_1 on six qubits T at once (a group of the commuting-reorder
+// fusion of Sections 4.2-4.5), every gradient inside it
 // still follows from the two states taken before B^dagger is applied: with
 // x_s, y_s the 64 amplitudes of psi and lambda over T in set s,
 //   M = sum_s x_s y_s^dagger                      (64 x 64, all sets)
@@ -31,7 +32,8 @@
 // finished one into the CTA's FP64 part of M, so no FP32 sum runs over more
 // than 2048 sets.  Every mbarrier wait is bounded (about two seconds of
 // clock64); on timeout the CTA sets the error flag, drains its MMAs, frees
-// tensor memory and exits.
+// tensor memory and exits.  Launched with programmatic dependent launch: the
+// prologue runs while the previous pass finishes (pdl_wait_then_release).
 #include <stdint.h>
 
 #include <algorithm>
