@@ -9,7 +9,8 @@ walk over the block's records, then B^dagger on both states.  Its inputs
 psi = U|0> and lambda = H psi come from the FP64 oracle; its gradients must
 equal exact parameter shift on the oracle (to the complex64 gate matrices'
 rounding, which the records carry), with exactly one gradient record per
-parameter.  The circuit has blocks with every kind of target placement."""
+parameter.  Two circuits: blocks with every kind of target placement, and
+the benchmark's layered ansatz."""
 
 import os
 import shutil
@@ -75,14 +76,30 @@ def _compile(tmp):
     return exe
 
 
-def test_block_sweep_host_logic_matches_parameter_shift(tmp_path):
-    n, reps = 13, 2
-    P = block_circuit(n, reps, np.zeros(100000)).num_params
+def _ansatz(n, layers, theta):
+    circ = C.ansatz_circuit(n, layers, theta)
+    circ.num_params = C.ansatz_num_params(n, layers)
+    return circ
+
+
+@pytest.fixture(scope="module")
+def emulator(tmp_path_factory):
+    return _compile(str(tmp_path_factory.mktemp("emu")))
+
+
+@pytest.mark.parametrize("case", ["placements", "ansatz"])
+def test_block_sweep_host_logic_matches_parameter_shift(tmp_path, emulator, case):
+    if case == "placements":
+        n, make = 13, (lambda t: block_circuit(13, 2, t))
+        P = make(np.zeros(100000)).num_params
+    else:  # the benchmark's layered ansatz (RY, RZ, CZ chain)
+        n, make = 12, (lambda t: _ansatz(12, 3, t))
+        P = C.ansatz_num_params(12, 3)
     rng = Xoshiro256ss(727)
     theta = np.array([rng.uniform_range(-np.pi, np.pi) for _ in range(P)])
     terms = C.ising_hamiltonian(n) + [C.PauliTerm(0.5, ((2, "Y"), (n - 1, "X"))),
                                       C.PauliTerm(0.3, ((0, "Z"), (7, "Y")))]
-    circ = block_circuit(n, reps, theta)
+    circ = make(theta)
     psi = oracle.simulate(n, circ.gates)
     lam = oracle.apply_pauli_sum(psi, n, terms)
     tmp = str(tmp_path)
@@ -99,12 +116,11 @@ def test_block_sweep_host_logic_matches_parameter_shift(tmp_path):
         f.write("\n".join(lines) + "\n")
     psi.astype(np.complex128).tofile(os.path.join(tmp, "psi.bin"))
     lam.astype(np.complex128).tofile(os.path.join(tmp, "lam.bin"))
-    exe = _compile(tmp)
-    r = subprocess.run([exe, os.path.join(tmp, "circuit.txt"), os.path.join(tmp, "psi.bin"),
+    r = subprocess.run([emulator, os.path.join(tmp, "circuit.txt"), os.path.join(tmp, "psi.bin"),
                         os.path.join(tmp, "lam.bin")], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     g = np.array([float(x) for x in r.stdout.split()])
     assert g.shape == (P,)
-    ps = oracle.parameter_shift_gradient(n, lambda t: block_circuit(n, reps, t).gates, theta, terms)
+    ps = oracle.parameter_shift_gradient(n, lambda t: make(t).gates, theta, terms)
     # the records carry complex64 gate matrices: agreement to their rounding
     assert np.max(np.abs(g - ps)) < 1e-5 * max(1.0, np.max(np.abs(ps))), np.max(np.abs(g - ps))
