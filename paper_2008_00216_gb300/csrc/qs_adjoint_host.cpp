@@ -1121,7 +1121,7 @@ static qs_status run_block_sweep(BlockSweep& bs, const qs_options& fast, qs_stat
     const size_t o_gmats = o_gate0 + up(sizeof(int) * bs.gate0.size());
     const size_t host_bytes = o_gmats + up(sizeof(float) * bs.gmats.size());
     const size_t o_M = host_bytes, o_ws = o_M + up(sizeof(double) * 8192 * (size_t)nslots);
-    const size_t total = o_ws + sizeof(double) * gram_workspace_elems() * (size_t)nslots;
+    const size_t total = o_ws + sizeof(double) * gram_workspace_elems(psi->n) * (size_t)nslots;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = t_sweep_stage.reserve(host_bytes, dev);
@@ -1165,7 +1165,7 @@ static qs_status run_block_sweep(BlockSweep& bs, const qs_options& fast, qs_stat
         const int sl = bs.slot[i];
         if (sl >= 0)
             e = launch_gram(psi->data, lam->data, psi->n, bs.targets[sl].data(),
-                            ws + gram_workspace_elems() * (size_t)sl, psi->errflag, sm);
+                            ws + gram_workspace_elems(psi->n) * (size_t)sl, psi->errflag, sm);
         if (e != cudaSuccess) break;
         if (i + 1 == npass) break;  // the first block's inverse: nothing reads the states after it
         st = qs_plan_execute_range(psi, bs.inv, i, 1);

@@ -531,9 +531,10 @@ __global__ void __launch_bounds__(kGradThreads) k_block_grads(const double* __re
 
 bool gram_supported(int n) { return n >= 12; }
 
-size_t gram_workspace_elems() { return (size_t)num_sms() * gram::kMElems; }
-
 static int gram_grid(int n) { return (int)std::min<uint64_t>((1ull << (n - 6)) / gram::kKSets, (uint64_t)num_sms()); }
+
+// one part per CTA of the n-qubit Gram kernel's grid
+size_t gram_workspace_elems(int n) { return (size_t)gram_grid(n) * gram::kMElems; }
 
 cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, int* err,
                         cudaStream_t st) {
@@ -574,7 +575,7 @@ cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targ
 cudaError_t launch_gram_reduce(const double* ws, int n, int nslots, double* Mall, cudaStream_t st) {
     if (nslots <= 0) return cudaSuccess;
     const dim3 grid(gram::kMElems / 32, (unsigned)nslots);
-    gram::k_gram_reduce<<<grid, 32 * gram::kRedParts, 0, st>>>(ws, gram_grid(n), gram_workspace_elems(), Mall);
+    gram::k_gram_reduce<<<grid, 32 * gram::kRedParts, 0, st>>>(ws, gram_grid(n), gram_workspace_elems(n), Mall);
     return cudaGetLastError();
 }
 

@@ -351,14 +351,14 @@ struct BlockGradGate {
 };
 constexpr int kGradNoUpdate = 1, kGradCompactDiag = 2;
 bool gram_supported(int n);
-size_t gram_workspace_elems();   // doubles of one Gram matrix's per-CTA parts
-// The per-CTA parts (into ws, gram_workspace_elems() doubles) of
+size_t gram_workspace_elems(int n);   // doubles of one n-qubit Gram matrix's per-CTA parts
+// The per-CTA parts (into ws, gram_workspace_elems(n) doubles) of
 // M = sum over the sets of psi_s lambda_s^dagger over the six `targets`
 // (descending); M is 2 x 64 x 64 FP64, Re rows then Im rows.
 cudaError_t launch_gram(const void* psi, const void* lam, int n, const int* targets, double* ws, int* err,
                         cudaStream_t st);
 // M of nslots Gram matrices (Mall, 8192 doubles each) from their parts
-// (ws, gram_workspace_elems() doubles each), FP64 in a fixed order.
+// (ws, gram_workspace_elems(n) doubles each), FP64 in a fixed order.
 cudaError_t launch_gram_reduce(const double* ws, int n, int nslots, double* Mall, cudaStream_t st);
 // One CTA per block: gates[gate0[b] .. gate0[b+1]) from the block's last
 // gate to its first; gradient of parameter p into sums[2p + 1].
