@@ -342,7 +342,7 @@ qs_status qs_apply_pauli_sum(const qs_state* psi, const qs_pauli_sum* h, qs_stat
  * (psi, lambda), then their inverse as fused passes.  Complex64 states of 12
  * or more qubits undo whole fused 6-qubit blocks instead: every gradient of
  * a block follows from the 64 x 64 matrix sum_s psi_s lambda_s^dag over its
- * qubits (tensor cores) and the block's gates; its scratch (about 64 KB per
+ * qubits (tensor cores) and the block's gates; its scratch (up to 64 KB per
  * SM for each block with parameters) comes from a memory pool of the library
  * that keeps its reservation until the process exits.  `psi` and `lam` are
  * work states with the circuit's n and a common dtype and stream (their
