@@ -952,19 +952,24 @@ struct BlockSweep {
 
 // Plan the block sweep; QS_ERR_UNSUPPORTED when a group is not one block of
 // at most six qubits (wide diagonal clusters), so the stage sweep is used.
-static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options& fast, BlockSweep& bs) {
+// known (optional): the groups' block products, already formed by the
+// streamed forward (taken over when there is one per group).
+static qs_status build_block_sweep(const qs_circuit& c, int n, const qs_options& fast, BlockSweep& bs,
+                                   std::vector<GateRec>* known = nullptr) {
     std::vector<std::vector<int>> groups;
     qs_status st = fuse_each(n, c.gates, 6, fast.fusion_effort, c.fuse_cache.get(),
                              [&](std::vector<int>&& g) { groups.push_back(std::move(g)); });
     if (st != QS_OK) return st;
     const size_t G = groups.size();
     std::vector<GateRec> blocks(G);
+    const bool reuse = known && known->size() == G;
+    if (reuse) blocks.swap(*known);
     std::vector<Pass> fwd_inv(G);
     std::vector<char> bad(G, 0);
     std::atomic<size_t> next(0);
     auto work = [&]() {
         for (size_t i = next++; i < G; i = next++) {
-            block_product(n, c.gates, groups[i], blocks[i]);
+            if (!reuse) block_product(n, c.gates, groups[i], blocks[i]);
             if (blocks[i].k == 0) {
                 bad[i] = 1;
                 continue;
@@ -1301,9 +1306,10 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
         ~BlockReleaser() { s.release(); }
     } block_releaser{bsw};
     bool use_blocks = false;
+    std::vector<GateRec> fwd_blocks;  // the forward's block products (kept when the sweep is planned here)
     auto plan_sweep = [&]() {
         if (psi->dt == QS_C64 && fast.k_max == 6 && gram_supported(psi->n)) {
-            sweep_st = build_block_sweep(*c, psi->n, fast, bsw);
+            sweep_st = build_block_sweep(*c, psi->n, fast, bsw, &fwd_blocks);
             if (sweep_st == QS_OK) {
                 use_blocks = true;
                 return;
@@ -1334,7 +1340,7 @@ qs_status qs_adjoint_gradient(qs_circuit* c, const double* theta, int num_params
     if (fast.k_max == 6) {  // on the tensor cores: fused and run together (the GPU starts at once)
         cudaError_t le = launch_init_basis(psi->data, psi->n, psi->dt, 0, sm);
         if (le != cudaSuccess) return cuda_fail(le, "init");
-        st = apply_streamed(psi, c, fast);
+        st = apply_streamed(psi, c, fast, own_thread ? nullptr : &fwd_blocks);
         if (st != QS_OK) return st;
     } else {
         qs_plan* fwd = nullptr;

@@ -702,7 +702,8 @@ cudaError_t qsgb::lib_malloc_async(void** ptr, size_t bytes, cudaStream_t st) {
 // passes already queued (so the GPU starts at once, also when the grouping
 // comes from the cache all at once) up to 3 passes while the search runs and
 // 8 once it is done.
-qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt) {
+qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt,
+                               std::vector<GateRec>* blocks_out) {
     constexpr size_t kWindow = 3, kWindowDone = 8;
     const int n = c->n;
     const size_t esz = s->amp_bytes();
@@ -710,6 +711,7 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
     std::condition_variable cv;
     std::vector<std::vector<int>> groups;           // in search order
     std::vector<std::unique_ptr<Pass>> formed;      // formed[i]: the pass of group i, once ready
+    std::deque<GateRec> kept;                       // kept[i]: group i's block (blocks_out only)
     size_t next_group = 0;                          // the next group a worker takes
     bool done = false, stop = false;
     qs_status fst = QS_OK;
@@ -720,6 +722,7 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
                                            std::lock_guard<std::mutex> lk(mu);
                                            groups.push_back(std::move(g));
                                            formed.emplace_back();
+                                           if (blocks_out) kept.emplace_back();
                                            cv.notify_all();
                                        });
         std::lock_guard<std::mutex> lk(mu);
@@ -736,6 +739,7 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
         factor_tile_scalars(*p);
         std::lock_guard<std::mutex> lk(mu);
         formed[i] = std::move(p);
+        if (blocks_out) kept[i] = std::move(b);
         cv.notify_all();
     };
     auto worker = [&]() {
@@ -896,6 +900,7 @@ qs_status qsgb::apply_streamed(qs_state* s, const qs_circuit* c, const qs_option
     drain(true, true);
     if (dbuf) cudaFreeAsync(dbuf, s->stream);  // after the passes, which waited for every copy
     if (t_stage.done) cudaEventRecord(t_stage.done, s->stream);  // the staging buffer is free once this passes
+    if (blocks_out && st == QS_OK) blocks_out->assign(std::make_move_iterator(kept.begin()), std::make_move_iterator(kept.end()));
     return st;
 }
 

@@ -297,7 +297,10 @@ qs_status build_passes(int n, qs_dtype dt, const std::vector<GateRec>& blocks,
 void single_block_pass(int n, qs_dtype dt, const qs_options& opt, const GateRec& g, Pass& p);
 // Fuse and run together on the tensor cores: each block's pass is launched
 // as soon as it is found and multiplied (qs_host.cpp)
-qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt);
+// blocks_out (optional): the block products of the circuit's fusion groups,
+// in group order (filled when the call succeeds)
+qs_status apply_streamed(qs_state* s, const qs_circuit* c, const qs_options& opt,
+                         std::vector<GateRec>* blocks_out = nullptr);
 // bit-0 placement over 6-qubit passes (qs_plan.cpp)
 int bit0_plan(int n, const std::vector<const Pass*>& run, int s0, bool end_free, std::vector<int>& choice);
 int bit0_apply(Pass& p, int s, int bc);

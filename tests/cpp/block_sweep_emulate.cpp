@@ -8,7 +8,9 @@
 // qubits, the gradient kernel's walk over the block's records (gradient
 // Im tr(P M), then M <- U^dagger M U), then B^dagger on both states.
 //
-// argv: circuit file, psi file, lambda file (complex128, little endian).
+// argv: circuit file, psi file, lambda file (complex128, little endian),
+// and optionally "known": the planner then takes the groups' block
+// products formed beforehand (as the streamed forward hands them over).
 // Circuit file: "n" on the first line, then one gate per line:
 //   R k q_0 .. q_{k-1} param paulis theta     (exp(-i theta P / 2))
 //   F k q_0 .. q_{k-1} m_0 .. m_{2 4^k - 1}    (row-major, interleaved)
@@ -55,7 +57,8 @@ static std::vector<Cd> read_state(const char* path, int n) {
 }
 
 int main(int argc, char** argv) {
-    if (argc != 4) return 2;
+    if (argc != 4 && argc != 5) return 2;
+    const bool known_blocks = argc == 5 && std::string(argv[4]) == "known";
     std::ifstream cf(argv[1]);
     int n = 0;
     cf >> n;
@@ -88,7 +91,17 @@ int main(int argc, char** argv) {
     fast.precision = QS_PREC_3XTF32;
     fast.fusion_effort = 1;
     BlockSweep bs;
-    if (build_block_sweep(*c, n, fast, bs) != QS_OK) return 6;
+    std::vector<GateRec> known;
+    if (known_blocks) {
+        std::vector<std::vector<int>> groups;
+        if (fuse_each(n, c->gates, 6, fast.fusion_effort, c->fuse_cache.get(),
+                      [&](std::vector<int>&& g) { groups.push_back(std::move(g)); }) != QS_OK)
+            return 8;
+        known.resize(groups.size());
+        for (size_t i = 0; i < groups.size(); ++i) block_product(n, c->gates, groups[i], known[i]);
+    }
+    if (build_block_sweep(*c, n, fast, bs, known_blocks ? &known : nullptr) != QS_OK) return 6;
+    if (known_blocks && !known.empty() && !known[0].m.empty()) return 9;  // the planner must have taken them over
     std::vector<double> grad(nparams, 0.0);
     std::vector<int> seen(nparams, 0);
     for (size_t i = 0; i < bs.blocks.size(); ++i) {

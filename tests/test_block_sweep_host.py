@@ -87,12 +87,12 @@ def emulator(tmp_path_factory):
     return _compile(str(tmp_path_factory.mktemp("emu")))
 
 
-@pytest.mark.parametrize("case", ["placements", "ansatz"])
+@pytest.mark.parametrize("case", ["placements", "ansatz", "ansatz-known-blocks"])
 def test_block_sweep_host_logic_matches_parameter_shift(tmp_path, emulator, case):
     if case == "placements":
         n, make = 13, (lambda t: block_circuit(13, 2, t))
         P = make(np.zeros(100000)).num_params
-    else:  # the benchmark's layered ansatz (RY, RZ, CZ chain)
+    else:  # the benchmark's layered ansatz (RY, RZ, CZ chain); "known": blocks formed beforehand
         n, make = 12, (lambda t: _ansatz(12, 3, t))
         P = C.ansatz_num_params(12, 3)
     rng = Xoshiro256ss(727)
@@ -116,8 +116,10 @@ def test_block_sweep_host_logic_matches_parameter_shift(tmp_path, emulator, case
         f.write("\n".join(lines) + "\n")
     psi.astype(np.complex128).tofile(os.path.join(tmp, "psi.bin"))
     lam.astype(np.complex128).tofile(os.path.join(tmp, "lam.bin"))
-    r = subprocess.run([emulator, os.path.join(tmp, "circuit.txt"), os.path.join(tmp, "psi.bin"),
-                        os.path.join(tmp, "lam.bin")], capture_output=True, text=True, timeout=600)
+    args = [emulator, os.path.join(tmp, "circuit.txt"), os.path.join(tmp, "psi.bin"), os.path.join(tmp, "lam.bin")]
+    if case.endswith("known-blocks"):
+        args.append("known")
+    r = subprocess.run(args, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, (r.returncode, r.stderr[-2000:])
     g = np.array([float(x) for x in r.stdout.split()])
     assert g.shape == (P,)
